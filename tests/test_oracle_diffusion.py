@@ -1,0 +1,135 @@
+"""Pins for the oracle's diffusion (Sec. 3.7, App. A) and RKL2 (Sec. 3.7.2)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import sft_inputs as I
+
+NU500 = 500.0 * O.KM2_S_TO_RS2_HR
+
+
+def test_stencil_equals_assembled_matrix_with_variable_nu():
+    """Eq. (diffusion_op) applied directly == the Eq. (diffusion_matrix)
+    coefficients assembled entry by entry (brute force, 8 x 16, random nu)."""
+    rng = np.random.default_rng(1)
+    g = O.Grid(8, 16)
+    nu = rng.uniform(0.5, 2.0, size=(g.nt - 1, g.np))
+    B = rng.normal(size=(g.nt, g.np))
+    B[0] = B[0, 0]
+    B[-1] = B[-1, 0]
+    L = O.diffusion_operator(g, B, nu)
+    M = O.diffusion_matrix(g, nu)
+    got = M @ O.unique_unknowns(B)
+    np.testing.assert_allclose(got, O.unique_unknowns(L), rtol=1e-12, atol=1e-12 * np.abs(L).max())
+
+
+def test_matrix_is_self_adjoint_and_annihilates_constants():
+    rng = np.random.default_rng(2)
+    g = O.Grid(10, 12)
+    nu = rng.uniform(0.5, 2.0, size=(g.nt - 1, g.np))
+    M = O.diffusion_matrix(g, nu).toarray()
+    w = O.unique_unknowns(g.area)
+    w[0] = w[-1] = g.cap_area
+    WM = w[:, None] * M
+    assert np.abs(WM - WM.T).max() <= 1e-13 * np.abs(WM).max()
+    assert np.abs(M.sum(axis=1)).max() <= 1e-12 * np.abs(M).max()
+
+
+def test_diffusion_conserves_total_flux():
+    g = O.Grid(24, 48)
+    B = I.initial_map(24, 48, seed=11)
+    L = O.diffusion_operator(g, B, O.constant_nu(g, NU500))
+    assert abs((g.area * L).sum()) <= 1e-14 * (g.area * np.abs(L)).sum()
+
+
+def test_euler_limit_bounds_the_spectrum():
+    g = O.Grid(9, 12)
+    nu = O.constant_nu(g, 1.0)
+    M = O.diffusion_matrix(g, nu).toarray()
+    lam = np.linalg.eigvals(M)
+    assert np.abs(lam.imag).max() < 1e-9 * np.abs(lam).max()
+    dte = O.euler_dt_limit(g, nu)
+    true_limit = 2.0 / np.abs(lam.real).max()
+    assert dte <= true_limit * (1 + 1e-12)
+    assert dte >= 0.5 * true_limit
+
+
+def test_euler_limit_matches_paper_512x1024(paper_values):
+    v = paper_values["euler_dt_512x1024_nu500_hours"]
+    g = O.Grid(512, 1024)
+    dte = O.euler_dt_limit(g, O.constant_nu(g, NU500))
+    assert dte == pytest.approx(v["value"], rel=v["rel_tol"])
+
+
+def _rkl2_scalar(s, z):
+    z = np.asarray(z, dtype=np.complex128)
+    return O.rkl2_advance(np.ones_like(z), 1.0, lambda y: z * y, s)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 7, 16, 50, 145, 600])
+def test_rkl2_stable_on_its_interval(s):
+    """|R_s(z)| <= 1 for z in [-(s^2+s-2)/2, 0] (Meyer, Balsara & Aslam 2014)."""
+    z = np.linspace(-(s * s + s - 2) / 2.0, 0.0, 40001)
+    assert np.abs(_rkl2_scalar(s, z)).max() <= 1.0 + 1e-9
+
+
+@pytest.mark.parametrize("s", [2, 5, 40])
+def test_rkl2_is_second_order(s):
+    for z in (1e-2, 2e-3):
+        err = abs(_rkl2_scalar(s, [-z])[0] - (1 - z + z * z / 2))
+        assert err < 0.5 * z**3
+
+
+def test_rkl2_stage_count_is_minimal():
+    for ratio in (0.3, 1.0, 1.01, 7.9, 20888.0, 1.4e7):
+        s = O.rkl2_stage_count(ratio, 1.0)
+        assert (s * s + s - 2) / 4.0 >= ratio
+        assert s == 2 or ((s - 1) ** 2 + (s - 1) - 2) / 4.0 < ratio
+
+
+def test_soccer_ball_second_order_in_space(paper_values):
+    """Eq. (soccerball) decays as exp(-42 nu t); the discrete solution
+    converges at second order (Sec. 3.8)."""
+    errs = []
+    for nt, np_ in ((32, 64), (64, 128), (128, 256)):
+        g = O.Grid(nt, np_)
+        r = O.Realization(g, O.Params(advection=False, nu=500.0), I.soccer_ball(nt, np_))
+        r.dt_adv = 8.0
+        r.advance(672.0)
+        errs.append(O.hh_metric(r.B, I.soccer_ball(nt, np_, NU500, 672.0)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 <= o <= 2.2 for o in orders), orders
+
+
+def test_axial_dipole_decay_and_pole_cap():
+    """l = 1: cos(theta) decays as exp(-2 nu t); the pole cap value follows it
+    and the measured axial dipole converges at second order."""
+    dec = math.exp(-2.0 * NU500 * 672.0)
+    errD = []
+    for nt, np_ in ((32, 64), (64, 128)):
+        g = O.Grid(nt, np_)
+        r = O.Realization(g, O.Params(advection=False, nu=500.0), I.dipole(nt, np_, 1.0))
+        r.dt_adv = 24.0
+        r.advance(672.0)
+        assert r.B[0, 0] == pytest.approx(dec, rel=2e-5)
+        assert r.B[-1, 0] == pytest.approx(-dec, rel=2e-5)
+        errD.append(abs(O.diagnostics(g, r.B).dipole_axial / dec - 1))
+    assert 1.8 <= math.log2(errD[0] / errD[1]) <= 2.2
+
+
+def test_soccer_ball_one_rkl2_step_matches_paper(paper_values):
+    """Sec. 3.7.2: one 672 hr RKL2 step of the diffusion-only soccer ball at
+    512x1024 ends with HH = 8.0e-5.  The oracle's matrix form (pinned equal
+    to its stencil above) is used for speed."""
+    v = paper_values["soccer_ball_rkl2_one_step_hh"]
+    nu = v["nu_km2_s"] * O.KM2_S_TO_RS2_HR
+    g = O.Grid(v["nt"], v["np"])
+    M = O.diffusion_matrix(g, O.constant_nu(g, nu))
+    dte = 1.0 / np.abs(M.diagonal()).max()
+    s = O.rkl2_stage_count(v["t_hours"], dte)
+    u0 = O.unique_unknowns(I.soccer_ball(g.nt, g.np))
+    u = O.rkl2_advance(u0, v["t_hours"], lambda y: M @ y, s)
+    ex = O.unique_unknowns(I.soccer_ball(g.nt, g.np, nu, v["t_hours"]))
+    assert O.hh_metric(u, ex) == pytest.approx(v["value"], rel=v["rel_tol"])
