@@ -1,0 +1,328 @@
+"""Benchmark of the batched SFT step (one JSON line on rank 0).
+
+Workload (the batched-ensemble configuration): 64 realizations on a
+1024(theta) x 2048(phi) grid, FP32 state, per-realization rotation
+coefficients +-10 %, meridional amplitude U[10,20] m/s and eta U[250,750]
+km^2/s (seed 3), 8 seeded dipole + active-region start maps, CFL-limited
+steps toward a 27-day end time.  One bench "step" = one call of sft_step
+advancing every realization by one time step (SSPRK(4,3) WENO3-CS(h)
+advection + RKL2 diffusion, ~410-714 stages) plus the FP64 flux
+diagnostics of every realization.
+
+value: realization-cell-updates/s (sum over realizations of ntheta*nphi per
+step / device time), inputs resident in HBM.  e2e: the same step driven
+through the C-ABI with pinned host buffers (set_state from host, step,
+get_state to host) inside the timed region.  roofline: the RKL2 stage
+kernel (dominant), algorithmic bytes (4s-1 words per cell per step) over
+its CUDA-event time.  cpu_baseline: the FP64 oracle on a bounded sample.
+
+Multi-GPU (torchrun): realizations are independent, so each rank runs its
+own 64-realization ensemble (weak scaling, no collective on the data path);
+the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+NT, NP, NREAL = 1024, 2048, 64
+T_END = 27 * 24.0
+WORKLOAD = ("batched ensemble: 64 realizations x 1024(theta) x 2048(phi), FP32 state, "
+            "FP64 flux diagnostics, SSPRK(4,3) WENO3-CS(h) + RKL2, eta U[250,750] km^2/s, "
+            "rotation +-10%, meridional U[10,20] m/s, 27-day run, CFL-limited steps")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(nreal, rank):
+    import sft_inputs as I
+    from paper_2501_06377_gb300.sft import FlowParams
+    draws = I.draw_realization_params(nreal, seed=3 + 1000 * rank)
+    params = [FlowParams(*d) for d in draws]
+    maps = [I.initial_map(NT, NP, seed=1 + i + 100 * rank).astype(np.float32) for i in range(8)]
+    return params, maps
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# --------------------------------------------------------------------------
+_ORACLE = {}
+
+
+def oracle_sample(n_stages=16):
+    """Time the FP64 oracle on one realization of the workload: one full
+    SSPRK(4,3) advection step plus n_stages of its RKL2 stages, and
+    extrapolate to a full step.  Returns (cell-updates/s, ms per full step,
+    description, seconds timed).  Set-up (tables, limits) is not timed."""
+    import oracle as O
+    import sft_inputs as I
+    if "r" not in _ORACLE:
+        d = I.draw_realization_params(1, seed=3)[0]
+        B0 = I.initial_map(NT, NP, seed=1)
+        _ORACLE["r"] = O.Realization(O.Grid(NT, NP), O.Params(*d), B0)
+    r = _ORACLE["r"]
+    dt = min(r.dt_adv, T_END)
+    s = O.rkl2_stage_count(dt, r.dt_euler)
+    t0 = time.perf_counter()
+    B1 = O.ssprk43_advance(r.B, dt, r.FA)
+    t1 = time.perf_counter()
+    mu, nu, mut, gt = O.rkl2_coefficients(s)
+    LY0 = r.L(B1)
+    Ym2, Ym1 = B1, B1 + mut[1] * dt * LY0
+    for j in range(2, n_stages + 1):
+        Y = (mu[j] * Ym1 + nu[j] * Ym2 + (1.0 - mu[j] - nu[j]) * B1
+             + mut[j] * dt * r.L(Ym1) + gt[j] * dt * LY0)
+        Ym2, Ym1 = Ym1, Y
+    t2 = time.perf_counter()
+    t_step = (t1 - t0) + (t2 - t1) * s / n_stages
+    cells = NT * NP
+    desc = ("1 realization of %dx%d: one SSPRK(4,3) advection step + %d of its %d RKL2 stages "
+            "timed (%.1f s), full step extrapolated" % (NT, NP, n_stages, s, t2 - t0))
+    return cells / t_step, 1e3 * t_step, desc, t2 - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_stages = 8
+    vals, tot = [], 0.0
+    for i in range(args.warmup + args.steps):
+        v, ms, desc, el = oracle_sample(n_stages)
+        tot += el
+        if i >= args.warmup:
+            vals.append((v, ms))
+    v = statistics.median(x[0] for x in vals)
+    ms = statistics.median(x[1] for x in vals)
+    line = {
+        "impl": "reference", "metric": "realization-cell-updates/s", "value": v,
+        "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "per step: " + desc},
+        "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2501_06377_gb300 import build as B
+    from paper_2501_06377_gb300.sft import Grid
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    stream = torch.cuda.Stream()
+    nreal = args.nreal
+    params, maps = make_inputs(nreal, rank)
+    g = Grid([(NT, NP)] * nreal, "fp32", stream=stream)
+    for r in range(nreal):
+        g.set_state(r, maps[r % len(maps)])
+    g.balance_flux()
+    g.set_flows(params)
+    cells_per_step = float(nreal * NT * NP)
+
+    def one_step():
+        n = g.step(T_END, max_steps=1)
+        g.diagnostics()
+        return n
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (autotune + graph capture happen in the first step)
+    for _ in range(args.warmup):
+        one_step()
+    g.reset_stats()
+    g.set_profiling(True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        e0.record(stream)
+        steps_done = 0
+        for _ in range(args.steps):
+            steps_done += one_step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    st = g.stats()
+    ms = max_over_ranks(ms)
+    updates = st["cell_updates"] * world
+    value = updates / (ms * 1e-3)
+    peak, peak_kind = _peaks()
+    diff_launch_ms = st["diff_ms"] / max(st["diff_launches"], 1)
+    diff_launch_bytes = st["diff_bytes"] / max(st["diff_launches"], 1)
+    achieved = diff_launch_bytes / (diff_launch_ms * 1e-3) / 1e9
+    launches_per_step = st["kernel_launches"] / max(st["global_steps"], 1)
+    # e2e: host-resident state, pinned host buffers, copies inside the timing
+    g.set_profiling(False)
+    e2e_ms = float("nan")
+    if not args.no_e2e:
+        host = [torch.from_numpy(maps[r % len(maps)].copy()).pin_memory() for r in range(nreal)]
+        e2e_steps = max(2, min(args.steps, 6))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for r in range(nreal):
+                g.set_state(r, host[r])
+            g.step(T_END, max_steps=1)
+            g.diagnostics()
+            for r in range(nreal):
+                g.get_state(r, host[r])
+        barrier()
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps)
+    bytes_state = nreal * NT * NP * 4
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cms, desc, el = oracle_sample(16)
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": desc}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": "realization-cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "realizations_per_gpu": nreal, "grid": [NT, NP],
+                       "l2": "inputs larger than L2 (537 MB per state array)",
+                       "parallelism": "realizations sharded over ranks, no collective",
+                       "cell_stage_updates_per_s": (st["diff_cell_stages"] + st["adv_cell_stages"])
+                       * world / (ms * 1e-3),
+                       "rkl2_stages_per_step": st["diff_cell_stages"] / max(st["cell_updates"], 1),
+                       "graph": True},
+            "roofline": {"bound": "hbm", "kernel": "rkl2_stage_kernel<float>", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind + " hbm_gbs",
+                         "bytes_per_launch": diff_launch_bytes, "ms_per_launch": diff_launch_ms,
+                         "traffic": None},
+            "e2e": {"value": cells_per_step * world / (e2e_ms * 1e-3), "unit": "cell-updates/s",
+                    "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": int(st["kernel_launches"] + 2 * st["global_steps"]),
+            "gpu_launches_per_step": launches_per_step + 2,
+            "clocks": clocks,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nreal", type=int, default=NREAL,
+                    help="realizations per GPU (smaller only for profiling captures)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * sft.h -- C-ABI of libsft, a GB300 (sm_103a) implementation of the
+ * surface-flux-transport (SFT) time step of HipFT (Caplan et al., "Open-source
+ * Flux Transport (OFT) I. HipFT").
+ *
+ * The library advances the radial photospheric field Br(theta, phi) of many
+ * independent realizations, each on its own uniform logically-rectangular
+ * grid (Sec. 3.2), by the model of Eq. (main_model) restricted to advection,
+ * diffusion and data assimilation:
+ *   - advection by analytic differential rotation and meridional flow
+ *     (Eq. dr, Eq. mf) with WENO3-CS(h) or upwind face fluxes (Sec. 3.6.1,
+ *     App. B) and SSPRK(4,3) / SSPRK(3,3) / forward-Euler stages (Sec. 3.6.2);
+ *   - diffusion with the 5-point operator of Eq. (diffusion_op) advanced by
+ *     RKL2 super time stepping (Sec. 3.7.2);
+ *   - finite-volume polar caps (App. A) and a periodic phi boundary;
+ *   - Lie operator splitting A then D (Eq. num_opsplit_nostrang) with the
+ *     time-step controller of Sec. 3.4;
+ *   - the weighted, optionally flux-balanced assimilation blend of Sec. 2.3
+ *     (Eq. data_assim, data_assim_f, data_assim_deltab, fluxbal);
+ *   - the analysis quantities of Sec. 2.6.
+ *
+ * Conventions for every call:
+ *   - Maps are row-major [ntheta][nphi], phi contiguous, in the handle's
+ *     precision (float for SFT_FP32, double for SFT_FP64).  ntheta counts
+ *     theta points INCLUDING both poles (theta_j = j*pi/(ntheta-1)); nphi
+ *     counts unique longitudes (phi_k = k*2*pi/nphi).  Rows 0 and ntheta-1
+ *     are the poles; the library reads a pole's value from its k = 0 entry
+ *     and always writes the whole pole row with one value.
+ *   - Units are the paper's code units (Sec. 3.3): R_sun = 6.96e8 m,
+ *     time in hours, Br in Gauss.
+ *   - Pointers flagged on_device = 1 are CUDA device pointers of the current
+ *     device; on_device = 0 means host memory.  The library copies caller
+ *     arrays and never retains a caller pointer.
+ *   - The handle owns all device memory it uses (cudaMalloc at
+ *     sft_create_grid, cudaFree at sft_destroy); no call allocates after
+ *     sft_create_grid except the graph/coefficient caches of sft_step.
+ *   - Work is queued on the handle's CUDA stream.  sft_get_state (host
+ *     destination), sft_flux_diagnostics, sft_get_stats and sft_step with
+ *     profiling on synchronise that stream; the other calls are asynchronous.
+ *   - Errors are returned as sft_status codes (never abort or trap);
+ *     sft_last_error() gives a one-line description.  A device-side status
+ *     word (non-finite values seen by the watchdog) is checked at each
+ *     synchronising call and turns into SFT_ERR_UNSTABLE.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef SFT_H_
+#define SFT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFT_ABI_VERSION 1
+
+typedef struct sft_grid* sft_handle;
+
+typedef enum {
+  SFT_OK = 0,
+  SFT_ERR_ARG = 1,      /* invalid argument; the handle is unchanged */
+  SFT_ERR_OOM = 2,      /* cudaMalloc failed, or the HBM budget cannot hold one realization */
+  SFT_ERR_CUDA = 3,     /* a CUDA runtime call failed (text in sft_last_error) */
+  SFT_ERR_UNSTABLE = 4, /* non-finite values seen by the watchdog */
+  SFT_ERR_TIMEOUT = 5,  /* reserved for bounded device waits */
+  SFT_ERR_STATE = 6     /* calls out of order (e.g. sft_step before sft_set_flows) */
+} sft_status;
+
+typedef enum { SFT_FP32 = 0, SFT_FP64 = 1 } sft_prec;
+
+/* advection spatial scheme (Sec. 3.6.1, App. B) */
+enum { SFT_ADV_WENO3_CSH = 0, SFT_ADV_UPWIND = 1 };
+/* advection time scheme (Sec. 3.6.2) */
+enum { SFT_TIME_SSPRK43 = 0, SFT_TIME_SSPRK33 = 1, SFT_TIME_FE = 2 };
+/* diffusion time scheme (Sec. 3.7.2) */
+enum { SFT_DIFF_RKL2 = 0, SFT_DIFF_OFF = 1 };
+
+typedef struct {
+  int32_t ntheta; /* >= 5, poles included */
+  int32_t nphi;   /* >= 8, unique longitudes */
+} sft_shape;
+
+/* Per-realization model and method parameters (Sec. 2.1, 2.2, 2.5, 3.6, 3.7). */
+typedef struct {
+  double d0, d2, d4;  /* Eq. (dr): v_phi = (d0 + d2 cos^2 + d4 cos^4) sin(theta), m/s */
+  double m1, m3, m5;  /* Eq. (mf): v_theta = -(m1 cos + m3 cos^3 + m5 cos^5) sin(theta), m/s */
+  double nu;          /* diffusivity, km^2/s (constant per realization), >= 0 */
+  double alpha_uw;    /* upwind factor of the UW/CD flux (Sec. 3.6.1); 1 = upwind */
+  double cfl_safety;  /* safety factor on the flow CFL limit (Sec. 3.6.2), e.g. 0.9 */
+  double eps_w;       /* WENO epsilon: <= 0 selects eps_w = h (WENO3-CS(h)), > 0 a constant */
+  int32_t adv_space;  /* SFT_ADV_*  (may differ between realizations) */
+  int32_t adv_time;   /* SFT_TIME_* (must be the same for all realizations) */
+  int32_t diffusion;  /* SFT_DIFF_* (must be the same for all realizations) */
+  int32_t advection;  /* 1 = advection on, 0 = off (then dt is limited only by the target) */
+} sft_flow_params;
+
+/* Assimilation weight and balance options (Sec. 2.3). */
+typedef struct {
+  double alpha_mu;    /* exponent of mu in Eq. (data_assim_f) */
+  double mu_lim;      /* F = 0 unless mu > mu_lim */
+  double lat_lim_deg; /* F = 0 unless |latitude| < lat_lim_deg */
+  int32_t flux_balance; /* 1: balance Delta B by Eq. (fluxbal) before adding it */
+  int32_t reserved;
+} sft_assim_params;
+
+/* Analysis quantities of one realization (Sec. 2.6), all accumulated in FP64. */
+typedef struct {
+  double flux_signed, flux_pos, flux_neg; /* Mx */
+  double flux_pole_n, flux_pole_s;        /* Mx, |latitude| >= lat_cut */
+  double area_pole_n, area_pole_s;        /* cm^2 */
+  double brmin, brmax, absmin;            /* G */
+  double dipole_axial, h1, h2;            /* G: D and h1, h2 of Eq. (eqdipole1) */
+  double t_hours;                         /* the realization's simulated time */
+  int64_t steps;                          /* time steps taken by the realization */
+  int64_t nonfinite;                      /* number of non-finite map entries */
+} sft_diag;
+
+/* Work counters since creation or the last sft_reset_stats. */
+typedef struct {
+  int64_t global_steps;      /* iterations of the sft_step loop */
+  int64_t realization_steps; /* sum over realizations of time steps taken */
+  double cell_updates;       /* sum over realizations of ntheta*nphi*steps */
+  double adv_cell_stages;    /* ntheta*nphi x advection stages executed */
+  double diff_cell_stages;   /* ntheta*nphi x RKL2 stages executed */
+  int64_t kernel_launches;   /* library kernels launched (graph nodes included) */
+  int64_t graph_launches;    /* CUDA graph launches */
+  double diff_ms;            /* with profiling on: device time of the RKL2 stage kernels */
+  double adv_ms;             /* with profiling on: device time of the advection stage kernels */
+  int64_t diff_launches;     /* with profiling on: RKL2 stage kernels timed */
+  int64_t adv_launches;      /* with profiling on: advection stage kernels timed */
+  double diff_bytes;         /* algorithmic HBM bytes of the timed RKL2 stage kernels */
+  double adv_bytes;          /* algorithmic HBM bytes of the timed advection stage kernels */
+} sft_stats;
+
+/*
+ * Create a batch of n_real realizations; shapes[r] is realization r's grid
+ * (shapes may differ: an uneven batch).  prec is the state precision.
+ * hbm_budget_bytes bounds the device memory of the handle (0 = no bound):
+ * the state of every realization stays resident and the time-stepping work
+ * buffers are sized for the largest group of realizations ("wave") that fits
+ * the rest of the budget; sft_step then advances the waves one after another.
+ * SFT_ERR_OOM if the budget cannot hold the state plus one realization's
+ * work buffers.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  Maps start at zero and simulated times at 0 h.
+ */
+sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec prec,
+                           size_t hbm_budget_bytes, void* cuda_stream, sft_handle* out);
+
+/* Release every device resource of the handle.  NULL is accepted. */
+sft_status sft_destroy(sft_handle h);
+
+/* Copy realization r's map in (caller layout [ntheta][nphi]).  Pole rows are
+ * taken from their k = 0 entries. */
+sft_status sft_set_state(sft_handle h, int32_t r, const void* br, int32_t on_device);
+
+/* Copy realization r's map out (caller layout [ntheta][nphi]). */
+sft_status sft_get_state(sft_handle h, int32_t r, void* br, int32_t on_device);
+
+/* Set the simulated time of every realization (hours). */
+sft_status sft_set_time(sft_handle h, double t_hours);
+
+/* Per-realization simulated times (host array of n_real doubles). */
+sft_status sft_get_time(sft_handle h, double* t_hours);
+
+/* Set every realization's parameters (host array of n_real structs).
+ * Builds the per-realization flow tables (Eq. dr, mf), the flow CFL limit
+ * (Eq. ssprk43_dt / advection_timestep times cfl_safety) and the explicit
+ * diffusion limit (Gershgorin bound of the Eq. diffusion_matrix operator). */
+sft_status sft_set_flows(sft_handle h, const sft_flow_params* params);
+
+/*
+ * Advance every realization to t_target_hours (Sec. 3.4, 3.5): each time
+ * step is dt_r = min(t_target - t_r, CFL limit of r); advection then RKL2
+ * diffusion with s_r = min{s >= 2 : dt_r <= dt_E,r (s^2+s-2)/4} stages.
+ * All realizations step in lockstep (one batched launch per stage); a
+ * realization that has reached the target idles.  max_steps > 0 stops after
+ * that many loop iterations.  *steps_taken (may be NULL) receives the number
+ * of loop iterations.
+ */
+sft_status sft_step(sft_handle h, double t_target_hours, int32_t max_steps, int32_t* steps_taken);
+
+/*
+ * Assimilate observations (Sec. 2.3).  br_obs and mu are maps in the
+ * handle's precision: one map per realization (obs_per_realization = 1,
+ * concatenated in realization order) or one map shared by every
+ * realization (obs_per_realization = 0; all realizations must then have the
+ * same shape).  F = mu^alpha_mu where mu > mu_lim and |lat| < lat_lim, else
+ * 0 (Eq. data_assim_f); Delta B = F (B_obs - B) (Eq. data_assim_deltab),
+ * balanced by Eq. (fluxbal) when requested (skipped for a realization whose
+ * Delta B has no positive or no negative part); then B += Delta B.
+ * params: host array of n_real structs.
+ */
+sft_status sft_assimilate(sft_handle h, const void* br_obs, const void* mu,
+                          int32_t obs_per_realization, int32_t on_device,
+                          const sft_assim_params* params);
+
+/* Multiplicatively flux-balance every realization's map (the input-map
+ * option of Sec. 5.1): B > 0 divided by sqrt(r), B <= 0 multiplied by
+ * sqrt(r), r = |Phi+ / Phi-| (Eq. fluxbal applied to B). */
+sft_status sft_balance_flux(sft_handle h);
+
+/* Analysis quantities of Sec. 2.6 for every realization (host array of
+ * n_real structs), accumulated in FP64.  lat_cut_deg bounds the polar
+ * regions.  Synchronises. */
+sft_status sft_flux_diagnostics(sft_handle h, double lat_cut_deg, sft_diag* out);
+
+/* Work counters; synchronises so profiled times are complete. */
+sft_status sft_get_stats(sft_handle h, sft_stats* out);
+sft_status sft_reset_stats(sft_handle h);
+
+/* profile != 0: sft_step records CUDA events around its advection and RKL2
+ * stage kernels on the handle's stream and accumulates their device time in
+ * sft_stats (each step then synchronises). */
+sft_status sft_set_profiling(sft_handle h, int32_t profile);
+
+/* use_graphs != 0 (default): sft_step replays one captured CUDA graph per
+ * distinct step configuration; 0: plain launches. */
+sft_status sft_set_graphs(sft_handle h, int32_t use_graphs);
+
+/* Tile rows per block of the stage kernels for realizations of shape index
+ * shape_id (order of first appearance in shapes[]); 0 lets the built-in
+ * autotuner choose on the first step.  Valid values: 1, 2, 4, 8. */
+sft_status sft_set_tile_rows(sft_handle h, int32_t shape_id, int32_t rows);
+
+/* The tile rows chosen for shape_id (after autotuning), or 0 if not yet. */
+int32_t sft_get_tile_rows(sft_handle h, int32_t shape_id);
+
+/* Number of realizations per wave for the handle's HBM budget. */
+int32_t sft_wave_size(sft_handle h);
+
+/* The flow CFL limit (hours) and RKL2 stage count for a step of dt hours of
+ * realization r, as sft_step would use them.  Host-only computation. */
+sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cfl, double* dt_euler,
+                         int32_t* stages);
+
+/* One-line description of the last error on h (or of the last failed
+ * sft_create_grid when h is NULL).  Valid until the next call on h. */
+const char* sft_last_error(sft_handle h);
+
+/* SFT_ABI_VERSION of the loaded library. */
+int32_t sft_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFT_H_ */

@@ -1,0 +1,1193 @@
+// sft_api.cu -- host side of libsft: the C-ABI of include/sft.h.
+//
+// The handle keeps every realization's map resident in one device pool and
+// three work arrays sized for one "wave" of realizations (the HBM-budget
+// admission unit).  sft_step runs the Lie-split step of Sec. 3.5 for all
+// realizations of a wave in lockstep: the advection stages then the RKL2
+// stages, each ONE batched launch over a tile table whose prefix holds the
+// realizations still active at that stage.  Each distinct step
+// configuration (per-realization dt and stage count) owns its device
+// parameter block and, by default, one captured CUDA graph that replays the
+// whole step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sft.h"
+#include "sft_device.cuh"
+
+using namespace sft;
+
+namespace {
+
+// Sec. 3.3: R_sun = 6.96e8 m, time unit 1 hour.
+constexpr double kRsunM = 6.96e8;
+constexpr double kRsunCm = 6.96e10;
+constexpr double kMsToRsHr = 3600.0 / kRsunM;
+constexpr double kKm2sToRs2Hr = 3600.0 * 1.0e6 / (kRsunM * kRsunM);
+constexpr double kPi = 3.14159265358979323846;
+
+thread_local std::string g_create_error;
+
+struct ShapeInfo {
+  int nt = 0, np = 0, pitch = 0;
+  int geo = 0;        // first row in the geometry tables
+  int col = 0;        // first entry in the cos/sin(phi) tables
+  int tile_rows = 0;  // 0 = autotune on first step
+  double dth = 0, dph = 0, cap = 0;
+  std::vector<double> sin_t, sin_h, cos_t;  // sin th_j, sin th_{f+1/2}, cos th_j
+};
+
+struct RealInfo {
+  int shape = 0;
+  int64_t off = 0, woff = 0, cells = 0;  // cells = nt*pitch elements
+  int wave = 0;
+  int flow_row = 0;
+  double t = 0.0;
+  int64_t steps = 0;
+  bool has_flows = false;
+  sft_flow_params fp{};
+  double nu = 0.0;        // R_sun^2/hr
+  double dt_cfl = 0.0;    // hours (inf when advection is off)
+  double dt_euler = 0.0;  // hours (inf when nu == 0)
+};
+
+struct Config {
+  std::vector<double> dt;        // per wave member (wave order)
+  std::vector<int> s;            // per wave member
+  std::vector<int> tr;           // tile rows per shape at build time
+  int smax = 0, n_adv_tiles = 0;
+  std::vector<int> stage_tiles;  // [j] = tiles launched at RKL2 stage j (1..smax)
+  Tile* d_tiles = nullptr;
+  StepParam* d_sp = nullptr;
+  void* d_coef = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;
+  double cells_adv = 0, cell_stages_diff = 0, cell_updates = 0, diff_words = 0;
+  int64_t launches = 0;
+  int realization_steps = 0;
+};
+
+struct Wave {
+  std::vector<int> reals;
+  std::vector<std::unique_ptr<Config>> configs;
+};
+
+template <typename T> struct Tables {
+  RowGeo<T>* geo = nullptr;
+  RowFlow<T>* flow = nullptr;
+};
+
+}  // namespace
+
+struct sft_grid {
+  int n_real = 0;
+  sft_prec prec = SFT_FP32;
+  size_t elem = 4;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<ShapeInfo> shapes;
+  std::vector<RealInfo> reals;
+  std::vector<Wave> waves;
+  int wave_size = 0;
+  int64_t state_elems = 0, work_elems = 0;
+  // device memory
+  void* state = nullptr;
+  void* work[3] = {nullptr, nullptr, nullptr};
+  RealDesc* d_desc = nullptr;
+  ShapeConst* d_shc = nullptr;
+  void* d_geo = nullptr;       // RowGeo<T>
+  RowGeoD* d_geod = nullptr;
+  double* d_cosp = nullptr;
+  double* d_sinp = nullptr;
+  void* d_flow = nullptr;      // RowFlow<T>
+  int* d_status = nullptr;
+  RedTile* d_rtiles = nullptr;
+  int* d_rstart = nullptr;
+  int n_rtiles = 0;
+  double* d_partials = nullptr;
+  double* d_red = nullptr;     // per realization fold output
+  double* h_red = nullptr;     // pinned mirror
+  double* d_wpar = nullptr;
+  std::vector<double> h_wpar_last;
+  int64_t* d_obs_off = nullptr;
+  std::vector<int64_t> h_obs_off_last;
+  void* d_obs = nullptr;
+  size_t obs_bytes = 0;
+  int geo_rows = 0, flow_rows = 0, col_entries = 0;
+  // step machinery
+  bool flows_set = false;
+  bool use_graphs = true;
+  bool profiling = false;
+  uint64_t use_counter = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  sft_stats stats{};
+};
+
+namespace {
+
+sft_status fail(sft_handle h, sft_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define SFT_CUDA(h, call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? SFT_ERR_OOM : SFT_ERR_CUDA,     \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---- Sec. 3.2 geometry, per shape (FP64 on the host) ----------------------
+void build_shape(ShapeInfo& s) {
+  s.dth = kPi / (s.nt - 1);
+  s.dph = 2.0 * kPi / s.np;
+  s.cap = 2.0 * kPi * (1.0 - std::cos(0.5 * s.dth));
+  s.sin_t.resize(s.nt);
+  s.cos_t.resize(s.nt);
+  s.sin_h.resize(s.nt - 1);
+  for (int j = 0; j < s.nt; ++j) {
+    const double th = j == s.nt - 1 ? kPi : j * s.dth;
+    s.sin_t[j] = (j == 0 || j == s.nt - 1) ? 0.0 : std::sin(th);
+    s.cos_t[j] = std::cos(th);
+  }
+  for (int f = 0; f < s.nt - 1; ++f) s.sin_h[f] = std::sin((f + 0.5) * s.dth);
+}
+
+template <typename T>
+void geo_rows(const ShapeInfo& s, std::vector<RowGeo<T>>& g, std::vector<RowGeoD>& gd) {
+  for (int j = 0; j < s.nt; ++j) {
+    RowGeo<T> r{};
+    RowGeoD d{};
+    const bool pole = j == 0 || j == s.nt - 1;
+    d.cos_t = s.cos_t[j];
+    d.sin_t = s.sin_t[j];
+    d.lat = 0.5 * kPi - (j == s.nt - 1 ? kPi : j * s.dth);
+    if (pole) {
+      d.area = s.cap / s.np;
+    } else {
+      const double st = s.sin_t[j];
+      const double sdn = s.sin_h[j - 1], sup = s.sin_h[j];
+      r.cN = T(sdn / (s.dth * s.dth * st));
+      r.cS = T(sup / (s.dth * s.dth * st));
+      r.cE = T(1.0 / (s.dph * s.dph * st * st));
+      r.inv_sdth = T(1.0 / (st * s.dth));
+      r.inv_sdph = T(1.0 / (st * s.dph));
+      r.sdn = T(sdn);
+      r.sup = T(sup);
+      d.area = st * s.dth * s.dph;
+    }
+    g.push_back(r);
+    gd.push_back(d);
+  }
+}
+
+// ---- Sec. 2.1.1 flows and Sec. 3.6.2 / 3.7.2 limits -----------------------
+struct FlowRows {
+  std::vector<double> vt;  // faces f = 0..nt-2
+  std::vector<double> vp;  // rows
+};
+
+FlowRows flow_profiles(const ShapeInfo& s, const sft_flow_params& p) {
+  FlowRows f;
+  f.vp.resize(s.nt);
+  f.vt.resize(s.nt - 1);
+  for (int j = 0; j < s.nt; ++j) {
+    const double c = s.cos_t[j], c2 = c * c;
+    f.vp[j] = (p.d0 + p.d2 * c2 + p.d4 * c2 * c2) * s.sin_t[j] * kMsToRsHr;
+  }
+  for (int i = 0; i < s.nt - 1; ++i) {
+    const double c = std::cos((i + 0.5) * s.dth), c2 = c * c;
+    f.vt[i] = -(p.m1 * c + p.m3 * c * c2 + p.m5 * c * c2 * c2) * s.sin_h[i] * kMsToRsHr;
+  }
+  return f;
+}
+
+// Eq. (ssprk43_dt) (or Eq. advection_timestep for FE / SSPRK(3,3)) with the
+// flanking-maximum velocities, times the safety factor.
+double cfl_limit(const ShapeInfo& s, const FlowRows& f, const sft_flow_params& p) {
+  double rmax = 0.0;
+  for (int j = 1; j < s.nt - 1; ++j) {
+    const double vth = std::max(std::fabs(f.vt[j - 1]), std::fabs(f.vt[j]));
+    const double r = vth / s.dth + std::fabs(f.vp[j]) / (s.sin_t[j] * s.dph);
+    rmax = std::max(rmax, r);
+  }
+  if (rmax <= 0.0) return INFINITY;
+  double lim = 1.0 / rmax;
+  if (p.adv_time != SFT_TIME_SSPRK43) lim *= 0.5;
+  return p.cfl_safety * lim;
+}
+
+// Explicit-Euler diffusion limit 1 / max_i |a_ii| (Gershgorin) of the
+// Eq. (diffusion_matrix) operator with the App. A cap rows.
+double euler_limit(const ShapeInfo& s, double nu) {
+  if (nu <= 0.0) return INFINITY;
+  double amax = 0.0;
+  for (int j = 1; j < s.nt - 1; ++j) {
+    const double st = s.sin_t[j];
+    const double a = nu * ((s.sin_h[j - 1] + s.sin_h[j]) / (s.dth * s.dth * st) +
+                           2.0 / (s.dph * s.dph * st * st));
+    amax = std::max(amax, a);
+  }
+  const double pole = nu * std::sin(0.5 * s.dth) * s.dph * s.np / (s.dth * s.cap);
+  amax = std::max(amax, pole);
+  return 1.0 / amax;
+}
+
+// RKL2 stage count: smallest s >= 2 with dt <= dt_E (s^2 + s - 2) / 4.
+int rkl2_stages(double dt, double dte) {
+  if (!(dt > 0.0)) return 0;
+  if (!std::isfinite(dte)) return 0;
+  int s = (int)std::ceil(0.5 * (-1.0 + std::sqrt(9.0 + 16.0 * dt / dte)));
+  if (s < 2) s = 2;
+  while ((double)(s * (int64_t)s + s - 2) * dte < 4.0 * dt) ++s;
+  while (s > 2 && (double)((s - 1) * (int64_t)(s - 1) + (s - 1) - 2) * dte >= 4.0 * dt) --s;
+  return s;
+}
+
+// RKL2 coefficients (Meyer, Balsara & Aslam 2014) for stages 0..s, stored in
+// the increment form used by rkl2_stage_kernel: {mu_j, nu_j, mu~_j, mu~_j + gamma~_j}.
+template <typename T>
+void rkl2_coefs(int s, std::vector<Coef<T>>& out) {
+  const double w1 = 4.0 / ((double)s * s + s - 2.0);
+  auto b = [](int j) { return j <= 2 ? 1.0 / 3.0 : ((double)j * j + j - 2.0) / (2.0 * j * (j + 1.0)); };
+  out.push_back(Coef<T>{T(0), T(0), T(0), T(0)});  // stage 0 unused
+  out.push_back(Coef<T>{T(0), T(0), T(b(1) * w1), T(0)});
+  for (int j = 2; j <= s; ++j) {
+    const double mu = (2.0 * j - 1.0) / j * b(j) / b(j - 1);
+    const double nu = -(j - 1.0) / j * b(j) / b(j - 2);
+    const double mut = mu * w1;
+    const double gt = -(1.0 - b(j - 1)) * mut;
+    out.push_back(Coef<T>{T(mu), T(nu), T(mut), T(mut + gt)});
+  }
+}
+
+template <typename T> T* ptr(void* p) { return static_cast<T*>(p); }
+
+void free_config(Config& c) {
+  if (c.exec) cudaGraphExecDestroy(c.exec);
+  cudaFree(c.d_tiles);
+  cudaFree(c.d_sp);
+  cudaFree(c.d_coef);
+  c.exec = nullptr;
+  c.d_tiles = nullptr;
+  c.d_sp = nullptr;
+  c.d_coef = nullptr;
+}
+
+void free_handle(sft_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& w : h->waves)
+    for (auto& c : w.configs) free_config(*c);
+  cudaFree(h->state);
+  for (auto& w : h->work) cudaFree(w);
+  cudaFree(h->d_desc);
+  cudaFree(h->d_shc);
+  cudaFree(h->d_geo);
+  cudaFree(h->d_geod);
+  cudaFree(h->d_cosp);
+  cudaFree(h->d_sinp);
+  cudaFree(h->d_flow);
+  cudaFree(h->d_status);
+  cudaFree(h->d_rtiles);
+  cudaFree(h->d_rstart);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_red);
+  if (h->h_red) cudaFreeHost(h->h_red);
+  cudaFree(h->d_wpar);
+  cudaFree(h->d_obs_off);
+  cudaFree(h->d_obs);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+sft_status check_status_word(sft_handle h) {
+  int st = 0;
+  SFT_CUDA(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    SFT_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int)));
+    return fail(h, SFT_ERR_UNSTABLE, "non-finite values in the state (watchdog)");
+  }
+  return SFT_OK;
+}
+
+sft_status sync(sft_handle h) {
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+  return check_status_word(h);
+}
+
+// ---------------------------------------------------------------------------
+// step configurations
+// ---------------------------------------------------------------------------
+int vec_width(const sft_grid* h) { return h->prec == SFT_FP32 ? 4 : 2; }
+
+void append_tiles(const sft_grid* h, int r, int tr, std::vector<Tile>& tiles) {
+  const RealInfo& ri = h->reals[r];
+  const ShapeInfo& s = h->shapes[ri.shape];
+  const int tx = kThreads / tr;
+  int lx = 0;
+  while ((1 << lx) < tx) ++lx;
+  const int tc = tx * vec_width(h);
+  for (int j0 = 1; j0 <= s.nt - 2; j0 += tr)
+    for (int k0 = 0; k0 < s.np; k0 += tc) tiles.push_back(Tile{r, j0, k0, lx << 8});
+  tiles.push_back(Tile{r, 0, 0, 1});
+  tiles.push_back(Tile{r, 0, 0, 2});
+}
+
+template <typename T>
+sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
+                        const std::vector<int>& s, Config** out) {
+  auto c = std::make_unique<Config>();
+  c->dt = dt;
+  c->s = s;
+  for (auto& sh : h->shapes) c->tr.push_back(sh.tile_rows);
+  const int nw = (int)w.reals.size();
+  // active members (dt > 0) sorted by stage count, descending
+  std::vector<int> order;
+  for (int i = 0; i < nw; ++i)
+    if (dt[i] > 0.0) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s[a] > s[b]; });
+  std::vector<Tile> tiles;
+  std::vector<int> tile_end;
+  std::vector<StepParam> sp(h->n_real);
+  std::memset(sp.data(), 0, sp.size() * sizeof(StepParam));
+  std::vector<Coef<T>> coefs;
+  for (int i : order) {
+    const int r = w.reals[i];
+    const RealInfo& ri = h->reals[r];
+    const ShapeInfo& sh = h->shapes[ri.shape];
+    append_tiles(h, r, std::max(1, sh.tile_rows), tiles);
+    tile_end.push_back((int)tiles.size());
+    StepParam& p = sp[r];
+    p.dt = dt[i];
+    p.nudt = ri.nu * dt[i];
+    p.eps_t = ri.fp.eps_w > 0.0 ? ri.fp.eps_w : sh.dth;
+    p.eps_p = ri.fp.eps_w > 0.0 ? ri.fp.eps_w : sh.dph;
+    p.alpha_uw = ri.fp.alpha_uw;
+    p.s = s[i];
+    p.weno = ri.fp.adv_space == SFT_ADV_WENO3_CSH ? 1 : 0;
+    p.adv = ri.fp.advection ? 1 : 0;
+    p.coef = (int)coefs.size();
+    if (s[i] > 0) rkl2_coefs<T>(s[i], coefs);
+    else coefs.push_back(Coef<T>{});
+    const double cells = (double)sh.nt * sh.np;
+    if (ri.fp.advection) c->cells_adv += cells;
+    c->cell_stages_diff += cells * s[i];
+    if (s[i] > 0) c->diff_words += cells * (4.0 * s[i] - 1.0);
+    c->cell_updates += cells;
+    c->smax = std::max(c->smax, s[i]);
+  }
+  c->realization_steps = (int)order.size();
+  c->n_adv_tiles = tile_end.empty() ? 0 : tile_end.back();
+  c->stage_tiles.assign(c->smax + 1, 0);
+  for (int j = 1; j <= c->smax; ++j) {
+    int n = 0;
+    while (n < (int)order.size() && s[order[n]] >= j) ++n;
+    c->stage_tiles[j] = n == 0 ? 0 : tile_end[n - 1];
+  }
+  if (!tiles.empty()) {
+    SFT_CUDA(h, cudaMalloc(&c->d_tiles, tiles.size() * sizeof(Tile)));
+    SFT_CUDA(h, cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(Tile),
+                                cudaMemcpyHostToDevice, h->stream));
+  }
+  SFT_CUDA(h, cudaMalloc(&c->d_sp, sp.size() * sizeof(StepParam)));
+  SFT_CUDA(h, cudaMemcpyAsync(c->d_sp, sp.data(), sp.size() * sizeof(StepParam),
+                              cudaMemcpyHostToDevice, h->stream));
+  if (coefs.empty()) coefs.push_back(Coef<T>{});
+  SFT_CUDA(h, cudaMalloc(&c->d_coef, coefs.size() * sizeof(Coef<T>)));
+  SFT_CUDA(h, cudaMemcpyAsync(c->d_coef, coefs.data(), coefs.size() * sizeof(Coef<T>),
+                              cudaMemcpyHostToDevice, h->stream));
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors die at return
+  // keep at most 8 configurations per wave
+  if (w.configs.size() >= 8) {
+    auto it = std::min_element(w.configs.begin(), w.configs.end(),
+                               [](const std::unique_ptr<Config>& a, const std::unique_ptr<Config>& b) {
+                                 return a->last_use < b->last_use;
+                               });
+    free_config(**it);
+    w.configs.erase(it);
+  }
+  *out = c.get();
+  w.configs.push_back(std::move(c));
+  return SFT_OK;
+}
+
+// The launches of one step (advection stages, then RKL2 stages).
+template <typename T>
+sft_status enqueue_step(sft_handle h, Config& c, bool record_events) {
+  const cudaStream_t st = h->stream;
+  T* B = ptr<T>(h->state);
+  T* W0 = ptr<T>(h->work[0]);
+  T* W1 = ptr<T>(h->work[1]);
+  T* W2 = ptr<T>(h->work[2]);
+  const auto* geo = ptr<const RowGeo<T>>(h->d_geo);
+  const auto* flow = ptr<const RowFlow<T>>(h->d_flow);
+  int adv_time = SFT_TIME_SSPRK43;
+  for (const auto& ri : h->reals) {
+    adv_time = ri.fp.adv_time;
+    break;
+  }
+  if (record_events) SFT_CUDA(h, cudaEventRecord(h->ev[0], st));
+  if (c.n_adv_tiles > 0) {
+    std::vector<AdvStage<T>> stages;
+    auto S = [&](const T* fin, int finw, const T* fn, int fnw, T* out, int outw, double a, double b,
+                 double cc) {
+      stages.push_back(AdvStage<T>{fin, fn, out, finw, fnw, outw, T(a), T(b), T(cc)});
+    };
+    if (adv_time == SFT_TIME_SSPRK43) {
+      S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 0.5);
+      S(W0, 1, nullptr, 0, W1, 1, 0.0, 1.0, 0.5);
+      S(W1, 1, B, 0, W0, 1, 2.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0);
+      S(W0, 1, nullptr, 0, B, 0, 0.0, 1.0, 0.5);
+    } else if (adv_time == SFT_TIME_SSPRK33) {
+      S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 1.0);
+      S(W0, 1, B, 0, W1, 1, 0.75, 0.25, 0.25);
+      S(W1, 1, B, 0, B, 0, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0);
+    } else {
+      S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 1.0);
+      S(W0, 1, nullptr, 0, B, 0, 0.0, 1.0, 0.0);  // copy back
+    }
+    for (auto& s : stages) {
+      SFT_CUDA(h, launch_adv_stage<T>(c.n_adv_tiles, st, c.d_tiles, h->d_desc, c.d_sp, geo, flow,
+                                      h->d_shc, B, W0, W1, s));
+    }
+  }
+  if (record_events) {
+    SFT_CUDA(h, cudaEventRecord(h->ev[1], st));
+    SFT_CUDA(h, cudaEventRecord(h->ev[2], st));
+  }
+  for (int j = 1; j <= c.smax; ++j) {
+    SFT_CUDA(h, launch_rkl2_stage<T>(c.stage_tiles[j], st, c.d_tiles, h->d_desc, c.d_sp, geo,
+                                     h->d_shc, ptr<const Coef<T>>(c.d_coef), B, W0, W1, W2, j, 1,
+                                     h->d_status));
+  }
+  if (record_events) SFT_CUDA(h, cudaEventRecord(h->ev[3], st));
+  return SFT_OK;
+}
+
+int adv_stage_count(sft_handle h) {
+  if (h->reals.empty()) return 0;
+  switch (h->reals[0].fp.adv_time) {
+    case SFT_TIME_SSPRK43: return 4;
+    case SFT_TIME_SSPRK33: return 3;
+    default: return 2;
+  }
+}
+
+template <typename T>
+sft_status autotune(sft_handle h, Wave& w);
+
+template <typename T>
+sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
+  const int nw = (int)w.reals.size();
+  std::vector<double> dt(nw, 0.0);
+  std::vector<int> s(nw, 0);
+  *any = false;
+  for (int i = 0; i < nw; ++i) {
+    const RealInfo& ri = h->reals[w.reals[i]];
+    const double rem = t_target - ri.t;
+    if (!(rem > 0.0)) continue;
+    // Sec. 3.4: the remaining time, cut to the flow limit
+    dt[i] = rem <= ri.dt_cfl ? rem : ri.dt_cfl;
+    s[i] = ri.fp.diffusion == SFT_DIFF_RKL2 ? rkl2_stages(dt[i], ri.dt_euler) : 0;
+    *any = true;
+  }
+  if (!*any) return SFT_OK;
+  for (int r : w.reals)
+    if (h->shapes[h->reals[r].shape].tile_rows == 0) {
+      sft_status st = autotune<T>(h, w);
+      if (st != SFT_OK) return st;
+      break;
+    }
+  Config* c = nullptr;
+  for (auto& cfg : w.configs) {
+    bool same = cfg->dt == dt && cfg->s == s;
+    for (size_t i = 0; same && i < h->shapes.size(); ++i) same = cfg->tr[i] == h->shapes[i].tile_rows;
+    if (same) {
+      c = cfg.get();
+      break;
+    }
+  }
+  if (!c) {
+    sft_status st = build_config<T>(h, w, dt, s, &c);
+    if (st != SFT_OK) return st;
+  }
+  c->last_use = ++h->use_counter;
+  const bool ev = h->profiling;
+  if (h->use_graphs) {
+    if (!c->exec) {
+      cudaGraph_t g = nullptr;
+      SFT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      sft_status st = enqueue_step<T>(h, *c, true);
+      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      if (st != SFT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(h, SFT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&c->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(h, SFT_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    SFT_CUDA(h, cudaGraphLaunch(c->exec, h->stream));
+    h->stats.graph_launches += 1;
+  } else {
+    sft_status st = enqueue_step<T>(h, *c, ev);
+    if (st != SFT_OK) return st;
+  }
+  const int n_adv = c->n_adv_tiles > 0 ? adv_stage_count(h) : 0;
+  h->stats.kernel_launches += n_adv + c->smax;
+  h->stats.realization_steps += c->realization_steps;
+  h->stats.cell_updates += c->cell_updates;
+  h->stats.adv_cell_stages += c->cells_adv * (adv_stage_count(h) == 2 ? 1 : adv_stage_count(h));
+  (void)0;
+  h->stats.diff_cell_stages += c->cell_stages_diff;
+  if (ev) {
+    SFT_CUDA(h, cudaEventSynchronize(h->ev[3]));
+    float a = 0.f, d = 0.f;
+    SFT_CUDA(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+    SFT_CUDA(h, cudaEventElapsedTime(&d, h->ev[2], h->ev[3]));
+    h->stats.adv_ms += a;
+    h->stats.diff_ms += d;
+    h->stats.adv_launches += n_adv;
+    h->stats.diff_launches += c->smax;
+    const double eb = (double)h->elem;
+    // Algorithmic bytes.  RKL2: stage 1 reads B, writes G and delta_1 (3
+    // words); stage 2 reads delta_1, G, writes delta_2 (3); middle stages
+    // read delta_{j-1}, delta_{j-2}, G and write delta_j (4); the last reads
+    // delta_{s-1}, delta_{s-2}, G, B and writes B (5): 4s - 1 words per cell.
+    // SSPRK(4,3): 2 + 2 + 3 + 2 = 9 words; SSPRK(3,3): 2 + 3 + 3 = 8; FE + copy: 4.
+    h->stats.diff_bytes += eb * c->diff_words;
+    const int na = adv_stage_count(h);
+    h->stats.adv_bytes += (na == 4 ? 9.0 : (na == 3 ? 8.0 : 4.0)) * eb * c->cells_adv;
+  }
+  for (int i = 0; i < nw; ++i) {
+    if (!(dt[i] > 0.0)) continue;
+    RealInfo& ri = h->reals[w.reals[i]];
+    const double rem = t_target - ri.t;
+    ri.t = dt[i] == rem ? t_target : ri.t + dt[i];
+    ri.steps += 1;
+  }
+  return SFT_OK;
+}
+
+// Pick the tile height of the stage kernels per shape by timing RKL2 stage 2
+// (a non-final stage: it writes only work arrays) for each candidate.
+template <typename T>
+sft_status autotune(sft_handle h, Wave& w) {
+  for (size_t si = 0; si < h->shapes.size(); ++si) {
+    ShapeInfo& sh = h->shapes[si];
+    if (sh.tile_rows != 0) continue;
+    std::vector<int> members;
+    for (int r : w.reals)
+      if (h->reals[r].shape == (int)si && members.size() < 8) members.push_back(r);
+    if (members.empty()) continue;
+    std::vector<StepParam> sp(h->n_real);
+    std::memset(sp.data(), 0, sp.size() * sizeof(StepParam));
+    for (int r : members) {
+      sp[r].dt = 1.0;
+      sp[r].nudt = 1e-6;
+      sp[r].s = 3;
+      sp[r].coef = 0;
+    }
+    std::vector<Coef<T>> coefs;
+    rkl2_coefs<T>(3, coefs);
+    StepParam* d_sp = nullptr;
+    Coef<T>* d_coef = nullptr;
+    Tile* d_tiles = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int best = 1;
+    float best_ms = 1e30f;
+    cudaError_t err = cudaSuccess;
+    err = cudaMalloc(&d_sp, sp.size() * sizeof(StepParam));
+    if (err == cudaSuccess) err = cudaMalloc(&d_coef, coefs.size() * sizeof(Coef<T>));
+    if (err == cudaSuccess) err = cudaMemcpy(d_sp, sp.data(), sp.size() * sizeof(StepParam), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(d_coef, coefs.data(), coefs.size() * sizeof(Coef<T>), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    const int cand[4] = {1, 2, 4, 8};
+    for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci) {
+      const int tr = cand[ci];
+      std::vector<Tile> tiles;
+      for (int r : members) append_tiles(h, r, tr, tiles);
+      cudaFree(d_tiles);
+      d_tiles = nullptr;
+      err = cudaMalloc(&d_tiles, tiles.size() * sizeof(Tile));
+      if (err != cudaSuccess) break;
+      err = cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+      if (err != cudaSuccess) break;
+      const int nt = (int)tiles.size();
+      const auto* geo = ptr<const RowGeo<T>>(h->d_geo);
+      T* B = ptr<T>(h->state);
+      T* W0 = ptr<T>(h->work[0]);
+      T* W1 = ptr<T>(h->work[1]);
+      T* W2 = ptr<T>(h->work[2]);
+      err = launch_rkl2_stage<T>(nt, h->stream, d_tiles, h->d_desc, d_sp, geo, h->d_shc, d_coef, B,
+                                 W0, W1, W2, 1, 0, h->d_status);
+      for (int it = 0; it < 2 && err == cudaSuccess; ++it)
+        err = launch_rkl2_stage<T>(nt, h->stream, d_tiles, h->d_desc, d_sp, geo, h->d_shc, d_coef,
+                                   B, W0, W1, W2, 2, 0, h->d_status);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+      const int reps = 6;
+      for (int it = 0; it < reps && err == cudaSuccess; ++it)
+        err = launch_rkl2_stage<T>(nt, h->stream, d_tiles, h->d_desc, d_sp, geo, h->d_shc, d_coef,
+                                   B, W0, W1, W2, 2, 0, h->d_status);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = tr;
+      }
+    }
+    cudaFree(d_tiles);
+    cudaFree(d_sp);
+    cudaFree(d_coef);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return fail(h, SFT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));
+    sh.tile_rows = best;
+  }
+  return SFT_OK;
+}
+
+template <typename T>
+sft_status upload_tables(sft_handle h) {
+  std::vector<RowGeo<T>> g;
+  std::vector<RowGeoD> gd;
+  std::vector<ShapeConst> sc;
+  std::vector<double> cp, sp;
+  for (auto& s : h->shapes) {
+    s.geo = (int)g.size();
+    geo_rows<T>(s, g, gd);
+    s.col = (int)cp.size();
+    for (int k = 0; k < s.np; ++k) {
+      cp.push_back(std::cos(k * s.dph));
+      sp.push_back(std::sin(k * s.dph));
+    }
+    const double line = std::sin(0.5 * s.dth) * s.dph;
+    sc.push_back(ShapeConst{line / (s.dth * s.cap), line / s.cap, s.dth, s.dph});
+  }
+  h->geo_rows = (int)g.size();
+  SFT_CUDA(h, cudaMalloc(&h->d_geo, g.size() * sizeof(RowGeo<T>)));
+  SFT_CUDA(h, cudaMemcpy(h->d_geo, g.data(), g.size() * sizeof(RowGeo<T>), cudaMemcpyHostToDevice));
+  SFT_CUDA(h, cudaMalloc(&h->d_geod, gd.size() * sizeof(RowGeoD)));
+  SFT_CUDA(h, cudaMemcpy(h->d_geod, gd.data(), gd.size() * sizeof(RowGeoD), cudaMemcpyHostToDevice));
+  SFT_CUDA(h, cudaMalloc(&h->d_cosp, cp.size() * sizeof(double)));
+  SFT_CUDA(h, cudaMemcpy(h->d_cosp, cp.data(), cp.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SFT_CUDA(h, cudaMalloc(&h->d_sinp, sp.size() * sizeof(double)));
+  SFT_CUDA(h, cudaMemcpy(h->d_sinp, sp.data(), sp.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SFT_CUDA(h, cudaMalloc(&h->d_shc, sc.size() * sizeof(ShapeConst)));
+  SFT_CUDA(h, cudaMemcpy(h->d_shc, sc.data(), sc.size() * sizeof(ShapeConst), cudaMemcpyHostToDevice));
+  // flow tables: one block of nt rows per realization (filled by sft_set_flows)
+  int rows = 0;
+  for (auto& r : h->reals) {
+    r.flow_row = rows;
+    rows += h->shapes[r.shape].nt;
+  }
+  h->flow_rows = rows;
+  SFT_CUDA(h, cudaMalloc(&h->d_flow, (size_t)rows * sizeof(RowFlow<T>)));
+  SFT_CUDA(h, cudaMemset(h->d_flow, 0, (size_t)rows * sizeof(RowFlow<T>)));
+  return SFT_OK;
+}
+
+template <typename T>
+sft_status set_flows_t(sft_handle h, const sft_flow_params* params) {
+  std::vector<RowFlow<T>> rows(h->flow_rows);
+  for (int r = 0; r < h->n_real; ++r) {
+    RealInfo& ri = h->reals[r];
+    const ShapeInfo& s = h->shapes[ri.shape];
+    const sft_flow_params& p = params[r];
+    const FlowRows f = flow_profiles(s, p);
+    for (int j = 0; j < s.nt; ++j) {
+      RowFlow<T> rf{};
+      if (j >= 1 && j <= s.nt - 2) {
+        rf.vdn = T(f.vt[j - 1]);
+        rf.vup = T(f.vt[j]);
+        double a = 0.0;
+        for (int fi = std::max(j - 3, 0); fi <= std::min(j + 2, s.nt - 2); ++fi)
+          a = std::max(a, std::fabs(f.vt[fi]));
+        rf.alpha = T(a);
+      }
+      rf.vp = T(f.vp[j]);
+      rows[ri.flow_row + j] = rf;
+    }
+    ri.fp = p;
+    ri.nu = p.nu * kKm2sToRs2Hr;
+    ri.dt_cfl = p.advection ? cfl_limit(s, f, p) : INFINITY;
+    ri.dt_euler = p.diffusion == SFT_DIFF_RKL2 ? euler_limit(s, ri.nu) : INFINITY;
+    ri.has_flows = true;
+  }
+  SFT_CUDA(h, cudaMemcpyAsync(h->d_flow, rows.data(), rows.size() * sizeof(RowFlow<T>),
+                              cudaMemcpyHostToDevice, h->stream));
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SFT_OK;
+}
+
+// reduction machinery
+template <typename T>
+sft_status reduce_fold(sft_handle h, int mode, double lat_cut, AssimArgs aa) {
+  SFT_CUDA(h, launch_reduce<T>(mode, h->n_rtiles, h->stream, h->d_rtiles, h->d_desc, h->d_geod,
+                               h->d_cosp, h->d_sinp, ptr<const T>(h->state), lat_cut, aa,
+                               h->d_partials));
+  SFT_CUDA(h, launch_fold(mode, h->n_real, h->stream, h->d_rstart, h->d_partials, aa.wpar, h->d_red));
+  return SFT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+int32_t sft_abi_version(void) { return SFT_ABI_VERSION; }
+
+const char* sft_last_error(sft_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec prec,
+                           size_t hbm_budget_bytes, void* cuda_stream, sft_handle* out) {
+  if (!out) return fail(nullptr, SFT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!shapes || n_real <= 0) return fail(nullptr, SFT_ERR_ARG, "need n_real > 0 shapes");
+  if (prec != SFT_FP32 && prec != SFT_FP64) return fail(nullptr, SFT_ERR_ARG, "bad precision");
+  for (int r = 0; r < n_real; ++r)
+    if (shapes[r].ntheta < 5 || shapes[r].nphi < 8 || shapes[r].ntheta > (1 << 20) ||
+        shapes[r].nphi > (1 << 20))
+      return fail(nullptr, SFT_ERR_ARG, "shape out of range (ntheta >= 5, nphi >= 8)");
+  sft_handle h = new sft_grid();
+  h->n_real = n_real;
+  h->prec = prec;
+  h->elem = prec == SFT_FP32 ? 4 : 8;
+  auto bail = [&](sft_status st) {
+    g_create_error = h->err;
+    free_handle(h);
+    return st;
+  };
+#define CREATE_CUDA(call)                                                                \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                       \
+      return bail(e_ == cudaErrorMemoryAllocation ? SFT_ERR_OOM : SFT_ERR_CUDA);         \
+    }                                                                                    \
+  } while (0)
+  CREATE_CUDA(cudaGetDevice(&h->device));
+  if (cuda_stream) {
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    CREATE_CUDA(cudaStreamCreate(&h->stream));  // blocking: ordered with the legacy stream
+    h->own_stream = true;
+  }
+  // shapes in order of first appearance
+  std::map<std::pair<int, int>, int> shape_id;
+  h->reals.resize(n_real);
+  for (int r = 0; r < n_real; ++r) {
+    auto key = std::make_pair(shapes[r].ntheta, shapes[r].nphi);
+    auto it = shape_id.find(key);
+    if (it == shape_id.end()) {
+      ShapeInfo s;
+      s.nt = key.first;
+      s.np = key.second;
+      s.pitch = (int)round_up(s.np, 32);
+      build_shape(s);
+      it = shape_id.emplace(key, (int)h->shapes.size()).first;
+      h->shapes.push_back(std::move(s));
+    }
+    RealInfo& ri = h->reals[r];
+    ri.shape = it->second;
+    const ShapeInfo& s = h->shapes[ri.shape];
+    ri.cells = (int64_t)s.nt * s.pitch;
+    ri.off = h->state_elems;
+    h->state_elems += ri.cells;
+  }
+  // HBM admission: the state stays resident; work arrays hold one wave.
+  const int64_t state_bytes = h->state_elems * (int64_t)h->elem;
+  int64_t avail = INT64_MAX;
+  if (hbm_budget_bytes > 0) {
+    const int64_t reserve = 64ll << 20;  // tables, tiles, reductions
+    avail = (int64_t)hbm_budget_bytes - state_bytes - reserve;
+  }
+  {
+    Wave cur;
+    int64_t used = 0;  // bytes per work array in the current wave
+    for (int r = 0; r < n_real; ++r) {
+      const int64_t per_array = h->reals[r].cells * (int64_t)h->elem;
+      if (3 * per_array > avail) {
+        h->err = "HBM budget too small for one realization's work buffers";
+        return bail(SFT_ERR_OOM);
+      }
+      if (3 * (used + per_array) > avail && !cur.reals.empty()) {
+        h->waves.push_back(std::move(cur));
+        cur = Wave();
+        used = 0;
+      }
+      h->reals[r].woff = used / (int64_t)h->elem;
+      h->reals[r].wave = (int)h->waves.size();
+      cur.reals.push_back(r);
+      used += per_array;
+      h->work_elems = std::max<int64_t>(h->work_elems, used / (int64_t)h->elem);
+    }
+    if (!cur.reals.empty()) h->waves.push_back(std::move(cur));
+    h->wave_size = 0;
+    for (auto& w : h->waves) h->wave_size = std::max<int>(h->wave_size, (int)w.reals.size());
+  }
+  CREATE_CUDA(cudaMalloc(&h->state, state_bytes));
+  CREATE_CUDA(cudaMemsetAsync(h->state, 0, state_bytes, h->stream));
+  for (auto& w : h->work) {
+    CREATE_CUDA(cudaMalloc(&w, std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem));
+    CREATE_CUDA(cudaMemsetAsync(w, 0, std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem, h->stream));
+  }
+  sft_status st = prec == SFT_FP32 ? upload_tables<float>(h) : upload_tables<double>(h);
+  if (st != SFT_OK) return bail(st);
+  std::vector<RealDesc> desc(n_real);
+  for (int r = 0; r < n_real; ++r) {
+    const RealInfo& ri = h->reals[r];
+    const ShapeInfo& s = h->shapes[ri.shape];
+    desc[r] = RealDesc{ri.off, ri.woff, s.nt, s.np, s.pitch, ri.shape, s.geo, ri.flow_row, s.col, 0};
+  }
+  CREATE_CUDA(cudaMalloc(&h->d_desc, desc.size() * sizeof(RealDesc)));
+  CREATE_CUDA(cudaMemcpy(h->d_desc, desc.data(), desc.size() * sizeof(RealDesc), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMalloc(&h->d_status, sizeof(int)));
+  CREATE_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+  // reduction tiles: bands of about 32k cells
+  std::vector<RedTile> rt;
+  std::vector<int> rstart;
+  for (int r = 0; r < n_real; ++r) {
+    const ShapeInfo& s = h->shapes[h->reals[r].shape];
+    rstart.push_back((int)rt.size());
+    const int band = std::max(1, 32768 / s.np);
+    for (int j0 = 0; j0 < s.nt; j0 += band) rt.push_back(RedTile{r, j0, std::min(s.nt, j0 + band), 0});
+  }
+  rstart.push_back((int)rt.size());
+  h->n_rtiles = (int)rt.size();
+  CREATE_CUDA(cudaMalloc(&h->d_rtiles, rt.size() * sizeof(RedTile)));
+  CREATE_CUDA(cudaMemcpy(h->d_rtiles, rt.data(), rt.size() * sizeof(RedTile), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMalloc(&h->d_rstart, rstart.size() * sizeof(int)));
+  CREATE_CUDA(cudaMemcpy(h->d_rstart, rstart.data(), rstart.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMalloc(&h->d_partials, (size_t)h->n_rtiles * kDiagFields * sizeof(double)));
+  CREATE_CUDA(cudaMalloc(&h->d_red, (size_t)n_real * kDiagFields * sizeof(double)));
+  CREATE_CUDA(cudaMallocHost(&h->h_red, (size_t)n_real * kDiagFields * sizeof(double)));
+  CREATE_CUDA(cudaMalloc(&h->d_wpar, (size_t)n_real * 4 * sizeof(double)));
+  CREATE_CUDA(cudaMalloc(&h->d_obs_off, (size_t)n_real * sizeof(int64_t)));
+  for (auto& e : h->ev) CREATE_CUDA(cudaEventCreate(&e));
+  CREATE_CUDA(cudaStreamSynchronize(h->stream));
+#undef CREATE_CUDA
+  *out = h;
+  return SFT_OK;
+}
+
+sft_status sft_destroy(sft_handle h) {
+  free_handle(h);
+  return SFT_OK;
+}
+
+static sft_status check_r(sft_handle h, int32_t r) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (r < 0 || r >= h->n_real) return fail(h, SFT_ERR_ARG, "realization index out of range");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  return SFT_OK;
+}
+
+sft_status sft_set_state(sft_handle h, int32_t r, const void* br, int32_t on_device) {
+  sft_status st = check_r(h, r);
+  if (st != SFT_OK) return st;
+  if (!br) return fail(h, SFT_ERR_ARG, "br is NULL");
+  const RealInfo& ri = h->reals[r];
+  const ShapeInfo& s = h->shapes[ri.shape];
+  char* dst = static_cast<char*>(h->state) + ri.off * h->elem;
+  SFT_CUDA(h, cudaMemcpy2DAsync(dst, s.pitch * h->elem, br, s.np * h->elem, s.np * h->elem, s.nt,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                h->stream));
+  if (h->prec == SFT_FP32) {
+    SFT_CUDA(h, launch_fix_poles<float>(h->n_real, h->stream, h->d_desc, ptr<float>(h->state), r));
+  } else {
+    SFT_CUDA(h, launch_fix_poles<double>(h->n_real, h->stream, h->d_desc, ptr<double>(h->state), r));
+  }
+  return SFT_OK;
+}
+
+sft_status sft_get_state(sft_handle h, int32_t r, void* br, int32_t on_device) {
+  sft_status st = check_r(h, r);
+  if (st != SFT_OK) return st;
+  if (!br) return fail(h, SFT_ERR_ARG, "br is NULL");
+  const RealInfo& ri = h->reals[r];
+  const ShapeInfo& s = h->shapes[ri.shape];
+  const char* src = static_cast<const char*>(h->state) + ri.off * h->elem;
+  SFT_CUDA(h, cudaMemcpy2DAsync(br, s.np * h->elem, src, s.pitch * h->elem, s.np * h->elem, s.nt,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                h->stream));
+  if (!on_device) return sync(h);
+  return SFT_OK;
+}
+
+sft_status sft_set_time(sft_handle h, double t_hours) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  for (auto& r : h->reals) r.t = t_hours;
+  return SFT_OK;
+}
+
+sft_status sft_get_time(sft_handle h, double* t_hours) {
+  if (!h || !t_hours) return fail(h, SFT_ERR_ARG, "NULL argument");
+  for (int r = 0; r < h->n_real; ++r) t_hours[r] = h->reals[r].t;
+  return SFT_OK;
+}
+
+sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
+  if (!h || !params) return fail(h, SFT_ERR_ARG, "NULL argument");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  for (int r = 0; r < h->n_real; ++r) {
+    const sft_flow_params& p = params[r];
+    if (p.adv_time != params[0].adv_time || p.diffusion != params[0].diffusion)
+      return fail(h, SFT_ERR_ARG, "adv_time and diffusion must be the same for all realizations");
+    if (p.adv_space != SFT_ADV_WENO3_CSH && p.adv_space != SFT_ADV_UPWIND)
+      return fail(h, SFT_ERR_ARG, "bad adv_space");
+    if (p.adv_time < SFT_TIME_SSPRK43 || p.adv_time > SFT_TIME_FE)
+      return fail(h, SFT_ERR_ARG, "bad adv_time");
+    if (p.diffusion != SFT_DIFF_RKL2 && p.diffusion != SFT_DIFF_OFF)
+      return fail(h, SFT_ERR_ARG, "bad diffusion");
+    if (!(p.nu >= 0.0) || !(p.cfl_safety > 0.0) || !std::isfinite(p.d0 + p.d2 + p.d4 + p.m1 + p.m3 + p.m5))
+      return fail(h, SFT_ERR_ARG, "bad flow parameters (nu >= 0, cfl_safety > 0, finite)");
+  }
+  // stale configurations refer to the old parameters
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (auto& w : h->waves) {
+    for (auto& c : w.configs) free_config(*c);
+    w.configs.clear();
+  }
+  sft_status st = h->prec == SFT_FP32 ? set_flows_t<float>(h, params) : set_flows_t<double>(h, params);
+  if (st == SFT_OK) h->flows_set = true;
+  return st;
+}
+
+sft_status sft_step(sft_handle h, double t_target_hours, int32_t max_steps, int32_t* steps_taken) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (steps_taken) *steps_taken = 0;
+  if (!h->flows_set) return fail(h, SFT_ERR_STATE, "sft_set_flows must come before sft_step");
+  if (!std::isfinite(t_target_hours)) return fail(h, SFT_ERR_ARG, "t_target must be finite");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  int n = 0;
+  while (max_steps <= 0 || n < max_steps) {
+    bool any_wave = false;
+    for (auto& w : h->waves) {
+      bool any = false;
+      sft_status st = h->prec == SFT_FP32 ? run_step<float>(h, w, t_target_hours, &any)
+                                          : run_step<double>(h, w, t_target_hours, &any);
+      if (st != SFT_OK) return st;
+      any_wave |= any;
+    }
+    if (!any_wave) break;
+    ++n;
+    h->stats.global_steps += 1;
+    if (h->profiling) {
+      sft_status st = check_status_word(h);
+      if (st != SFT_OK) return st;
+    }
+  }
+  if (steps_taken) *steps_taken = n;
+  return SFT_OK;
+}
+
+sft_status sft_assimilate(sft_handle h, const void* br_obs, const void* mu, int32_t obs_per_realization,
+                          int32_t on_device, const sft_assim_params* params) {
+  if (!h || !br_obs || !mu || !params) return fail(h, SFT_ERR_ARG, "NULL argument");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  std::vector<int64_t> off(h->n_real, 0);
+  int64_t total = 0;
+  if (obs_per_realization) {
+    for (int r = 0; r < h->n_real; ++r) {
+      const ShapeInfo& s = h->shapes[h->reals[r].shape];
+      off[r] = total;
+      total += (int64_t)s.nt * s.np;
+    }
+  } else {
+    for (int r = 1; r < h->n_real; ++r)
+      if (h->reals[r].shape != h->reals[0].shape)
+        return fail(h, SFT_ERR_ARG, "shared observations need one grid shape for all realizations");
+    const ShapeInfo& s = h->shapes[h->reals[0].shape];
+    total = (int64_t)s.nt * s.np;
+  }
+  std::vector<double> w(4 * h->n_real);
+  for (int r = 0; r < h->n_real; ++r) {
+    const sft_assim_params& p = params[r];
+    if (!(p.mu_lim >= -1.0) || !std::isfinite(p.alpha_mu)) return fail(h, SFT_ERR_ARG, "bad assim params");
+    w[4 * r + 0] = p.alpha_mu;
+    w[4 * r + 1] = p.mu_lim;
+    w[4 * r + 2] = p.lat_lim_deg * kPi / 180.0;
+    w[4 * r + 3] = p.flux_balance ? 1.0 : 0.0;
+  }
+  if (w != h->h_wpar_last) {
+    SFT_CUDA(h, cudaMemcpyAsync(h->d_wpar, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
+    SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->h_wpar_last = w;
+  }
+  if (off != h->h_obs_off_last) {
+    SFT_CUDA(h, cudaMemcpyAsync(h->d_obs_off, off.data(), off.size() * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, h->stream));
+    SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->h_obs_off_last = off;
+  }
+  const void* dobs = br_obs;
+  const void* dmu = mu;
+  if (!on_device) {
+    const size_t bytes = (size_t)total * h->elem;
+    if (2 * bytes > h->obs_bytes) {
+      SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+      cudaFree(h->d_obs);
+      h->d_obs = nullptr;
+      h->obs_bytes = 0;
+      SFT_CUDA(h, cudaMalloc(&h->d_obs, 2 * bytes));
+      h->obs_bytes = 2 * bytes;
+    }
+    char* base = static_cast<char*>(h->d_obs);
+    SFT_CUDA(h, cudaMemcpyAsync(base, br_obs, bytes, cudaMemcpyHostToDevice, h->stream));
+    SFT_CUDA(h, cudaMemcpyAsync(base + bytes, mu, bytes, cudaMemcpyHostToDevice, h->stream));
+    dobs = base;
+    dmu = base + bytes;
+  }
+  AssimArgs aa{dobs, dmu, h->d_obs_off, h->d_wpar};
+  sft_status st;
+  if (h->prec == SFT_FP32) {
+    st = reduce_fold<float>(h, RED_ASSIM, 0.0, aa);
+    if (st != SFT_OK) return st;
+    SFT_CUDA(h, launch_apply<float>(RED_ASSIM, h->n_rtiles, h->stream, h->d_rtiles, h->d_desc, h->d_geod,
+                                    ptr<float>(h->state), aa, h->d_red));
+  } else {
+    st = reduce_fold<double>(h, RED_ASSIM, 0.0, aa);
+    if (st != SFT_OK) return st;
+    SFT_CUDA(h, launch_apply<double>(RED_ASSIM, h->n_rtiles, h->stream, h->d_rtiles, h->d_desc, h->d_geod,
+                                     ptr<double>(h->state), aa, h->d_red));
+  }
+  if (!on_device) SFT_CUDA(h, cudaStreamSynchronize(h->stream));  // staging reused next call
+  return SFT_OK;
+}
+
+sft_status sft_balance_flux(sft_handle h) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  AssimArgs aa{nullptr, nullptr, nullptr, nullptr};
+  sft_status st;
+  if (h->prec == SFT_FP32) {
+    st = reduce_fold<float>(h, RED_BALANCE, 0.0, aa);
+    if (st != SFT_OK) return st;
+    SFT_CUDA(h, launch_apply<float>(RED_BALANCE, h->n_rtiles, h->stream, h->d_rtiles, h->d_desc,
+                                    h->d_geod, ptr<float>(h->state), aa, h->d_red));
+  } else {
+    st = reduce_fold<double>(h, RED_BALANCE, 0.0, aa);
+    if (st != SFT_OK) return st;
+    SFT_CUDA(h, launch_apply<double>(RED_BALANCE, h->n_rtiles, h->stream, h->d_rtiles, h->d_desc,
+                                     h->d_geod, ptr<double>(h->state), aa, h->d_red));
+  }
+  return SFT_OK;
+}
+
+sft_status sft_flux_diagnostics(sft_handle h, double lat_cut_deg, sft_diag* out) {
+  if (!h || !out) return fail(h, SFT_ERR_ARG, "NULL argument");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  AssimArgs aa{nullptr, nullptr, nullptr, nullptr};
+  const double cut = lat_cut_deg * kPi / 180.0;
+  sft_status st = h->prec == SFT_FP32 ? reduce_fold<float>(h, RED_DIAG, cut, aa)
+                                      : reduce_fold<double>(h, RED_DIAG, cut, aa);
+  if (st != SFT_OK) return st;
+  SFT_CUDA(h, cudaMemcpyAsync(h->h_red, h->d_red, (size_t)h->n_real * kDiagFields * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+  const double mx = kRsunCm * kRsunCm;
+  const double k3 = 3.0 / (4.0 * kPi);
+  for (int r = 0; r < h->n_real; ++r) {
+    const double* v = h->h_red + (size_t)r * kDiagFields;
+    sft_diag& d = out[r];
+    d.flux_signed = v[0] * mx;
+    d.flux_pos = v[1] * mx;
+    d.flux_neg = v[2] * mx;
+    d.flux_pole_n = v[3] * mx;
+    d.flux_pole_s = v[4] * mx;
+    d.area_pole_n = v[5] * mx;
+    d.area_pole_s = v[6] * mx;
+    d.dipole_axial = k3 * v[7];
+    d.h1 = k3 * v[8];
+    d.h2 = k3 * v[9];
+    d.nonfinite = (int64_t)v[10];
+    d.brmin = v[11];
+    d.brmax = v[12];
+    d.absmin = v[13];
+    d.t_hours = h->reals[r].t;
+    d.steps = h->reals[r].steps;
+  }
+  return check_status_word(h);
+}
+
+sft_status sft_get_stats(sft_handle h, sft_stats* out) {
+  if (!h || !out) return fail(h, SFT_ERR_ARG, "NULL argument");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = h->stats;
+  return SFT_OK;
+}
+
+sft_status sft_reset_stats(sft_handle h) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  h->stats = sft_stats{};
+  return SFT_OK;
+}
+
+sft_status sft_set_profiling(sft_handle h, int32_t profile) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  h->profiling = profile != 0;
+  return SFT_OK;
+}
+
+sft_status sft_set_graphs(sft_handle h, int32_t use_graphs) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  h->use_graphs = use_graphs != 0;
+  return SFT_OK;
+}
+
+sft_status sft_set_tile_rows(sft_handle h, int32_t shape_id, int32_t rows) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (shape_id < 0 || shape_id >= (int)h->shapes.size()) return fail(h, SFT_ERR_ARG, "bad shape id");
+  if (rows != 0 && rows != 1 && rows != 2 && rows != 4 && rows != 8)
+    return fail(h, SFT_ERR_ARG, "tile rows must be 0, 1, 2, 4 or 8");
+  h->shapes[shape_id].tile_rows = rows;
+  return SFT_OK;
+}
+
+int32_t sft_get_tile_rows(sft_handle h, int32_t shape_id) {
+  if (!h || shape_id < 0 || shape_id >= (int)h->shapes.size()) return 0;
+  return h->shapes[shape_id].tile_rows;
+}
+
+int32_t sft_wave_size(sft_handle h) { return h ? h->wave_size : 0; }
+
+sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cfl, double* dt_euler,
+                         int32_t* stages) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (r < 0 || r >= h->n_real) return fail(h, SFT_ERR_ARG, "realization index out of range");
+  if (!h->flows_set) return fail(h, SFT_ERR_STATE, "sft_set_flows first");
+  const RealInfo& ri = h->reals[r];
+  if (dt_cfl) *dt_cfl = ri.dt_cfl;
+  if (dt_euler) *dt_euler = ri.dt_euler;
+  if (stages) *stages = ri.fp.diffusion == SFT_DIFF_RKL2 ? rkl2_stages(dt_hours, ri.dt_euler) : 0;
+  return SFT_OK;
+}
+
+}  // extern "C"

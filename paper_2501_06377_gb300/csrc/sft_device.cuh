@@ -1,0 +1,154 @@
+// sft_device.cuh -- device-side data layout and kernels of libsft.
+//
+// Layout (all realizations of a handle share one pool per array):
+//   map[r](j, k) = pool[desc[r].off + j * pitch + k], j = 0..nt-1 (poles at
+//   j = 0 and nt-1, each pole row holding one value), k = 0..np-1 unique
+//   longitudes, pitch = np rounded up to 32 elements (128-B rows in FP32).
+// Work arrays (advection stage buffers, RKL2 increments) use the same layout
+// at desc[r].woff.
+//
+// Every stage kernel is launched over a table of tiles.  An interior tile is
+// TR rows x TC columns of one realization, one thread per V consecutive
+// longitudes (V = 4 floats or 2 doubles: one 16-byte vector); a pole tile is
+// one block that reduces the ring next to the pole in FP64 and rewrites the
+// pole row.  Tiles are ordered so that the realizations still active at a
+// given stage form a prefix of the table: a stage launches only that prefix.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sft {
+
+constexpr int kThreads = 256;
+
+template <typename T> struct VecT;
+template <> struct VecT<float> { using type = float4; static constexpr int N = 4; };
+template <> struct VecT<double> { using type = double2; static constexpr int N = 2; };
+
+struct RealDesc {
+  int64_t off;     // element offset of row 0 in the state pool
+  int64_t woff;    // element offset of row 0 in each work array
+  int32_t nt, np, pitch, shape;
+  int32_t geo;     // first row of the shape's geometry table
+  int32_t flow;    // first row of this realization's flow table
+  int32_t col;     // first entry of the shape's cos/sin(phi_k) tables
+  int32_t pad;
+};
+
+// Per-row geometry of a shape (uniform grid, Sec. 3.2).
+template <typename T> struct RowGeo {
+  T cN;        // sin(th_{j-1/2}) / (dth^2 sin th_j)   (Eq. diffusion_matrix a_{j-1,k} / nu)
+  T cS;        // sin(th_{j+1/2}) / (dth^2 sin th_j)   (a_{j+1,k} / nu)
+  T cE;        // 1 / (dph^2 sin^2 th_j)               (a_{j,k+-1} / nu)
+  T inv_sdth;  // 1 / (sin th_j dth)
+  T inv_sdph;  // 1 / (sin th_j dph)
+  T sdn;       // sin th_{j-1/2}
+  T sup;       // sin th_{j+1/2}
+  T pad;
+};
+
+// Per-row FP64 geometry for the reductions.
+struct RowGeoD {
+  double area;   // area of one stored entry: sin th_j dth dph, or cap/np on a pole row
+  double cos_t;  // cos th_j
+  double sin_t;  // sin th_j
+  double lat;    // latitude of row j (rad)
+};
+
+// Per-row flow of a realization (Eq. dr, Eq. mf, code units).
+template <typename T> struct RowFlow {
+  T vdn;    // v_theta at face j-1/2
+  T vup;    // v_theta at face j+1/2
+  T vp;     // v_phi on row j
+  T alpha;  // LLF alpha_j = max |v_theta| over faces j-5/2..j+5/2 (App. B)
+};
+
+struct ShapeConst {
+  double pole_diff;  // sin(dth/2) dph / (dth * cap)  (times nu: diffusion cap operator)
+  double pole_adv;   // sin(dth/2) dph / cap          (advection cap operator)
+  double dth, dph;
+};
+
+// Per-realization parameters of one time step.
+struct StepParam {
+  double dt;        // hours; 0 = idle this step
+  double nudt;      // nu * dt (R_sun^2)
+  double eps_t;     // WENO eps in the theta sweep
+  double eps_p;     // WENO eps in the phi sweep
+  double alpha_uw;  // UW/CD factor
+  int32_t s;        // RKL2 stages (0 = no diffusion)
+  int32_t coef;     // index of this realization's stage-0 coefficients
+  int32_t weno;     // 1 = WENO3-CS(h), 0 = UW
+  int32_t adv;      // 1 = advection on for this realization
+};
+
+// RKL2 stage coefficients in increment form (see rkl2_stage_kernel).
+template <typename T> struct Coef {
+  T mu, nu, mut, gsum;  // mu_j, nu_j, mu~_j, mu~_j + gamma~_j
+};
+
+// kind & 3: 0 interior, 1 north cap, 2 south cap.  kind >> 8: log2 of the
+// threads per tile row (256 threads = TR rows x 256/TR threads), so tiles of
+// different heights (one per grid shape) run in the same launch.
+struct Tile {
+  int32_t r;     // realization
+  int32_t j0;    // first row (interior tiles)
+  int32_t k0;    // first longitude (interior tiles)
+  int32_t kind;
+};
+
+// Advection stage: out = a * fn + b * fin - c * dt * F_A(fin)   (Sec. 3.6.2)
+template <typename T> struct AdvStage {
+  const T* fin;
+  const T* fn;
+  T* out;
+  int fin_work, fn_work, out_work;  // 1: array is a work array (use woff), 0: the state pool
+  T a, b, c;
+};
+
+// Launch wrappers (defined in sft_kernels.cu).
+template <typename T>
+cudaError_t launch_rkl2_stage(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                              const StepParam* sp, const RowGeo<T>* geo, const ShapeConst* shc,
+                              const Coef<T>* coef, T* B, T* G, T* D0, T* D1, int stage,
+                              int allow_final, int* status);
+template <typename T>
+cudaError_t launch_adv_stage(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                             const StepParam* sp, const RowGeo<T>* geo, const RowFlow<T>* flow,
+                             const ShapeConst* shc, T* state, T* work_base0, T* work_base1,
+                             AdvStage<T> s);
+template <typename T>
+cudaError_t launch_fix_poles(int n_real, cudaStream_t st, const RealDesc* rd, T* state, int only_r);
+
+// Reductions: one block per (realization, band of rows); partial results
+// per block; a second kernel folds them per realization in a fixed order.
+enum RedMode { RED_DIAG = 0, RED_ASSIM = 1, RED_BALANCE = 2 };
+constexpr int kDiagFields = 14;
+
+struct RedTile {
+  int32_t r, j0, j1, pad;  // rows [j0, j1)
+};
+
+// Observed maps and mu maps in caller layout [nt][np] (pitch np); realization
+// r's maps start at element obs_off[r] of obs / mu (all 0 when shared).
+struct AssimArgs {
+  const void* obs;
+  const void* mu;
+  const int64_t* obs_off;
+  const double* wpar;  // per realization: alpha_mu, mu_lim, lat_lim (rad), balance flag
+};
+
+template <typename T>
+cudaError_t launch_reduce(int mode, int n_tiles, cudaStream_t st, const RedTile* tiles,
+                          const RealDesc* rd, const RowGeoD* geod, const double* cosp,
+                          const double* sinp, const T* state, double lat_cut, AssimArgs aa,
+                          double* partials);
+cudaError_t launch_fold(int mode, int n_real, cudaStream_t st, const int* tile_start,
+                        const double* partials, const double* wpar, double* out);
+template <typename T>
+cudaError_t launch_apply(int mode, int n_tiles, cudaStream_t st, const RedTile* tiles,
+                         const RealDesc* rd, const RowGeoD* geod, T* state, AssimArgs aa,
+                         const double* factors);
+
+}  // namespace sft

@@ -1,0 +1,681 @@
+// sft_kernels.cu -- sm_103a kernels of the SFT step.
+//
+//  rkl2_stage_kernel  one RKL2 stage (Sec. 3.7.2) of the 5-point diffusion
+//                     operator of Eq. (diffusion_op) with constant nu and the
+//                     polar caps of App. A, in increment form (see below).
+//  adv_stage_kernel   one SSPRK / FE stage (Sec. 3.6.2) of the conservative
+//                     advection operator of Sec. 3.6.1 with WENO3-CS(h)
+//                     (App. B) or UW face fluxes and the App. A caps.
+//  reduce/fold/apply  FP64 reductions for the analysis quantities (Sec. 2.6),
+//                     the assimilation balance (Sec. 2.3) and map balancing.
+//
+// All stage kernels are HBM-streaming stencils: one 16-byte vector per
+// thread per array, phi neighbours through warp shuffles (global loads only
+// at warp edges, the periodic seam and the ragged last tile), theta
+// neighbours as vector loads of the adjacent rows (served by L2 when the
+// adjacent tile ran just before).
+#include <math.h>
+
+#include "sft_device.cuh"
+
+namespace sft {
+
+namespace {
+
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  static constexpr int N = 4;
+  __device__ __forceinline__ static void ldg(const float* p, float (&c)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+  }
+  __device__ __forceinline__ static void ld(const float* p, float (&c)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+  }
+  __device__ __forceinline__ static void st(float* p, const float (&c)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(c[0], c[1], c[2], c[3]);
+  }
+};
+template <> struct Vec<double> {
+  static constexpr int N = 2;
+  __device__ __forceinline__ static void ldg(const double* p, double (&c)[2]) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    c[0] = v.x; c[1] = v.y;
+  }
+  __device__ __forceinline__ static void ld(const double* p, double (&c)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    c[0] = v.x; c[1] = v.y;
+  }
+  __device__ __forceinline__ static void st(double* p, const double (&c)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(c[0], c[1]);
+  }
+};
+
+// e[H + i] = row value at column kc + i (periodic), for i = -H .. N+H-1.
+// Every lane of the warp must call this (warp shuffles); lanes with kc >= np
+// skip their global loads and get undefined e.
+template <typename T, int N, int H>
+__device__ __forceinline__ void row_ext(const T* __restrict__ row, int kc, int np, int lane,
+                                        const T (&c)[N], T (&e)[N + 2 * H]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) e[H + i] = c[i];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    e[H - 1 - m] = __shfl_up_sync(0xffffffffu, c[N - 1 - m], 1);
+    e[H + N + m] = __shfl_down_sync(0xffffffffu, c[m], 1);
+  }
+  if (kc >= np) return;
+  if (lane == 0 || kc == 0) {
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      const int k = kc - 1 - m;
+      e[H - 1 - m] = row[k < 0 ? k + np : k];
+    }
+  }
+  if (lane == 31 || kc + N >= np) {
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      const int k = kc + N + m;
+      e[H + N + m] = row[k >= np ? k - np : k];
+    }
+  }
+  if (kc + N > np) {  // ragged last vector: columns >= np hold the wrapped values
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (kc + i >= np) e[H + i] = row[kc + i - np];
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block, result returned to every thread.  Contains barriers.
+__device__ double block_sum(double v, double* sm) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < nw; ++i) t += sm[i];  // fixed order: deterministic
+  return t;
+}
+
+// UW/CD flux at a face (Sec. 3.6.1): v/2 [(1-uw) B_hi + (1+uw) B_lo],
+// uw = alpha_uw sign(v), sign(0) = +1.
+template <typename T>
+__device__ __forceinline__ T uw_flux(T v, T blo, T bhi, T auw) {
+  const T uw = v >= T(0) ? auw : -auw;
+  return v * T(0.5) * ((T(1) - uw) * bhi + (T(1) + uw) * blo);
+}
+
+// WENO3-CS(h) face flux (App. B) on a uniform grid, from LM_{i-2}, LM_{i-1},
+// LM_i and LP_{i-1}, LP_i, LP_{i+1}.  Weight algebra is written as
+// w0/(w0+w1) = 1 / (1 + 2 ((eps+b0)/(eps+b1))^2) with linear weights 1/3, 2/3.
+template <typename T>
+__device__ __forceinline__ T weno_half(T p0, T p1, T b0, T b1, T eps) {
+  const T q0 = eps + b0, q1 = eps + b1;
+  const T a0 = q1 * q1;            // (1/3)/q0^2 scaled by 3 q0^2 q1^2
+  const T a1 = T(2) * q0 * q0;     // (2/3)/q1^2 scaled the same way
+  return (a0 * p0 + a1 * p1) / (a0 + a1);
+}
+
+template <typename T>
+__device__ __forceinline__ T weno_flux(T lmm2, T lmm1, T lm0, T lpm1, T lp0, T lpp1, T eps) {
+  const T dm0 = lmm1 - lmm2, dm1 = lm0 - lmm1;
+  const T um = weno_half(T(1.5) * lmm1 - T(0.5) * lmm2, T(0.5) * (lmm1 + lm0), dm0 * dm0,
+                         dm1 * dm1, eps);
+  const T dp0 = lpp1 - lp0, dp1 = lp0 - lpm1;
+  const T up = weno_half(T(1.5) * lp0 - T(0.5) * lpp1, T(0.5) * (lp0 + lpm1), dp0 * dp0,
+                         dp1 * dp1, eps);
+  return um + up;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// RKL2 stage, increment form.
+//
+// The RKL2 stages Y_j = mu_j Y_{j-1} + nu_j Y_{j-2} + (1-mu_j-nu_j) Y_0
+//   + mu~_j dt L(Y_{j-1}) + gamma~_j dt L(Y_0)   (Meyer, Balsara & Aslam 2014)
+// are carried as increments delta_j = Y_j - Y_0 (L is linear):
+//   G = dt L(Y_0),  delta_1 = mu~_1 G,
+//   delta_j = mu_j delta_{j-1} + nu_j delta_{j-2} + mu~_j dt L(delta_{j-1})
+//             + (mu~_j + gamma~_j) G,
+//   Y_s = Y_0 + delta_s   (written to the state by the last stage).
+// Identical in exact arithmetic; in FP32 the rounding is relative to the
+// increment, not to |B|.  Per stage HBM traffic: read delta_{j-1},
+// delta_{j-2}, G; write delta_j (over delta_{j-2}) = 16 B per cell (FP32).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+rkl2_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+                  const StepParam* __restrict__ sp, const RowGeo<T>* __restrict__ geo,
+                  const ShapeConst* __restrict__ shc, const Coef<T>* __restrict__ coef,
+                  T* __restrict__ B, T* __restrict__ G, T* __restrict__ D0, T* __restrict__ D1,
+                  int stage, int allow_final, int* __restrict__ status) {
+  constexpr int N = Vec<T>::N;
+  __shared__ double sm[kThreads / 32];
+  const Tile tl = tiles[blockIdx.x];
+  const int kind = tl.kind & 3, lx = tl.kind >> 8;  // lx = log2(threads per tile row)
+  const RealDesc d = rd[tl.r];
+  const StepParam p = sp[tl.r];
+  if (stage > p.s) return;
+  const bool first = stage == 1;
+  const bool last = stage == p.s && allow_final;
+  const Coef<T> cf = coef[p.coef + stage];
+  const T nudt = T(p.nudt);
+  T* Dout = ((stage & 1) ? D1 : D0) + d.woff;          // delta_j (over delta_{j-2})
+  const T* Din = ((stage & 1) ? D0 : D1) + d.woff;     // delta_{j-1}
+  T* Gw = G + d.woff;
+  T* Bs = B + d.off;
+  const T* Y = first ? Bs : Din;
+  const int pitch = d.pitch, np = d.np;
+
+  if (kind != 0) {
+    // App. A cap: div(nu grad B) = sin(dth/2) dph sum_k nu (Y_adj,k - Y_p)/dth / cap
+    const int jp = kind == 1 ? 0 : d.nt - 1;
+    const int ja = kind == 1 ? 1 : d.nt - 2;
+    const T* ya = Y + (int64_t)ja * pitch;
+    const double yp = double(Y[(int64_t)jp * pitch]);
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) acc += double(ya[k]) - yp;
+    const int64_t po = (int64_t)jp * pitch;
+    // pointwise pole operands, read before the barrier inside block_sum
+    double gp = 0.0, d2 = 0.0, b0 = 0.0;
+    if (!first) {
+      gp = double(Gw[po]);
+      if (stage > 2) d2 = double(Dout[po]);
+      if (last) b0 = double(Bs[po]);
+    }
+    const double Lp = shc[d.shape].pole_diff * block_sum(acc, sm);
+    if (first) {
+      const T g = T(double(nudt) * Lp);
+      const T o = cf.mut * g;
+      for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        Gw[po + k] = g;
+        Dout[po + k] = o;
+      }
+    } else {
+      const double o = double(cf.mu) * yp + double(cf.nu) * d2 +
+                       double(cf.mut) * double(nudt) * Lp + double(cf.gsum) * gp;
+      if (last) {
+        const T v = T(b0 + o);
+        if (threadIdx.x == 0 && !isfinite(double(v))) atomicOr(status, 1);
+        for (int k = threadIdx.x; k < np; k += blockDim.x) Bs[po + k] = v;
+      } else {
+        const T v = T(o);
+        for (int k = threadIdx.x; k < np; k += blockDim.x) Dout[po + k] = v;
+      }
+    }
+    return;
+  }
+
+  const int ty = threadIdx.x >> lx, tx = threadIdx.x & ((1 << lx) - 1), lane = threadIdx.x & 31;
+  const int j = tl.j0 + ty;
+  if (j > d.nt - 2) return;  // a warp lies within one row: uniform exit
+  const int kc = tl.k0 + tx * N;
+  const int64_t ro = (int64_t)j * pitch;
+  T c[N], up[N], dn[N];
+  if (kc < np) {
+    Vec<T>::ldg(Y + ro + kc, c);
+    Vec<T>::ldg(Y + ro - pitch + kc, up);
+    Vec<T>::ldg(Y + ro + pitch + kc, dn);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) c[i] = up[i] = dn[i] = T(0);
+  }
+  T e[N + 2];
+  row_ext<T, N, 1>(Y + ro, kc, np, lane, c, e);
+  if (kc >= np) return;
+  const RowGeo<T> g = geo[d.geo + j];
+  T L[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    L[i] = g.cN * (up[i] - c[i]) + g.cS * (dn[i] - c[i]) + g.cE * ((e[i] - c[i]) + (e[i + 2] - c[i]));
+  T o[N];
+  if (first) {
+    T gv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      gv[i] = nudt * L[i];
+      o[i] = cf.mut * gv[i];
+    }
+    Vec<T>::st(Gw + ro + kc, gv);
+    Vec<T>::st(Dout + ro + kc, o);
+    return;
+  }
+  T gv[N], d2[N];
+  Vec<T>::ldg(Gw + ro + kc, gv);
+  if (stage > 2) {
+    Vec<T>::ld(Dout + ro + kc, d2);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) d2[i] = T(0);
+  }
+  const T mutdt = cf.mut * nudt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = cf.mu * c[i] + cf.nu * d2[i] + mutdt * L[i] + cf.gsum * gv[i];
+  if (last) {
+    T b[N];
+    Vec<T>::ld(Bs + ro + kc, b);
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      b[i] += o[i];
+      bad |= (kc + i < np) && !isfinite(double(b[i]));
+    }
+    Vec<T>::st(Bs + ro + kc, b);
+    if (bad) atomicOr(status, 1);
+  } else {
+    Vec<T>::st(Dout + ro + kc, o);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Advection stage: out = a fn + b fin - c dt F_A(fin).
+// F_A(B)_{j,k} = (sin th_{j+1/2} F_{j+1/2} - sin th_{j-1/2} F_{j-1/2}) / (sin th_j dth)
+//              + (F_{k+1/2} - F_{k-1/2}) / (sin th_j dph)           (Sec. 3.6.1)
+// theta faces f <= 1 and f >= nt-3 (the cap faces and the other face of each
+// pole-adjacent cell) use UW; the rest WENO3-CS(h) (or all UW).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+                 const StepParam* __restrict__ sp, const RowGeo<T>* __restrict__ geo,
+                 const RowFlow<T>* __restrict__ flow, const ShapeConst* __restrict__ shc,
+                 T* __restrict__ state, T* __restrict__ w0, T* __restrict__ w1, AdvStage<T> s) {
+  constexpr int N = Vec<T>::N;
+  __shared__ double sm[kThreads / 32];
+  (void)w0;
+  (void)w1;
+  const Tile tl = tiles[blockIdx.x];
+  const int kind = tl.kind & 3, lx = tl.kind >> 8;
+  const RealDesc d = rd[tl.r];
+  const StepParam p = sp[tl.r];
+  if (p.dt == 0.0 || p.adv == 0) return;
+  const T* fin = s.fin + (s.fin_work ? d.woff : d.off);
+  const T* fn = s.fn ? s.fn + (s.fn_work ? d.woff : d.off) : nullptr;
+  T* out = s.out + (s.out_work ? d.woff : d.off);
+  const int pitch = d.pitch, np = d.np, nt = d.nt;
+  const T cdt = s.c * T(p.dt);
+  const T auw = T(p.alpha_uw);
+
+  if (kind != 0) {
+    const bool north = kind == 1;
+    const int jp = north ? 0 : nt - 1;
+    const int ja = north ? 1 : nt - 2;
+    const int64_t po = (int64_t)jp * pitch;
+    const T* ba = fin + (int64_t)ja * pitch;
+    const T bp = fin[po];
+    const T v = north ? flow[d.flow + 1].vdn : flow[d.flow + nt - 2].vup;
+    double acc = 0.0;
+    if (s.c != T(0)) {
+      for (int k = threadIdx.x; k < np; k += blockDim.x)
+        acc += double(north ? uw_flux(v, bp, ba[k], auw) : uw_flux(v, ba[k], bp, auw));
+    }
+    const double fnp = fn ? double(fn[po]) : 0.0;  // read before the barrier
+    const double div = (north ? 1.0 : -1.0) * shc[d.shape].pole_adv * block_sum(acc, sm);
+    const T o = T(double(s.a) * fnp + double(s.b) * double(bp) - double(s.c) * p.dt * div);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) out[po + k] = o;
+    return;
+  }
+
+  const int ty = threadIdx.x >> lx, tx = threadIdx.x & ((1 << lx) - 1), lane = threadIdx.x & 31;
+  const int j = tl.j0 + ty;
+  if (j > nt - 2) return;
+  const int kc = tl.k0 + tx * N;
+  const int64_t ro = (int64_t)j * pitch;
+  T R[5][N];
+  if (kc < np) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      int jj = j - 2 + m;
+      jj = jj < 0 ? 0 : (jj > nt - 1 ? nt - 1 : jj);
+      Vec<T>::ldg(fin + (int64_t)jj * pitch + kc, R[m]);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int i = 0; i < N; ++i) R[m][i] = T(0);
+  }
+  T e[N + 4];
+  row_ext<T, N, 2>(fin + ro, kc, np, lane, R[2], e);
+  if (kc >= np) return;
+  T o[N];
+  if (s.c == T(0)) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] = s.b * R[2][i];
+  } else {
+    const RowGeo<T> g = geo[d.geo + j];
+    RowFlow<T> fl[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      int jj = j - 2 + m;
+      jj = jj < 1 ? 1 : (jj > nt - 2 ? nt - 2 : jj);
+      fl[m] = flow[d.flow + jj];
+    }
+    const bool weno = p.weno != 0;
+    // phi faces k-1/2, k = kc .. kc+N
+    T F[N + 1];
+    const T v = fl[2].vp;
+    if (weno) {
+      const T eps = T(p.eps_p);
+      const T av = fabs(v);
+      const T hp = T(0.5) * (v + av), hm = T(0.5) * (v - av);
+#pragma unroll
+      for (int i = 0; i <= N; ++i)
+        F[i] = weno_flux(hp * e[i], hp * e[i + 1], hp * e[i + 2], hm * e[i + 1], hm * e[i + 2],
+                         hm * e[i + 3], eps);
+    } else {
+#pragma unroll
+      for (int i = 0; i <= N; ++i) F[i] = uw_flux(v, e[i + 1], e[i + 2], auw);
+    }
+    // theta faces j-1/2 (f = j-1) and j+1/2 (f = j)
+    const bool wdn = weno && (j - 1 >= 2) && (j - 1 <= nt - 4);
+    const bool wup = weno && (j >= 2) && (j <= nt - 4);
+    const T eps = T(p.eps_t);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T Fdn, Fup;
+      if (wdn) {
+        Fdn = weno_flux(T(0.5) * R[0][i] * (fl[0].vdn + fl[0].alpha),
+                        T(0.5) * R[1][i] * (fl[1].vdn + fl[1].alpha),
+                        T(0.5) * R[2][i] * (fl[2].vdn + fl[2].alpha),
+                        T(0.5) * R[1][i] * (fl[1].vup - fl[1].alpha),
+                        T(0.5) * R[2][i] * (fl[2].vup - fl[2].alpha),
+                        T(0.5) * R[3][i] * (fl[3].vup - fl[3].alpha), eps);
+      } else {
+        Fdn = uw_flux(fl[2].vdn, R[1][i], R[2][i], auw);
+      }
+      if (wup) {
+        Fup = weno_flux(T(0.5) * R[1][i] * (fl[1].vdn + fl[1].alpha),
+                        T(0.5) * R[2][i] * (fl[2].vdn + fl[2].alpha),
+                        T(0.5) * R[3][i] * (fl[3].vdn + fl[3].alpha),
+                        T(0.5) * R[2][i] * (fl[2].vup - fl[2].alpha),
+                        T(0.5) * R[3][i] * (fl[3].vup - fl[3].alpha),
+                        T(0.5) * R[4][i] * (fl[4].vup - fl[4].alpha), eps);
+      } else {
+        Fup = uw_flux(fl[2].vup, R[2][i], R[3][i], auw);
+      }
+      const T div = (g.sup * Fup - g.sdn * Fdn) * g.inv_sdth + (F[i + 1] - F[i]) * g.inv_sdph;
+      o[i] = s.b * R[2][i] - cdt * div;
+    }
+  }
+  if (fn != nullptr && s.a != T(0)) {
+    T f0[N];
+    Vec<T>::ld(fn + ro + kc, f0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] += s.a * f0[i];
+  }
+  Vec<T>::st(out + ro + kc, o);
+}
+
+template <typename T>
+__global__ void fix_poles_kernel(const RealDesc* __restrict__ rd, T* __restrict__ state, int only_r) {
+  const int r = only_r >= 0 ? only_r : blockIdx.x >> 1;
+  const RealDesc d = rd[r];
+  const int jp = (blockIdx.x & 1) ? d.nt - 1 : 0;
+  T* row = state + d.off + (int64_t)jp * d.pitch;
+  const T v = row[0];
+  __syncthreads();
+  for (int k = threadIdx.x + 1; k < d.np; k += blockDim.x) row[k] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions (FP64 accumulation)
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ldT(const void* p, int64_t i) {
+  return static_cast<const T*>(p)[i];
+}
+
+// Eq. (data_assim_f): F = mu^alpha_mu if mu > mu_lim and |lat| < lat_lim.
+template <typename T>
+__device__ __forceinline__ T assim_weight(T mu, double lat, const double* w) {
+  if (!(double(mu) > w[1]) || !(fabs(lat) < w[2])) return T(0);
+  return pow(mu, T(w[0]));
+}
+
+__device__ double block_min(double v, double* sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  double t = sm[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = fmin(t, sm[i]);
+  return t;
+}
+
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+              const RowGeoD* __restrict__ geod, const double* __restrict__ cosp,
+              const double* __restrict__ sinp, const T* __restrict__ state, double lat_cut,
+              AssimArgs aa, double* __restrict__ partials) {
+  __shared__ double sm[kThreads / 32];
+  const RedTile tl = tiles[blockIdx.x];
+  const RealDesc d = rd[tl.r];
+  const T* b = state + d.off;
+  double acc[11];
+#pragma unroll
+  for (int f = 0; f < 11; ++f) acc[f] = 0.0;
+  double mn = INFINITY, mx = -INFINITY, amn = INFINITY;
+  const double* w = aa.wpar ? aa.wpar + 4 * tl.r : nullptr;
+  const int64_t obase = aa.obs_off ? aa.obs_off[tl.r] : 0;
+  for (int j = tl.j0; j < tl.j1; ++j) {
+    const RowGeoD gd = geod[d.geo + j];
+    const bool pole = (j == 0) || (j == d.nt - 1);
+    const T* row = b + (int64_t)j * d.pitch;
+    for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+      const T bv = row[k];
+      if (mode == RED_DIAG) {
+        const double x = double(bv);
+        if (!isfinite(x)) {
+          acc[10] += 1.0;
+          continue;
+        }
+        const double ab = gd.area * x;
+        acc[0] += ab;
+        if (x > 0.0) acc[1] += ab;
+        if (x < 0.0) acc[2] += ab;
+        if (gd.lat >= lat_cut - 1e-12) { acc[3] += ab; acc[5] += gd.area; }
+        if (gd.lat <= -lat_cut + 1e-12) { acc[4] += ab; acc[6] += gd.area; }
+        acc[7] += ab * gd.cos_t;
+        acc[8] += ab * gd.sin_t * cosp[d.col + k];
+        acc[9] += ab * gd.sin_t * sinp[d.col + k];
+        mn = fmin(mn, x);
+        mx = fmax(mx, x);
+        amn = fmin(amn, fabs(x));
+      } else {
+        T x;
+        if (mode == RED_ASSIM) {
+          const int kk = pole ? 0 : k;
+          const int64_t oi = obase + (int64_t)j * d.np + kk;
+          const T F = assim_weight<T>(ldT<T>(aa.mu, oi), gd.lat, w);
+          x = F * (ldT<T>(aa.obs, oi) - bv);
+        } else {
+          x = bv;
+        }
+        const double ax = gd.area * double(x);
+        if (x > T(0)) acc[0] += ax;
+        if (x < T(0)) acc[1] += ax;
+      }
+    }
+  }
+  double* out = partials + (int64_t)blockIdx.x * kDiagFields;
+  const int nf = mode == RED_DIAG ? 11 : 2;
+  for (int f = 0; f < nf; ++f) {
+    const double t = block_sum(acc[f], sm);
+    if (threadIdx.x == 0) out[f] = t;
+  }
+  if (mode == RED_DIAG) {
+    const double a = block_min(mn, sm);
+    if (threadIdx.x == 0) out[11] = a;
+    const double c = -block_min(-mx, sm);
+    if (threadIdx.x == 0) out[12] = c;
+    const double e = block_min(amn, sm);
+    if (threadIdx.x == 0) out[13] = e;
+  }
+}
+
+// One block per realization: fold its tiles' partials in a fixed order.
+// RED_DIAG: out[r*kDiagFields + f].  RED_ASSIM / RED_BALANCE: out[r*4 + ...] =
+// {phi+, phi-, factor for x > 0, factor for x <= 0} (Eq. fluxbal).
+__global__ void fold_kernel(int mode, const int* __restrict__ tile_start,
+                            const double* __restrict__ partials, const double* __restrict__ wpar,
+                            double* __restrict__ out) {
+  __shared__ double sm[kThreads / 32];
+  const int r = blockIdx.x;
+  const int t0 = tile_start[r], t1 = tile_start[r + 1];
+  const int nf = mode == RED_DIAG ? kDiagFields : 2;
+  double res[kDiagFields];
+  for (int f = 0; f < nf; ++f) {
+    const bool is_min = mode == RED_DIAG && (f == 11 || f == 13);
+    const bool is_max = mode == RED_DIAG && f == 12;
+    double v = is_min ? INFINITY : (is_max ? -INFINITY : 0.0);
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+      const double x = partials[(int64_t)t * kDiagFields + f];
+      v = is_min ? fmin(v, x) : (is_max ? fmax(v, x) : v + x);
+    }
+    if (is_min) res[f] = block_min(v, sm);
+    else if (is_max) res[f] = -block_min(-v, sm);
+    else res[f] = block_sum(v, sm);
+  }
+  if (threadIdx.x != 0) return;
+  if (mode == RED_DIAG) {
+    for (int f = 0; f < kDiagFields; ++f) out[(int64_t)r * kDiagFields + f] = res[f];
+    return;
+  }
+  const double pp = res[0], pm = res[1];
+  double fp = 1.0, fm = 1.0;
+  const bool balance = mode == RED_BALANCE || (wpar && wpar[4 * r + 3] != 0.0);
+  if (balance && pp != 0.0 && pm != 0.0) {
+    const double ratio = fabs(pp / pm);
+    fp = 1.0 / sqrt(ratio);
+    fm = sqrt(ratio);
+  }
+  out[4 * r + 0] = pp;
+  out[4 * r + 1] = pm;
+  out[4 * r + 2] = fp;
+  out[4 * r + 3] = fm;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+apply_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+             const RowGeoD* __restrict__ geod, T* __restrict__ state, AssimArgs aa,
+             const double* __restrict__ fac) {
+  const RedTile tl = tiles[blockIdx.x];
+  const RealDesc d = rd[tl.r];
+  T* b = state + d.off;
+  const T fp = T(fac[4 * tl.r + 2]), fm = T(fac[4 * tl.r + 3]);
+  const double* w = aa.wpar ? aa.wpar + 4 * tl.r : nullptr;
+  const int64_t obase = aa.obs_off ? aa.obs_off[tl.r] : 0;
+  for (int j = tl.j0; j < tl.j1; ++j) {
+    const double lat = geod[d.geo + j].lat;
+    const bool pole = (j == 0) || (j == d.nt - 1);
+    T* row = b + (int64_t)j * d.pitch;
+    for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+      const T bv = row[k];
+      if (mode == RED_ASSIM) {
+        const int kk = pole ? 0 : k;
+        const int64_t oi = obase + (int64_t)j * d.np + kk;
+        const T F = assim_weight<T>(ldT<T>(aa.mu, oi), lat, w);
+        const T x = F * (ldT<T>(aa.obs, oi) - bv);
+        row[k] = bv + (x > T(0) ? x * fp : x * fm);
+      } else {
+        row[k] = bv > T(0) ? bv * fp : bv * fm;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_rkl2_stage(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                              const StepParam* sp, const RowGeo<T>* geo, const ShapeConst* shc,
+                              const Coef<T>* coef, T* B, T* G, T* D0, T* D1, int stage,
+                              int allow_final, int* status) {
+  if (n_tiles <= 0) return cudaSuccess;
+  rkl2_stage_kernel<T><<<n_tiles, kThreads, 0, st>>>(tiles, rd, sp, geo, shc, coef, B, G, D0, D1,
+                                                     stage, allow_final, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adv_stage(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                             const StepParam* sp, const RowGeo<T>* geo, const RowFlow<T>* flow,
+                             const ShapeConst* shc, T* state, T* w0, T* w1, AdvStage<T> s) {
+  if (n_tiles <= 0) return cudaSuccess;
+  adv_stage_kernel<T><<<n_tiles, kThreads, 0, st>>>(tiles, rd, sp, geo, flow, shc, state, w0, w1, s);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fix_poles(int n_real, cudaStream_t st, const RealDesc* rd, T* state, int only_r) {
+  const int blocks = only_r >= 0 ? 2 : 2 * n_real;
+  if (blocks <= 0) return cudaSuccess;
+  fix_poles_kernel<T><<<blocks, kThreads, 0, st>>>(rd, state, only_r);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce(int mode, int n_tiles, cudaStream_t st, const RedTile* tiles,
+                          const RealDesc* rd, const RowGeoD* geod, const double* cosp,
+                          const double* sinp, const T* state, double lat_cut, AssimArgs aa,
+                          double* partials) {
+  if (n_tiles <= 0) return cudaSuccess;
+  reduce_kernel<T><<<n_tiles, kThreads, 0, st>>>(mode, tiles, rd, geod, cosp, sinp, state, lat_cut,
+                                                 aa, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold(int mode, int n_real, cudaStream_t st, const int* tile_start,
+                        const double* partials, const double* wpar, double* out) {
+  if (n_real <= 0) return cudaSuccess;
+  fold_kernel<<<n_real, kThreads, 0, st>>>(mode, tile_start, partials, wpar, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply(int mode, int n_tiles, cudaStream_t st, const RedTile* tiles,
+                         const RealDesc* rd, const RowGeoD* geod, T* state, AssimArgs aa,
+                         const double* factors) {
+  if (n_tiles <= 0) return cudaSuccess;
+  apply_kernel<T><<<n_tiles, kThreads, 0, st>>>(mode, tiles, rd, geod, state, aa, factors);
+  return cudaGetLastError();
+}
+
+#define SFT_INSTANTIATE(T)                                                                       \
+  template cudaError_t launch_rkl2_stage<T>(int, cudaStream_t, const Tile*, const RealDesc*,      \
+                                            const StepParam*, const RowGeo<T>*, const ShapeConst*, \
+                                            const Coef<T>*, T*, T*, T*, T*, int, int, int*);       \
+  template cudaError_t launch_adv_stage<T>(int, cudaStream_t, const Tile*, const RealDesc*,       \
+                                           const StepParam*, const RowGeo<T>*, const RowFlow<T>*, \
+                                           const ShapeConst*, T*, T*, T*, AdvStage<T>);           \
+  template cudaError_t launch_fix_poles<T>(int, cudaStream_t, const RealDesc*, T*, int);          \
+  template cudaError_t launch_reduce<T>(int, int, cudaStream_t, const RedTile*, const RealDesc*,  \
+                                        const RowGeoD*, const double*, const double*, const T*,   \
+                                        double, AssimArgs, double*);                              \
+  template cudaError_t launch_apply<T>(int, int, cudaStream_t, const RedTile*, const RealDesc*,   \
+                                       const RowGeoD*, T*, AssimArgs, const double*);
+
+SFT_INSTANTIATE(float)
+SFT_INSTANTIATE(double)
+
+}  // namespace sft

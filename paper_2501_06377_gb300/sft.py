@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libsft (include/sft.h).
+
+Argument marshalling only: every step of the SFT path runs in the CUDA
+kernels of libsft.so.  Loading fails loudly when the library is missing;
+there is no CPU fallback.
+
+Maps may be numpy arrays (host) or torch tensors (host or CUDA), row-major
+[ntheta][nphi] in the grid's precision.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsft.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "sft.h")
+
+SFT_OK, SFT_ERR_ARG, SFT_ERR_OOM, SFT_ERR_CUDA, SFT_ERR_UNSTABLE, SFT_ERR_TIMEOUT, SFT_ERR_STATE = range(7)
+STATUS_NAMES = {0: "SFT_OK", 1: "SFT_ERR_ARG", 2: "SFT_ERR_OOM", 3: "SFT_ERR_CUDA",
+                4: "SFT_ERR_UNSTABLE", 5: "SFT_ERR_TIMEOUT", 6: "SFT_ERR_STATE"}
+SFT_FP32, SFT_FP64 = 0, 1
+ADV_SPACE = {"weno3": 0, "upwind": 1}
+ADV_TIME = {"ssprk43": 0, "ssprk33": 1, "fe": 2}
+DIFFUSION = {"rkl2": 0, "off": 1}
+
+
+class SFTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class sft_shape(C.Structure):
+    _fields_ = [("ntheta", C.c_int32), ("nphi", C.c_int32)]
+
+
+class sft_flow_params(C.Structure):
+    _fields_ = [("d0", C.c_double), ("d2", C.c_double), ("d4", C.c_double),
+                ("m1", C.c_double), ("m3", C.c_double), ("m5", C.c_double),
+                ("nu", C.c_double), ("alpha_uw", C.c_double), ("cfl_safety", C.c_double),
+                ("eps_w", C.c_double), ("adv_space", C.c_int32), ("adv_time", C.c_int32),
+                ("diffusion", C.c_int32), ("advection", C.c_int32)]
+
+
+class sft_assim_params(C.Structure):
+    _fields_ = [("alpha_mu", C.c_double), ("mu_lim", C.c_double), ("lat_lim_deg", C.c_double),
+                ("flux_balance", C.c_int32), ("reserved", C.c_int32)]
+
+
+class sft_diag(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "flux_signed", "flux_pos", "flux_neg", "flux_pole_n", "flux_pole_s", "area_pole_n",
+        "area_pole_s", "brmin", "brmax", "absmin", "dipole_axial", "h1", "h2", "t_hours")] + [
+        ("steps", C.c_int64), ("nonfinite", C.c_int64)]
+
+
+class sft_stats(C.Structure):
+    _fields_ = [("global_steps", C.c_int64), ("realization_steps", C.c_int64),
+                ("cell_updates", C.c_double), ("adv_cell_stages", C.c_double),
+                ("diff_cell_stages", C.c_double), ("kernel_launches", C.c_int64),
+                ("graph_launches", C.c_int64), ("diff_ms", C.c_double), ("adv_ms", C.c_double),
+                ("diff_launches", C.c_int64), ("adv_launches", C.c_int64),
+                ("diff_bytes", C.c_double), ("adv_bytes", C.c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "sft_create_grid": (C.c_int, [C.POINTER(sft_shape), C.c_int32, C.c_int, C.c_size_t, C.c_void_p,
+                                  C.POINTER(C.c_void_p)]),
+    "sft_destroy": (C.c_int, [C.c_void_p]),
+    "sft_set_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "sft_get_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "sft_set_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "sft_get_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "sft_set_flows": (C.c_int, [C.c_void_p, C.POINTER(sft_flow_params)]),
+    "sft_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
+    "sft_assimilate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                 C.POINTER(sft_assim_params)]),
+    "sft_balance_flux": (C.c_int, [C.c_void_p]),
+    "sft_flux_diagnostics": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(sft_diag)]),
+    "sft_get_stats": (C.c_int, [C.c_void_p, C.POINTER(sft_stats)]),
+    "sft_reset_stats": (C.c_int, [C.c_void_p]),
+    "sft_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sft_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sft_set_tile_rows": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "sft_get_tile_rows": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "sft_wave_size": (C.c_int32, [C.c_void_p]),
+    "sft_step_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "sft_last_error": (C.c_char_p, [C.c_void_p]),
+    "sft_abi_version": (C.c_int32, []),
+}
+
+
+def header_functions(path=HEADER):
+    """Names of the functions declared in include/sft.h."""
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sft_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path=LIB_PATH):
+    """Load libsft.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsft.so not built (%s); run paper_2501_06377_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0, a
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0, a
+    raise TypeError("expected a numpy array or torch tensor, got %r" % type(a))
+
+
+@dataclass
+class FlowParams:
+    """Python view of sft_flow_params (Eq. dr, Eq. mf; nu in km^2/s)."""
+    d0: float = 46.0
+    d2: float = -262.0
+    d4: float = -379.0
+    m1: float = 22.0
+    m3: float = 11.0
+    m5: float = -28.0
+    nu: float = 500.0
+    alpha_uw: float = 1.0
+    cfl_safety: float = 0.9
+    eps_w: float = 0.0
+    adv_space: str = "weno3"
+    adv_time: str = "ssprk43"
+    diffusion: str = "rkl2"
+    advection: bool = True
+
+    def to_c(self):
+        return sft_flow_params(self.d0, self.d2, self.d4, self.m1, self.m3, self.m5, self.nu,
+                               self.alpha_uw, self.cfl_safety, self.eps_w,
+                               ADV_SPACE[self.adv_space], ADV_TIME[self.adv_time],
+                               DIFFUSION[self.diffusion], 1 if self.advection else 0)
+
+
+@dataclass
+class AssimParams:
+    alpha_mu: float = 4.0
+    mu_lim: float = 0.1
+    lat_lim_deg: float = 90.0
+    flux_balance: bool = True
+
+    def to_c(self):
+        return sft_assim_params(self.alpha_mu, self.mu_lim, self.lat_lim_deg,
+                                1 if self.flux_balance else 0, 0)
+
+
+class Grid:
+    """A batch of realizations (sft_create_grid ... sft_destroy)."""
+
+    def __init__(self, shapes, prec="fp32", hbm_budget=0, stream=None):
+        lib = load()
+        self.lib = lib
+        self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        self.n_real = len(self.shapes)
+        self.prec = prec
+        self.dtype = np.float32 if prec == "fp32" else np.float64
+        arr = (sft_shape * self.n_real)(*[sft_shape(a, b) for a, b in self.shapes])
+        h = C.c_void_p()
+        if stream is None:
+            s = None
+        elif isinstance(stream, int):
+            s = stream
+        else:
+            s = stream.cuda_stream
+        st = lib.sft_create_grid(arr, self.n_real, SFT_FP32 if prec == "fp32" else SFT_FP64,
+                                 int(hbm_budget), s, C.byref(h))
+        if st != SFT_OK:
+            raise SFTError(st, lib.sft_last_error(None).decode())
+        self.h = h
+
+    # -- helpers ---------------------------------------------------------
+    def _check(self, st):
+        if st != SFT_OK:
+            raise SFTError(st, self.lib.sft_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- C-ABI mirrors -----------------------------------------------------
+    def sft_set_state(self, r, br):
+        p, dev, keep = _ptr(br)
+        self._check(self.lib.sft_set_state(self.h, r, C.c_void_p(p), dev))
+        del keep
+
+    def set_state(self, r, br):
+        if isinstance(br, np.ndarray):
+            br = np.ascontiguousarray(br, dtype=self.dtype)
+        self.sft_set_state(r, br)
+
+    def get_state(self, r, out=None):
+        nt, np_ = self.shapes[r]
+        if out is None:
+            out = np.empty((nt, np_), dtype=self.dtype)
+        p, dev, _ = _ptr(out)
+        self._check(self.lib.sft_get_state(self.h, r, C.c_void_p(p), dev))
+        return out
+
+    def set_time(self, t):
+        self._check(self.lib.sft_set_time(self.h, float(t)))
+
+    def get_time(self):
+        out = (C.c_double * self.n_real)()
+        self._check(self.lib.sft_get_time(self.h, out))
+        return np.array(out[:])
+
+    def set_flows(self, params):
+        if isinstance(params, FlowParams):
+            params = [params] * self.n_real
+        arr = (sft_flow_params * self.n_real)(*[p.to_c() for p in params])
+        self._check(self.lib.sft_set_flows(self.h, arr))
+
+    def step(self, t_target, max_steps=0):
+        n = C.c_int32(0)
+        self._check(self.lib.sft_step(self.h, float(t_target), int(max_steps), C.byref(n)))
+        return n.value
+
+    def assimilate(self, obs, mu, per_realization, params):
+        if isinstance(params, AssimParams):
+            params = [params] * self.n_real
+        po, do, ko = _ptr(obs)
+        pm, dm, km = _ptr(mu)
+        if do != dm:
+            raise ValueError("obs and mu must both be on the host or both on the device")
+        arr = (sft_assim_params * self.n_real)(*[p.to_c() for p in params])
+        self._check(self.lib.sft_assimilate(self.h, C.c_void_p(po), C.c_void_p(pm),
+                                            1 if per_realization else 0, do, arr))
+        del ko, km
+
+    def balance_flux(self):
+        self._check(self.lib.sft_balance_flux(self.h))
+
+    def diagnostics(self, lat_cut_deg=60.0):
+        out = (sft_diag * self.n_real)()
+        self._check(self.lib.sft_flux_diagnostics(self.h, float(lat_cut_deg), out))
+        return [{f[0]: getattr(d, f[0]) for f in sft_diag._fields_} for d in out]
+
+    def stats(self):
+        s = sft_stats()
+        self._check(self.lib.sft_get_stats(self.h, C.byref(s)))
+        return {f[0]: getattr(s, f[0]) for f in sft_stats._fields_}
+
+    def reset_stats(self):
+        self._check(self.lib.sft_reset_stats(self.h))
+
+    def set_profiling(self, on):
+        self._check(self.lib.sft_set_profiling(self.h, 1 if on else 0))
+
+    def set_graphs(self, on):
+        self._check(self.lib.sft_set_graphs(self.h, 1 if on else 0))
+
+    def set_tile_rows(self, shape_id, rows):
+        self._check(self.lib.sft_set_tile_rows(self.h, shape_id, rows))
+
+    def get_tile_rows(self, shape_id):
+        return self.lib.sft_get_tile_rows(self.h, shape_id)
+
+    def wave_size(self):
+        return self.lib.sft_wave_size(self.h)
+
+    def step_plan(self, r, dt):
+        a, b, s = C.c_double(), C.c_double(), C.c_int32()
+        self._check(self.lib.sft_step_plan(self.h, r, float(dt), C.byref(a), C.byref(b), C.byref(s)))
+        return a.value, b.value, s.value
+
+
+__all__ = ["Grid", "FlowParams", "AssimParams", "SFTError", "load", "header_functions",
+           "LIB_PATH", "sft_flow_params", "sft_assim_params", "sft_diag", "sft_stats"]
+del fields

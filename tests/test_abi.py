@@ -1,0 +1,41 @@
+"""The C-ABI library builds, loads and exports every symbol include/sft.h
+declares; argument errors are reported without touching a GPU."""
+import ctypes as C
+
+import pytest
+
+from paper_2501_06377_gb300 import build as B
+from paper_2501_06377_gb300 import sft
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return sft.load()
+
+
+def test_every_header_function_is_exported(lib):
+    names = sft.header_functions()
+    assert len(names) >= 20
+    raw = C.CDLL(sft.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(lib):
+    assert set(sft.header_functions()) == set(sft._SIGS)
+
+
+def test_abi_version(lib):
+    assert lib.sft_abi_version() == 1
+
+
+def test_create_rejects_bad_arguments_before_any_cuda_call(lib):
+    h = C.c_void_p()
+    assert lib.sft_create_grid(None, 0, 0, 0, None, C.byref(h)) == sft.SFT_ERR_ARG
+    shp = (sft.sft_shape * 1)(sft.sft_shape(4, 64))   # ntheta < 5
+    assert lib.sft_create_grid(shp, 1, 0, 0, None, C.byref(h)) == sft.SFT_ERR_ARG
+    assert b"shape" in lib.sft_last_error(None)
+    shp = (sft.sft_shape * 1)(sft.sft_shape(16, 64))
+    assert lib.sft_create_grid(shp, 1, 7, 0, None, C.byref(h)) == sft.SFT_ERR_ARG
+    assert lib.sft_step(None, 1.0, 0, None) == sft.SFT_ERR_ARG
