@@ -158,7 +158,7 @@ def oracle_sample(n_stages=16):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    n_stages = 8
+    n_stages = 48
     vals, tot = [], 0.0
     for i in range(args.warmup + args.steps):
         v, ms, desc, el = oracle_sample(n_stages)
@@ -267,7 +267,7 @@ def run_gpu(args, rank, world, local_rank):
     bytes_state = nreal * NT * NP * 4
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cms, desc, el = oracle_sample(16)
+        v, cms, desc, el = oracle_sample(128)
         cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": desc}
     clocks = clk.summary()
     if rank == 0:

@@ -141,8 +141,9 @@ typedef struct {
  * buffers are sized for the largest group of realizations ("wave") that fits
  * the rest of the budget; sft_step then advances the waves one after another.
  * SFT_ERR_OOM if the budget cannot hold the state plus one realization's
- * work buffers.  cuda_stream is a cudaStream_t (NULL = legacy default
- * stream).  Maps start at zero and simulated times at 0 h.
+ * work buffers.  cuda_stream is the cudaStream_t all work is queued on; NULL
+ * makes the handle create its own blocking stream (ordered with the legacy
+ * default stream).  Maps start at zero and simulated times at 0 h.
  */
 sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec prec,
                            size_t hbm_budget_bytes, void* cuda_stream, sft_handle* out);
@@ -157,8 +158,9 @@ sft_status sft_set_state(sft_handle h, int32_t r, const void* br, int32_t on_dev
 /* Copy realization r's map out (caller layout [ntheta][nphi]). */
 sft_status sft_get_state(sft_handle h, int32_t r, void* br, int32_t on_device);
 
-/* Set the simulated time of every realization (hours). */
-sft_status sft_set_time(sft_handle h, double t_hours);
+/* Set the simulated time (hours) of realization r, or of every realization
+ * when r = -1 (checkpoint/resume). */
+sft_status sft_set_time(sft_handle h, int32_t r, double t_hours);
 
 /* Per-realization simulated times (host array of n_real doubles). */
 sft_status sft_get_time(sft_handle h, double* t_hours);

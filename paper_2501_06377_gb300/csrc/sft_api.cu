@@ -430,8 +430,14 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
 }
 
 // The launches of one step (advection stages, then RKL2 stages).
+// Record a profiling event; under stream capture it must be an external
+// event node (a plain record would only mark a capture dependency).
+cudaError_t record(cudaEvent_t e, cudaStream_t st, bool capturing) {
+  return capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+}
+
 template <typename T>
-sft_status enqueue_step(sft_handle h, Config& c, bool record_events) {
+sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool capturing) {
   const cudaStream_t st = h->stream;
   T* B = ptr<T>(h->state);
   T* W0 = ptr<T>(h->work[0]);
@@ -444,7 +450,7 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events) {
     adv_time = ri.fp.adv_time;
     break;
   }
-  if (record_events) SFT_CUDA(h, cudaEventRecord(h->ev[0], st));
+  if (record_events) SFT_CUDA(h, record(h->ev[0], st, capturing));
   if (c.n_adv_tiles > 0) {
     std::vector<AdvStage<T>> stages;
     auto S = [&](const T* fin, int finw, const T* fn, int fnw, T* out, int outw, double a, double b,
@@ -470,15 +476,15 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events) {
     }
   }
   if (record_events) {
-    SFT_CUDA(h, cudaEventRecord(h->ev[1], st));
-    SFT_CUDA(h, cudaEventRecord(h->ev[2], st));
+    SFT_CUDA(h, record(h->ev[1], st, capturing));
+    SFT_CUDA(h, record(h->ev[2], st, capturing));
   }
   for (int j = 1; j <= c.smax; ++j) {
     SFT_CUDA(h, launch_rkl2_stage<T>(c.stage_tiles[j], st, c.d_tiles, h->d_desc, c.d_sp, geo,
                                      h->d_shc, ptr<const Coef<T>>(c.d_coef), B, W0, W1, W2, j, 1,
                                      h->d_status));
   }
-  if (record_events) SFT_CUDA(h, cudaEventRecord(h->ev[3], st));
+  if (record_events) SFT_CUDA(h, record(h->ev[3], st, capturing));
   return SFT_OK;
 }
 
@@ -535,7 +541,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     if (!c->exec) {
       cudaGraph_t g = nullptr;
       SFT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-      sft_status st = enqueue_step<T>(h, *c, true);
+      sft_status st = enqueue_step<T>(h, *c, true, true);
       cudaError_t e = cudaStreamEndCapture(h->stream, &g);
       if (st != SFT_OK) {
         if (g) cudaGraphDestroy(g);
@@ -549,7 +555,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     SFT_CUDA(h, cudaGraphLaunch(c->exec, h->stream));
     h->stats.graph_launches += 1;
   } else {
-    sft_status st = enqueue_step<T>(h, *c, ev);
+    sft_status st = enqueue_step<T>(h, *c, ev, false);
     if (st != SFT_OK) return st;
   }
   const int n_adv = c->n_adv_tiles > 0 ? adv_stage_count(h) : 0;
@@ -939,9 +945,12 @@ sft_status sft_get_state(sft_handle h, int32_t r, void* br, int32_t on_device) {
   return SFT_OK;
 }
 
-sft_status sft_set_time(sft_handle h, double t_hours) {
+sft_status sft_set_time(sft_handle h, int32_t r, double t_hours) {
   if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
-  for (auto& r : h->reals) r.t = t_hours;
+  if (r < -1 || r >= h->n_real) return fail(h, SFT_ERR_ARG, "realization index out of range");
+  if (!std::isfinite(t_hours)) return fail(h, SFT_ERR_ARG, "time must be finite");
+  for (int i = 0; i < h->n_real; ++i)
+    if (r < 0 || i == r) h->reals[i].t = t_hours;
   return SFT_OK;
 }
 

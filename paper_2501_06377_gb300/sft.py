@@ -76,7 +76,7 @@ _SIGS = {
     "sft_destroy": (C.c_int, [C.c_void_p]),
     "sft_set_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
     "sft_get_state": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
-    "sft_set_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "sft_set_time": (C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
     "sft_get_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "sft_set_flows": (C.c_int, [C.c_void_p, C.POINTER(sft_flow_params)]),
     "sft_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
@@ -234,6 +234,8 @@ class Grid:
         self.sft_set_state(r, br)
 
     def get_state(self, r, out=None):
+        if not 0 <= r < self.n_real:   # let the library report the bad index
+            self._check(self.lib.sft_get_state(self.h, r, None, 0))
         nt, np_ = self.shapes[r]
         if out is None:
             out = np.empty((nt, np_), dtype=self.dtype)
@@ -241,8 +243,14 @@ class Grid:
         self._check(self.lib.sft_get_state(self.h, r, C.c_void_p(p), dev))
         return out
 
-    def set_time(self, t):
-        self._check(self.lib.sft_set_time(self.h, float(t)))
+    def set_time(self, t, r=-1):
+        """Set realization r's time (all when r = -1); t may be a sequence of
+        per-realization times."""
+        if np.ndim(t) == 0:
+            self._check(self.lib.sft_set_time(self.h, int(r), float(t)))
+        else:
+            for i, ti in enumerate(t):
+                self._check(self.lib.sft_set_time(self.h, i, float(ti)))
 
     def get_time(self):
         out = (C.c_double * self.n_real)()
