@@ -178,3 +178,20 @@ def test_phi_advection_order_rigid_rotation(space, eps, lo, hi):
     assert lo <= order <= hi, order
     if space == "weno3" and eps == "h":
         assert e2 < _phi_error(512, "weno3", 1e-12)
+
+
+def test_flow_profiles_closed_forms():
+    """Eq. (dr) with d_i from a rotation rate Omega(lat) = o0 + o2 sin^2 + o4 sin^4
+    (deg/day, relative to a frame) is v_phi = (Omega - frame) * pi/180/24 * sin(theta)
+    in R_sun/hr; Eq. (mf) with m1 = 2U, m3 = m5 = 0 is -U sin(2 theta) (m/s)."""
+    g = O.Grid(37, 72)
+    o = (13.38, -2.30, -1.62)
+    frame = 360.0 / 27.2753
+    d = I.omega_to_dr_coeffs(*o, frame_deg_day=frame)
+    vt, vp = O.flow_profiles(g, d[0], d[1], d[2], 30.0, 0.0, 0.0)
+    lat = g.lat
+    omega = o[0] + o[1] * np.sin(lat) ** 2 + o[2] * np.sin(lat) ** 4 - frame
+    np.testing.assert_allclose(vp, omega * math.pi / 180 / 24 * g.sin_t, rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(vt, -15.0 * np.sin(2 * g.theta_h) * O.M_S_TO_RS_HR, rtol=1e-12, atol=1e-20)
+    # poleward: negative (toward theta = 0) in the north, positive in the south
+    assert vt[: (g.nt - 1) // 2].max() < 0 < vt[(g.nt - 1) // 2:].min()
