@@ -236,8 +236,36 @@ int32_t sft_wave_size(sft_handle h);
 sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cfl, double* dt_euler,
                          int32_t* stages);
 
+/*
+ * Flux diagnostics of one map that the caller keeps in its own device memory,
+ * without allocating any device memory.  No counterpart in the paper: this
+ * exists for callers that cannot call cudaMalloc while they run (a solver
+ * coupled into a model that has already reserved the device memory through
+ * its own pool, or a real-time pipeline that forbids allocation after
+ * start-up because cudaMalloc can stall the device).
+ *
+ * br_device: device pointer to a [ntheta][nphi] map (pitch nphi) in
+ * precision prec; the grid convention is that of every other call.  The
+ * result (the sft_diag of sft_flux_diagnostics, with t_hours = steps = 0) is
+ * written to the host struct *out; the call synchronises cuda_stream (NULL =
+ * legacy default stream).
+ * Scratch: one fixed file-scope device array of SFT_NOALLOC_SCRATCH_BYTES
+ * (held by every GPU that loads the library until the process exits).  A map
+ * whose tables and partial sums do not fit is rejected with SFT_ERR_ARG
+ * (roughly up to 8192 x 16384).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU race; errors are reported through
+ * sft_last_error(NULL).
+ */
+#define SFT_NOALLOC_SCRATCH_BYTES (4u << 20)
+sft_status sft_flux_diagnostics_noalloc(const void* br_device, int32_t ntheta, int32_t nphi,
+                                        sft_prec prec, double lat_cut_deg, void* cuda_stream,
+                                        sft_diag* out);
+
 /* One-line description of the last error on h (or of the last failed
- * sft_create_grid when h is NULL).  Valid until the next call on h. */
+ * sft_create_grid or handle-free call when h is NULL).  Valid until the next
+ * call on h. */
 const char* sft_last_error(sft_handle h);
 
 /* SFT_ABI_VERSION of the loaded library. */

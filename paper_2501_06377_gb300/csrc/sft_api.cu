@@ -760,6 +760,11 @@ sft_status reduce_fold(sft_handle h, int mode, double lat_cut, AssimArgs aa) {
 
 }  // namespace
 
+namespace sft {
+// Error text of calls without a handle (read by sft_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace sft
+
 // ===========================================================================
 // C-ABI
 // ===========================================================================

@@ -93,6 +93,8 @@ _SIGS = {
     "sft_wave_size": (C.c_int32, [C.c_void_p]),
     "sft_step_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "sft_flux_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int,
+                                               C.c_double, C.c_void_p, C.POINTER(sft_diag)]),
     "sft_last_error": (C.c_char_p, [C.c_void_p]),
     "sft_abi_version": (C.c_int32, []),
 }
@@ -317,6 +319,23 @@ class Grid:
         return a.value, b.value, s.value
 
 
-__all__ = ["Grid", "FlowParams", "AssimParams", "SFTError", "load", "header_functions",
+def flux_diagnostics_noalloc(br, lat_cut_deg=60.0, stream=None):
+    """sft_flux_diagnostics_noalloc on a contiguous CUDA tensor [ntheta][nphi]
+    (float32 or float64).  Allocates no device memory."""
+    lib = load()
+    import torch
+    if not (isinstance(br, torch.Tensor) and br.is_cuda and br.is_contiguous() and br.dim() == 2):
+        raise TypeError("expected a contiguous 2-D CUDA tensor")
+    prec = {torch.float32: SFT_FP32, torch.float64: SFT_FP64}[br.dtype]
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    out = sft_diag()
+    st = lib.sft_flux_diagnostics_noalloc(C.c_void_p(br.data_ptr()), br.shape[0], br.shape[1], prec,
+                                          float(lat_cut_deg), s, C.byref(out))
+    if st != SFT_OK:
+        raise SFTError(st, lib.sft_last_error(None).decode())
+    return {f[0]: getattr(out, f[0]) for f in sft_diag._fields_}
+
+
+__all__ = ["flux_diagnostics_noalloc", "Grid", "FlowParams", "AssimParams", "SFTError", "load", "header_functions",
            "LIB_PATH", "sft_flow_params", "sft_assim_params", "sft_diag", "sft_stats"]
 del fields

@@ -39,3 +39,15 @@ def test_create_rejects_bad_arguments_before_any_cuda_call(lib):
     shp = (sft.sft_shape * 1)(sft.sft_shape(16, 64))
     assert lib.sft_create_grid(shp, 1, 7, 0, None, C.byref(h)) == sft.SFT_ERR_ARG
     assert lib.sft_step(None, 1.0, 0, None) == sft.SFT_ERR_ARG
+
+
+def test_noalloc_rejects_oversized_maps_before_any_cuda_call(lib):
+    """The size check of sft_flux_diagnostics_noalloc comes before any CUDA
+    call, so it is checked here without a GPU (no map is ever read)."""
+    out = sft.sft_diag()
+    fake = C.c_void_p(256)   # never dereferenced: the call must stop at the size check
+    big = 1 << 20            # tables alone need 32 MiB >> the 4 MiB scratch
+    assert lib.sft_flux_diagnostics_noalloc(fake, big, big, 0, 60.0, None, C.byref(out)) == sft.SFT_ERR_ARG
+    assert b"scratch" in lib.sft_last_error(None)
+    assert lib.sft_flux_diagnostics_noalloc(fake, 64, 7, 0, 60.0, None, C.byref(out)) == sft.SFT_ERR_ARG
+    assert lib.sft_flux_diagnostics_noalloc(None, 64, 128, 0, 60.0, None, C.byref(out)) == sft.SFT_ERR_ARG
