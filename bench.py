@@ -282,8 +282,11 @@ def run_gpu(args, rank, world, local_rank):
                        "cell_stage_updates_per_s": (st["diff_cell_stages"] + st["adv_cell_stages"])
                        * world / (ms * 1e-3),
                        "rkl2_stages_per_step": st["diff_cell_stages"] / max(st["cell_updates"], 1),
-                       "graph": True},
-            "roofline": {"bound": "hbm", "kernel": "rkl2_stage_kernel<float>", "achieved": achieved,
+                       "graph": True, "rkl2_stages_per_launch": g.get_fusion()},
+            "roofline": {"bound": "hbm",
+                         "kernel": ("rkl2_fused_kernel (4 RKL2 stages per launch)" if g.get_fusion() == 4
+                                    else "rkl2_stage_kernel<float>"),
+                         "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind + " hbm_gbs",
                          "bytes_per_launch": diff_launch_bytes, "ms_per_launch": diff_launch_ms,

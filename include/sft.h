@@ -220,6 +220,16 @@ sft_status sft_set_profiling(sft_handle h, int32_t profile);
  * distinct step configuration; 0: plain launches. */
 sft_status sft_set_graphs(sft_handle h, int32_t use_graphs);
 
+/* RKL2 stages per kernel launch: 1 (one launch per stage) or 4 (temporal
+ * blocking: four stages per pass through HBM, shared-memory tiles with a
+ * four-point halo and full-ring cap blocks).  The fused path needs FP32 and
+ * every grid with ntheta >= 20 and nphi >= 16; it is the default when
+ * available.  Both paths evaluate the same per-point formulas. */
+sft_status sft_set_fusion(sft_handle h, int32_t stages_per_pass);
+
+/* Current RKL2 stages per launch (1 or 4). */
+int32_t sft_get_fusion(sft_handle h);
+
 /* Tile rows per block of the stage kernels for realizations of shape index
  * shape_id (order of first appearance in shapes[]); 0 lets the built-in
  * autotuner choose on the first step.  Valid values: 1, 2, 4, 8. */

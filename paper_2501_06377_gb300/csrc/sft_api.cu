@@ -61,6 +61,9 @@ struct RealInfo {
 };
 
 struct Config {
+  bool fused = false;            // built for the fused RKL2 path
+  Tile* d_ftiles = nullptr;      // fused-kernel tiles (caps first, then interior)
+  std::vector<int> fused_tiles;  // [j0] = fused tiles launched by the pass starting at stage j0
   std::vector<double> dt;        // per wave member (wave order)
   std::vector<int> s;            // per wave member
   std::vector<int> tr;           // tile rows per shape at build time
@@ -103,7 +106,12 @@ struct sft_grid {
   int64_t state_elems = 0, work_elems = 0;
   // device memory
   void* state = nullptr;
-  void* work[3] = {nullptr, nullptr, nullptr};
+  void* work[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int n_work = 3;              // 5 when the fused RKL2 path is possible
+  bool fused_ok = false;       // FP32 and every shape has an interior band
+  bool fused = false;          // use rkl2_fused_kernel (K stages per launch)
+  void* polar = nullptr;       // cap-block scratch of the fused path
+  int64_t polar_elems = 0;
   RealDesc* d_desc = nullptr;
   ShapeConst* d_shc = nullptr;
   void* d_geo = nullptr;       // RowGeo<T>
@@ -280,6 +288,8 @@ template <typename T> T* ptr(void* p) { return static_cast<T*>(p); }
 
 void free_config(Config& c) {
   if (c.exec) cudaGraphExecDestroy(c.exec);
+  cudaFree(c.d_ftiles);
+  c.d_ftiles = nullptr;
   cudaFree(c.d_tiles);
   cudaFree(c.d_sp);
   cudaFree(c.d_coef);
@@ -296,6 +306,7 @@ void free_handle(sft_handle h) {
     for (auto& c : w.configs) free_config(*c);
   cudaFree(h->state);
   for (auto& w : h->work) cudaFree(w);
+  cudaFree(h->polar);
   cudaFree(h->d_desc);
   cudaFree(h->d_shc);
   cudaFree(h->d_geo);
@@ -351,6 +362,16 @@ void append_tiles(const sft_grid* h, int r, int tr, std::vector<Tile>& tiles) {
   tiles.push_back(Tile{r, 0, 0, 2});
 }
 
+void append_fused_tiles(const sft_grid* h, int r, std::vector<Tile>& tiles) {
+  const ShapeInfo& s = h->shapes[h->reals[r].shape];
+  tiles.push_back(Tile{r, 0, 0, 1});
+  tiles.push_back(Tile{r, 0, 0, 2});
+  // interior: (band, strip) work items, one per warp, WARPS per block
+  const int n_strips = (s.np + fused::STRIP - 1) / fused::STRIP;
+  const int n_bands = (s.nt - 2 - 2 * fused::PB + fused::BAND - 1) / fused::BAND;
+  for (int i0 = 0; i0 < n_bands * n_strips; i0 += fused::WARPS) tiles.push_back(Tile{r, i0, 0, 0});
+}
+
 template <typename T>
 sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
                         const std::vector<int>& s, Config** out) {
@@ -395,6 +416,33 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     c->smax = std::max(c->smax, s[i]);
   }
   c->realization_steps = (int)order.size();
+  c->fused = h->fused;
+  if (c->fused) {
+    // fused passes start at stages 2, 2+K, 2+2K, ...; stage 1 uses the
+    // single-stage kernel (it forms G = dt L(Y_0)).
+    std::vector<Tile> ft;
+    std::vector<int> fend;
+    for (int i : order) {
+      append_fused_tiles(h, w.reals[i], ft);
+      fend.push_back((int)ft.size());
+    }
+    c->fused_tiles.assign(c->smax + 1, 0);
+    for (int j0 = 2; j0 <= c->smax; j0 += fused::K) {
+      int n = 0;
+      while (n < (int)order.size() && s[order[n]] >= j0) ++n;
+      c->fused_tiles[j0] = n == 0 ? 0 : fend[n - 1];
+    }
+    c->diff_words = 0.0;
+    for (int i : order) {
+      const ShapeInfo& sh = h->shapes[h->reals[w.reals[i]].shape];
+      if (s[i] > 0) c->diff_words += (double)sh.nt * sh.np * (3.0 + 5.0 * ((s[i] - 1 + fused::K - 1) / fused::K));
+    }
+    if (!ft.empty()) {
+      SFT_CUDA(h, cudaMalloc(&c->d_ftiles, ft.size() * sizeof(Tile)));
+      SFT_CUDA(h, cudaMemcpyAsync(c->d_ftiles, ft.data(), ft.size() * sizeof(Tile),
+                                  cudaMemcpyHostToDevice, h->stream));
+    }
+  }
   c->n_adv_tiles = tile_end.empty() ? 0 : tile_end.back();
   c->stage_tiles.assign(c->smax + 1, 0);
   for (int j = 1; j <= c->smax; ++j) {
@@ -479,10 +527,30 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
     SFT_CUDA(h, record(h->ev[1], st, capturing));
     SFT_CUDA(h, record(h->ev[2], st, capturing));
   }
-  for (int j = 1; j <= c.smax; ++j) {
-    SFT_CUDA(h, launch_rkl2_stage<T>(c.stage_tiles[j], st, c.d_tiles, h->d_desc, c.d_sp, geo,
-                                     h->d_shc, ptr<const Coef<T>>(c.d_coef), B, W0, W1, W2, j, 1,
+  if (c.fused && c.smax >= 1) {
+    // stage 1 (forms G and delta_1 = W2), then passes of K stages that
+    // alternate between the increment pairs (W1, W2) and (W3, W4)
+    SFT_CUDA(h, launch_rkl2_stage<T>(c.stage_tiles[1], st, c.d_tiles, h->d_desc, c.d_sp, geo,
+                                     h->d_shc, ptr<const Coef<T>>(c.d_coef), B, W0, W1, W2, 1, 1,
                                      h->d_status));
+    float* P[4] = {ptr<float>(h->work[1]), ptr<float>(h->work[2]), ptr<float>(h->work[3]),
+                   ptr<float>(h->work[4])};
+    int in = 0;  // input pair (P[in], P[in+1]) = (delta_{j0-2}, delta_{j0-1})
+    for (int j0 = 2; j0 <= c.smax; j0 += fused::K) {
+      const int out = 2 - in;
+      SFT_CUDA(h, launch_rkl2_fused(c.fused_tiles[j0], st, c.d_ftiles, h->d_desc, c.d_sp,
+                                    ptr<const RowGeo<float>>(h->d_geo), h->d_shc,
+                                    ptr<const Coef<float>>(c.d_coef), ptr<float>(h->state),
+                                    ptr<const float>(h->work[0]), P[in], P[in + 1], P[out],
+                                    P[out + 1], ptr<float>(h->polar), j0, h->d_status));
+      in = out;
+    }
+  } else {
+    for (int j = 1; j <= c.smax; ++j) {
+      SFT_CUDA(h, launch_rkl2_stage<T>(c.stage_tiles[j], st, c.d_tiles, h->d_desc, c.d_sp, geo,
+                                       h->d_shc, ptr<const Coef<T>>(c.d_coef), B, W0, W1, W2, j, 1,
+                                       h->d_status));
+    }
   }
   if (record_events) SFT_CUDA(h, record(h->ev[3], st, capturing));
   return SFT_OK;
@@ -524,7 +592,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     }
   Config* c = nullptr;
   for (auto& cfg : w.configs) {
-    bool same = cfg->dt == dt && cfg->s == s;
+    bool same = cfg->dt == dt && cfg->s == s && cfg->fused == h->fused;
     for (size_t i = 0; same && i < h->shapes.size(); ++i) same = cfg->tr[i] == h->shapes[i].tile_rows;
     if (same) {
       c = cfg.get();
@@ -559,7 +627,8 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     if (st != SFT_OK) return st;
   }
   const int n_adv = c->n_adv_tiles > 0 ? adv_stage_count(h) : 0;
-  h->stats.kernel_launches += n_adv + c->smax;
+  const int n_diff = c->fused ? (c->smax >= 1 ? 1 + (c->smax - 1 + fused::K - 1) / fused::K : 0) : c->smax;
+  h->stats.kernel_launches += n_adv + n_diff;
   h->stats.realization_steps += c->realization_steps;
   h->stats.cell_updates += c->cell_updates;
   h->stats.adv_cell_stages += c->cells_adv * (adv_stage_count(h) == 2 ? 1 : adv_stage_count(h));
@@ -573,7 +642,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     h->stats.adv_ms += a;
     h->stats.diff_ms += d;
     h->stats.adv_launches += n_adv;
-    h->stats.diff_launches += c->smax;
+    h->stats.diff_launches += n_diff;
     const double eb = (double)h->elem;
     // Algorithmic bytes.  RKL2: stage 1 reads B, writes G and delta_1 (3
     // words); stage 2 reads delta_1, G, writes delta_2 (3); middle stages
@@ -830,6 +899,12 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
     ri.off = h->state_elems;
     h->state_elems += ri.cells;
   }
+  // The fused RKL2 path (FP32, every shape with an interior band) needs two
+  // more increment arrays and a small cap-block scratch.
+  h->fused_ok = prec == SFT_FP32;
+  for (auto& s : h->shapes) h->fused_ok = h->fused_ok && fused::shape_ok(s.nt, s.np);
+  h->fused = h->fused_ok;
+  h->n_work = h->fused_ok ? 5 : 3;
   // HBM admission: the state stays resident; work arrays hold one wave.
   const int64_t state_bytes = h->state_elems * (int64_t)h->elem;
   int64_t avail = INT64_MAX;
@@ -842,11 +917,12 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
     int64_t used = 0;  // bytes per work array in the current wave
     for (int r = 0; r < n_real; ++r) {
       const int64_t per_array = h->reals[r].cells * (int64_t)h->elem;
-      if (3 * per_array > avail) {
+      const int64_t nw = h->n_work;
+      if (nw * per_array > avail) {
         h->err = "HBM budget too small for one realization's work buffers";
         return bail(SFT_ERR_OOM);
       }
-      if (3 * (used + per_array) > avail && !cur.reals.empty()) {
+      if (nw * (used + per_array) > avail && !cur.reals.empty()) {
         h->waves.push_back(std::move(cur));
         cur = Wave();
         used = 0;
@@ -863,9 +939,24 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   }
   CREATE_CUDA(cudaMalloc(&h->state, state_bytes));
   CREATE_CUDA(cudaMemsetAsync(h->state, 0, state_bytes, h->stream));
-  for (auto& w : h->work) {
-    CREATE_CUDA(cudaMalloc(&w, std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem));
-    CREATE_CUDA(cudaMemsetAsync(w, 0, std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem, h->stream));
+  for (int i = 0; i < h->n_work; ++i) {
+    CREATE_CUDA(cudaMalloc(&h->work[i], std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem));
+    CREATE_CUDA(cudaMemsetAsync(h->work[i], 0, std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem,
+                                h->stream));
+  }
+  std::vector<int32_t> poff(n_real, 0);
+  if (h->fused_ok) {
+    // cap scratch: 2 caps x 2 levels x NB rows per realization, per wave
+    for (auto& w : h->waves) {
+      int64_t used = 0;
+      for (int r : w.reals) {
+        poff[r] = (int32_t)used;
+        used += 4ll * fused::NB * h->shapes[h->reals[r].shape].pitch;
+      }
+      h->polar_elems = std::max(h->polar_elems, used);
+    }
+    CREATE_CUDA(cudaMalloc(&h->polar, std::max<int64_t>(h->polar_elems, 32) * sizeof(float)));
+    CREATE_CUDA(prepare_rkl2_fused());
   }
   sft_status st = prec == SFT_FP32 ? upload_tables<float>(h) : upload_tables<double>(h);
   if (st != SFT_OK) return bail(st);
@@ -873,7 +964,7 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   for (int r = 0; r < n_real; ++r) {
     const RealInfo& ri = h->reals[r];
     const ShapeInfo& s = h->shapes[ri.shape];
-    desc[r] = RealDesc{ri.off, ri.woff, s.nt, s.np, s.pitch, ri.shape, s.geo, ri.flow_row, s.col, 0};
+    desc[r] = RealDesc{ri.off, ri.woff, s.nt, s.np, s.pitch, ri.shape, s.geo, ri.flow_row, s.col, poff[r]};
   }
   CREATE_CUDA(cudaMalloc(&h->d_desc, desc.size() * sizeof(RealDesc)));
   CREATE_CUDA(cudaMemcpy(h->d_desc, desc.data(), desc.size() * sizeof(RealDesc), cudaMemcpyHostToDevice));
@@ -1175,6 +1266,19 @@ sft_status sft_set_graphs(sft_handle h, int32_t use_graphs) {
   h->use_graphs = use_graphs != 0;
   return SFT_OK;
 }
+
+sft_status sft_set_fusion(sft_handle h, int32_t stages_per_pass) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (stages_per_pass != 1 && stages_per_pass != fused::K)
+    return fail(h, SFT_ERR_ARG, "stages per pass must be 1 or " + std::to_string(fused::K));
+  if (stages_per_pass == fused::K && !h->fused_ok)
+    return fail(h, SFT_ERR_ARG, "fused RKL2 needs FP32 and grids with ntheta >= " +
+                                    std::to_string(2 * fused::NB + 2) + ", nphi >= 16");
+  h->fused = stages_per_pass == fused::K;
+  return SFT_OK;
+}
+
+int32_t sft_get_fusion(sft_handle h) { return h ? (h->fused ? fused::K : 1) : 0; }
 
 sft_status sft_set_tile_rows(sft_handle h, int32_t shape_id, int32_t rows) {
   if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");

@@ -33,7 +33,7 @@ struct RealDesc {
   int32_t geo;     // first row of the shape's geometry table
   int32_t flow;    // first row of this realization's flow table
   int32_t col;     // first entry of the shape's cos/sin(phi_k) tables
-  int32_t pad;
+  int32_t poff;    // element offset of this realization's polar-band scratch (fused RKL2)
 };
 
 // Per-row geometry of a shape (uniform grid, Sec. 3.2).
@@ -118,6 +118,30 @@ cudaError_t launch_adv_stage(int n_tiles, cudaStream_t st, const Tile* tiles, co
                              const StepParam* sp, const RowGeo<T>* geo, const RowFlow<T>* flow,
                              const ShapeConst* shc, T* state, T* work_base0, T* work_base1,
                              AdvStage<T> s);
+// Fused RKL2: K stages per launch (see rkl2_fused_kernel in sft_kernels.cu).
+namespace fused {
+constexpr int K = 4;             // RKL2 stages per pass
+constexpr int BAND = 64;         // rows of one interior band (a warp marches through it)
+constexpr int LANES = 32;
+constexpr int STRIP = 4 * LANES - 2 * K;   // output columns of one warp strip (lanes 1..30)
+constexpr int WARPS = 8;         // strips per block
+constexpr int PB = K;            // rows next to each pole owned by the cap blocks
+constexpr int NB = PB + K + 1;   // rows a cap block holds (pole row + PB + K halo rows)
+// A grid shape can use the fused path when the interior band is non-empty.
+inline bool shape_ok(int nt, int np) { return nt >= 2 * NB + 2 && np >= 16; }
+}  // namespace fused
+
+// Stages j0 .. j0+K-1 of every realization with s >= j0 (fewer, ending with
+// the final write B += delta_s, for a realization whose s ends inside the
+// pass).  Reads delta_{j0-2} (Dm2, zero when j0 == 2), delta_{j0-1} (Dm1), G;
+// writes delta_{j0+K-2} (Om2) and delta_{j0+K-1} (Om1).
+cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                              const StepParam* sp, const RowGeo<float>* geo, const ShapeConst* shc,
+                              const Coef<float>* coef, float* B, const float* G, const float* Dm2,
+                              const float* Dm1, float* Om2, float* Om1, float* polar, int j0,
+                              int* status);
+cudaError_t prepare_rkl2_fused();
+
 template <typename T>
 cudaError_t launch_fix_poles(int n_real, cudaStream_t st, const RealDesc* rd, T* state, int only_r);
 

@@ -417,6 +417,355 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
   Vec<T>::st(out + ro + kc, o);
 }
 
+// ---------------------------------------------------------------------------
+// Fused RKL2 (temporal blocking): fused::K stages per launch, FP32.
+//
+// Interior: one warp owns a strip of 128 longitudes (a float4 per lane) and
+// marches down a band of rows.  For every RKL2 level (the two inputs
+// delta_{j-2}, delta_{j-1} and the K levels it computes) the lane keeps a
+// rolling window of three rows in registers; at each row step it loads one
+// new row of the inputs and computes level m at the row m above, so level K
+// leaves the pipeline K rows behind the loads.  phi neighbours come from
+// warp shuffles.  Lanes 0 and 31 are the K-point phi halo and the first and
+// last K rows of the band the theta halo: their values go stale from the
+// edge inward, one point per level, and are never stored.  No shared
+// memory, no barriers.
+// Caps: the NB = PB + K + 1 rows next to each pole, full ring width, in an
+// L2-resident global scratch, with the FP64 ring sum of App. A done by the
+// block at every level (the only place that needs the whole ring).
+// Interior bands start at row PB+1 = K+1, so their halo never reaches a pole.
+// HBM traffic per pass: read delta_{j-2}, delta_{j-1}, G, write two
+// increments: 20 B per cell per K stages instead of 16 B per stage.
+// The per-point arithmetic is written exactly as in rkl2_stage_kernel.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float rkl2_point(const RowGeo<float>& g, const Coef<float>& cf, float mutdt,
+                                            float c, float up, float dn, float l, float r, float d2,
+                                            float gv) {
+  const float L = g.cN * (up - c) + g.cS * (dn - c) + g.cE * ((l - c) + (r - c));
+  return cf.mu * c + cf.nu * d2 + mutdt * L + cf.gsum * gv;
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// Four consecutive longitudes starting at column c0 (periodic), as a float4.
+__device__ __forceinline__ float4 load_cols(const float* row, int c0, int np, bool vec) {
+  if (vec) return ldg4(row + c0);
+  float v[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    int c = c0 + e;
+    c = c >= np ? c - np : c;
+    v[e] = __ldg(row + c);
+  }
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// One level update of a lane's 4 points; l/r neighbours across lanes.
+// The 5-point operator and the increment-form RKL2 combination are folded
+// into per-row coefficients:  o = a0 c + a1 up + a2 dn + a3 (l + r)
+// + nu d2 + gsum G  with a1..a3 = mu~ nu dt (cN, cS, cE) and
+// a0 = mu - mu~ nu dt (cN + cS + 2 cE)  (the same stage, other rounding).
+struct RowCoef {
+  float a0, a1, a2, a3, nu, gs;
+};
+
+__device__ __forceinline__ RowCoef row_coef(const RowGeo<float>& g, const Coef<float>& cf, float nudt) {
+  const float md = cf.mut * nudt;
+  RowCoef k;
+  k.a1 = md * g.cN;
+  k.a2 = md * g.cS;
+  k.a3 = md * g.cE;
+  k.a0 = cf.mu - (k.a1 + k.a2 + 2.f * k.a3);
+  k.nu = cf.nu;
+  k.gs = cf.gsum;
+  return k;
+}
+
+__device__ __forceinline__ float point2(const RowCoef& k, float c, float up, float dn, float l, float r,
+                                        float d2, float gv) {
+  return fmaf(k.a0, c, fmaf(k.a1, up, fmaf(k.a2, dn, fmaf(k.a3, l + r, fmaf(k.nu, d2, k.gs * gv)))));
+}
+
+__device__ __forceinline__ float4 level_update(const RowCoef& k, float4 c, float4 up, float4 dn, float4 d2,
+                                               float4 gv) {
+  const float l = __shfl_up_sync(0xffffffffu, c.w, 1);
+  const float r = __shfl_down_sync(0xffffffffu, c.x, 1);
+  float4 o;
+  o.x = point2(k, c.x, up.x, dn.x, l, c.y, d2.x, gv.x);
+  o.y = point2(k, c.y, up.y, dn.y, c.x, c.z, d2.y, gv.y);
+  o.z = point2(k, c.z, up.z, dn.z, c.y, c.w, d2.z, gv.z);
+  o.w = point2(k, c.w, up.w, dn.w, c.z, r, d2.w, gv.w);
+  return o;
+}
+
+// Lane state of the interior march.  Win[l][slot] holds level l (0..K-1) at
+// the row whose index mod 3 is slot; level l's window holds rows t-l-2..t-l.
+// The level j-2 input is only needed pointwise one row later (d2m1), level K
+// only at its output step, and the next row's inputs are prefetched one row
+// ahead (pc, pa, pg) so their latency overlaps a whole row of arithmetic.
+struct March {
+  float4 Win[fused::K][3];
+  float4 d2m1;      // delta_{j-2} at row t-1
+  float4 g1;        // G at row t-1
+  float4 pc, pa, pg;  // inputs of row t (prefetched during step t-1)
+};
+
+template <int P>
+__device__ __forceinline__ void march_row(March& S, int t, int kk, int tmin, int t_end, const float* gA,
+                                          const float* gC, const float* gG, const RowGeo<float>* geo,
+                                          const Coef<float> (&cf)[fused::K], float nudt, int pitch, int np,
+                                          int col, bool vec, bool zero_m2, int J0, int J1, bool fin,
+                                          float* oA, float* oC, float* Bs, bool lane_out, int n_out,
+                                          bool& bad) {
+  using namespace fused;
+  // this row's inputs arrived during the previous step
+  S.Win[0][P] = S.pc;
+  const float4 a_t = S.pa, g_t = S.pg;
+  if (t + 1 <= t_end) {  // prefetch row t+1
+    const int64_t rn = (int64_t)(t + 1) * pitch;
+    S.pc = load_cols(gC + rn, col, np, vec);
+    S.pa = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : load_cols(gA + rn, col, np, vec);
+    S.pg = load_cols(gG + rn, col, np, vec);
+  }
+  float4 top = make_float4(0.f, 0.f, 0.f, 0.f);  // level K at row t-K
+#pragma unroll
+  for (int m = 1; m <= K; ++m) {
+    if (m <= kk && t - m >= tmin) {  // rows above the first loaded one are never needed
+      const int row = t - m;
+      const int sc = ((P - m) % 3 + 3) % 3;       // slot of row t-m in level m-1's window
+      const int su = ((P - m - 1) % 3 + 3) % 3;   // row t-m-1
+      const int sd = ((P - m + 1) % 3 + 3) % 3;   // row t-m+1
+      const RowCoef k = row_coef(geo[row], cf[m - 1], nudt);
+      const float4 d2 = m == 1 ? S.d2m1 : S.Win[m - 2][sc];
+      const float4 gv = m == 1 ? S.g1 : load_cols(gG + (int64_t)row * pitch, col, np, vec);
+      const float4 o = level_update(k, S.Win[m - 1][sc], S.Win[m - 1][su], S.Win[m - 1][sd], d2, gv);
+      if (m < K) S.Win[m][sc] = o;
+      else top = o;
+    }
+  }
+  S.d2m1 = a_t;
+  S.g1 = g_t;
+  // leave the pipeline: level kk (and kk-1) at row t - kk
+  const int orow = t - kk;
+  if (orow >= J0 && orow < J1 && lane_out) {
+    // slots are compile-time (unrolled m, template P) so the state stays in registers
+    float4 lk = top, lk1 = S.Win[K - 1][((P - K) % 3 + 3) % 3];
+#pragma unroll
+    for (int m = 1; m < K; ++m)
+      if (m == kk) {
+        lk = S.Win[m][((P - m) % 3 + 3) % 3];
+        lk1 = S.Win[m - 1][((P - m) % 3 + 3) % 3];
+      }
+    const int64_t go = (int64_t)orow * pitch + col;
+    if (fin) {
+      float4 b = n_out == 4 && vec ? ld4(Bs + go) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (n_out == 4 && vec) {
+        b.x += lk.x; b.y += lk.y; b.z += lk.z; b.w += lk.w;
+        bad |= !isfinite(b.x) || !isfinite(b.y) || !isfinite(b.z) || !isfinite(b.w);
+        st4(Bs + go, b);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (e < n_out) {
+            int c = col + e;
+            c = c >= np ? c - np : c;
+            const float x = Bs[(int64_t)orow * pitch + c] + (e == 0 ? lk.x : e == 1 ? lk.y : e == 2 ? lk.z : lk.w);
+            bad |= !isfinite(x);
+            Bs[(int64_t)orow * pitch + c] = x;
+          }
+        }
+      }
+    } else if (n_out == 4 && vec) {
+      st4(oC + go, lk);
+      st4(oA + go, lk1);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (e < n_out) {
+          int c = col + e;
+          c = c >= np ? c - np : c;
+          oC[(int64_t)orow * pitch + c] = e == 0 ? lk.x : e == 1 ? lk.y : e == 2 ? lk.z : lk.w;
+          oA[(int64_t)orow * pitch + c] = e == 0 ? lk1.x : e == 1 ? lk1.y : e == 2 ? lk1.z : lk1.w;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads)
+rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+                  const StepParam* __restrict__ sp, const RowGeo<float>* __restrict__ geo,
+                  const ShapeConst* __restrict__ shc, const Coef<float>* __restrict__ coef,
+                  float* __restrict__ B, const float* __restrict__ G, const float* __restrict__ Dm2,
+                  const float* __restrict__ Dm1, float* __restrict__ Om2, float* __restrict__ Om1,
+                  float* __restrict__ polar, int j0, int* __restrict__ status) {
+  using namespace fused;
+  __shared__ double sm[kThreads / 32];
+  const Tile tl = tiles[blockIdx.x];
+  const int kind = tl.kind & 3;
+  const RealDesc d = rd[tl.r];
+  const StepParam p = sp[tl.r];
+  if (j0 > p.s) return;
+  const int kk = min(K, p.s - j0 + 1);  // levels of this realization in this pass
+  const bool fin = j0 + kk - 1 == p.s;  // the pass ends the realization's super-step
+  const float nudt = float(p.nudt);
+  const int pitch = d.pitch, np = d.np, nt = d.nt;
+  const float* gG = G + d.woff;
+  const float* gA = Dm2 + d.woff;  // delta_{j0-2}
+  const float* gC = Dm1 + d.woff;  // delta_{j0-1}
+  float* oA = Om2 + d.woff;
+  float* oC = Om1 + d.woff;
+  float* Bs = B + d.off;
+  const bool zero_m2 = j0 == 2;  // delta_0 = 0
+
+  if (kind != 0) {
+    const bool north = kind == 1;
+    const int base = north ? 0 : nt - NB;  // global row of local row 0
+    float* prv = polar + d.poff + (north ? 0 : 2 * NB * pitch);  // level m-2, updated to m
+    float* cur = prv + NB * pitch;                                // level m-1
+    for (int idx = threadIdx.x; idx < NB * np; idx += kThreads) {
+      const int i = idx / np, k = idx - i * np;
+      const int64_t go = (int64_t)(base + i) * pitch + k, lo = (int64_t)i * pitch + k;
+      cur[lo] = gC[go];
+      prv[lo] = zero_m2 ? 0.f : gA[go];
+    }
+    __syncthreads();
+    const int ip = north ? 0 : NB - 1;  // pole row (local)
+    const int ia = north ? 1 : NB - 2;  // ring next to the pole
+    double pole_last = 0.0;
+    for (int m = 1; m <= kk; ++m) {
+      const Coef<float> cf = coef[p.coef + j0 + m - 1];
+      const float mutdt = cf.mut * nudt;
+      const int i_lo = north ? 1 : m, i_hi = north ? NB - 1 - m : NB - 2;
+      const double yp = double(cur[(int64_t)ip * pitch]);
+      const double pp = double(prv[(int64_t)ip * pitch]);
+      const double gp = double(gG[(int64_t)(base + ip) * pitch]);
+      double acc = 0.0;
+      for (int k = threadIdx.x; k < np; k += blockDim.x) acc += double(cur[(int64_t)ia * pitch + k]) - yp;
+      const double Lp = shc[d.shape].pole_diff * block_sum(acc, sm);
+      const int nrow = i_hi - i_lo + 1;
+      for (int idx = threadIdx.x; idx < nrow * np; idx += kThreads) {
+        const int q = idx / np, k = idx - q * np, i = i_lo + q;
+        const float* cr = cur + (int64_t)i * pitch;
+        const RowGeo<float> g = geo[d.geo + base + i];
+        const int64_t lo = (int64_t)i * pitch + k;
+        prv[lo] = rkl2_point(g, cf, mutdt, cr[k], cr[k - pitch], cr[k + pitch],
+                             cr[k == 0 ? np - 1 : k - 1], cr[k == np - 1 ? 0 : k + 1], prv[lo],
+                             gG[(int64_t)(base + i) * pitch + k]);
+      }
+      pole_last = double(cf.mu) * yp + double(cf.nu) * pp + double(cf.mut) * double(nudt) * Lp +
+                  double(cf.gsum) * gp;
+      const float vp = float(pole_last);
+      for (int k = threadIdx.x; k < np; k += kThreads) prv[(int64_t)ip * pitch + k] = vp;
+      __syncthreads();
+      float* t = cur;
+      cur = prv;
+      prv = t;
+    }
+    const int o_lo = north ? 0 : NB - 1 - PB, o_hi = north ? PB : NB - 1;
+    bool bad = false;
+    for (int idx = threadIdx.x; idx < (o_hi - o_lo + 1) * np; idx += kThreads) {
+      const int q = idx / np, k = idx - q * np, i = o_lo + q;
+      const int64_t go = (int64_t)(base + i) * pitch + k, lo = (int64_t)i * pitch + k;
+      if (fin) {
+        const float v = i == ip ? float(double(Bs[go]) + pole_last) : Bs[go] + cur[lo];
+        bad |= !isfinite(v);
+        Bs[go] = v;
+      } else {
+        oC[go] = cur[lo];
+        oA[go] = prv[lo];
+      }
+    }
+    if (bad) atomicOr(status, 1);
+    return;
+  }
+
+  // interior: warp w of the block marches work item (tl.j0 + w) = (band, strip)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_strips = (np + STRIP - 1) / STRIP;
+  const int n_bands = (nt - 2 - 2 * PB + BAND - 1) / BAND;
+  const int item = tl.j0 + warp;
+  if (item >= n_bands * n_strips) return;  // whole warp
+  const int strip = item % n_strips;
+  const int J0 = PB + 1 + (item / n_strips) * BAND;
+  const int J1 = min(J0 + BAND, nt - 1 - PB);
+  int col = (strip * STRIP - K + 4 * lane) % np;  // first of the lane's 4 columns, periodic
+  col = col < 0 ? col + np : col;
+  const bool vec = (np & 3) == 0;
+  // output: lanes 1..30, columns strip*STRIP .. +STRIP-1 that are < np
+  const int first_out = strip * STRIP + 4 * (lane - 1);
+  const bool lane_out = lane >= 1 && lane <= 30 && first_out < np;
+  const int n_out = lane_out ? min(4, np - first_out) : 0;
+  Coef<float> cf[K];
+#pragma unroll
+  for (int m = 0; m < K; ++m) cf[m] = coef[p.coef + j0 + min(m, kk - 1)];
+  March S;
+#pragma unroll
+  for (int l = 0; l < K; ++l)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S.Win[l][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.d2m1 = S.g1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const RowGeo<float>* grow = geo + d.geo;
+  bool bad = false;
+  const int tmin = J0 - K;        // first row loaded
+  const int t_end = J1 - 1 + kk;  // last row loaded
+  {
+    const int64_t r0 = (int64_t)tmin * pitch;
+    S.pc = load_cols(gC + r0, col, np, vec);
+    S.pa = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : load_cols(gA + r0, col, np, vec);
+    S.pg = load_cols(gG + r0, col, np, vec);
+  }
+#define SFT_MARCH(PH, TT)                                                                         \
+  march_row<PH>(S, TT, kk, tmin, t_end, gA, gC, gG, grow, cf, nudt, pitch, np, col, vec, zero_m2, \
+                J0, J1, fin, oA, oC, Bs, lane_out, n_out, bad)
+  // the phase t mod 3 is a template argument: the row loop is unrolled by 3
+  int t = tmin;
+  const int ph = t % 3;
+  if (ph == 1) {
+    SFT_MARCH(1, t);
+    ++t;
+  }
+  if (ph != 0 && t <= t_end) {
+    SFT_MARCH(2, t);
+    ++t;
+  }
+  for (; t + 2 <= t_end; t += 3) {
+    SFT_MARCH(0, t);
+    SFT_MARCH(1, t + 1);
+    SFT_MARCH(2, t + 2);
+  }
+  if (t <= t_end) {
+    SFT_MARCH(0, t);
+    ++t;
+  }
+  if (t <= t_end) {
+    SFT_MARCH(1, t);
+    ++t;
+  }
+#undef SFT_MARCH
+  if (bad) atomicOr(status, 1);
+}
+
+cudaError_t prepare_rkl2_fused() { return cudaSuccess; }
+
+cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                              const StepParam* sp, const RowGeo<float>* geo, const ShapeConst* shc,
+                              const Coef<float>* coef, float* B, const float* G, const float* Dm2,
+                              const float* Dm1, float* Om2, float* Om1, float* polar, int j0,
+                              int* status) {
+  if (n_tiles <= 0) return cudaSuccess;
+  rkl2_fused_kernel<<<n_tiles, kThreads, 0, st>>>(tiles, rd, sp, geo, shc, coef, B, G,
+                                                                   Dm2, Dm1, Om2, Om1, polar, j0,
+                                                                   status);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void fix_poles_kernel(const RealDesc* __restrict__ rd, T* __restrict__ state, int only_r) {
   const int r = only_r >= 0 ? only_r : blockIdx.x >> 1;

@@ -88,6 +88,8 @@ _SIGS = {
     "sft_reset_stats": (C.c_int, [C.c_void_p]),
     "sft_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "sft_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sft_set_fusion": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sft_get_fusion": (C.c_int32, [C.c_void_p]),
     "sft_set_tile_rows": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "sft_get_tile_rows": (C.c_int32, [C.c_void_p, C.c_int32]),
     "sft_wave_size": (C.c_int32, [C.c_void_p]),
@@ -303,6 +305,12 @@ class Grid:
 
     def set_graphs(self, on):
         self._check(self.lib.sft_set_graphs(self.h, 1 if on else 0))
+
+    def set_fusion(self, stages_per_pass):
+        self._check(self.lib.sft_set_fusion(self.h, int(stages_per_pass)))
+
+    def get_fusion(self):
+        return self.lib.sft_get_fusion(self.h)
 
     def set_tile_rows(self, shape_id, rows):
         self._check(self.lib.sft_set_tile_rows(self.h, shape_id, rows))

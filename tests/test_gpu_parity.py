@@ -216,7 +216,8 @@ def test_graphs_tiles_and_waves_give_identical_bits():
         budget = 0
         if mode == "waves":
             cells = sum(a * ((b + 31) // 32 * 32) for a, b in shapes)
-            budget = cells * 4 + (64 << 20) + 3 * 4 * 33 * 96 * 2  # two realizations per wave
+            # room for two realizations' work arrays per wave (5 arrays on the fused FP32 path)
+            budget = cells * 4 + (64 << 20) + 5 * 4 * 33 * 96 * 2
         g = Grid(shapes, "fp32", hbm_budget=budget)
         if mode == "waves":
             assert g.wave_size() == 2
@@ -285,3 +286,34 @@ def test_error_codes():
         g.set_tile_rows(0, 3)
     with pytest.raises(SFTError):
         g.get_state(5)
+
+
+@pytest.mark.parametrize("shapes", [
+    [(20, 100), (57, 520), (20, 16)],          # smallest fused grids, ragged phi tails
+    [(129, 256), (64, 136), (129, 256)],
+])
+def test_fused_rkl2_matches_single_stage_launches(shapes):
+    """Four RKL2 stages per launch (shared-memory tiles with a 4-point halo,
+    full-ring cap blocks) against one launch per stage: the same per-point
+    formulas, so the maps agree to FP32 rounding."""
+    outs = {}
+    for k in (1, 4):
+        g, params, maps = _batch(shapes, "fp32", seed=31)
+        assert g.get_fusion() == 4   # default when available
+        g.set_fusion(k)
+        g.step(30.0)
+        outs[k] = [g.get_state(r) for r in range(len(shapes))]
+        if k == 4:
+            st = g.stats()
+            assert st["diff_cell_stages"] > 0
+    for a, b in zip(outs[1], outs[4]):
+        assert rel_linf(b, a) <= 2e-6, rel_linf(b, a)
+
+
+def test_fused_path_unavailable_for_small_grids_and_fp64():
+    g = Grid([(19, 64)], "fp32")
+    assert g.get_fusion() == 1
+    with pytest.raises(SFTError):
+        g.set_fusion(4)
+    g2 = Grid([(64, 64)], "fp64")
+    assert g2.get_fusion() == 1
