@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsft.so")
-SOURCES = ["sft_api.cu", "sft_kernels.cu", "sft_noalloc.cu"]
+SOURCES = ["sft_api.cu", "sft_kernels.cu", "sft_noalloc.cu", "sfs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

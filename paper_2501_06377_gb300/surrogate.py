@@ -1,0 +1,162 @@
+"""Thin ctypes binding of the learned surrogate (include/sfs.h).
+
+Marshalling only: the network's forward and backward passes, the optimizer
+and the error reductions run in the CUDA kernels of libsft.so.  Maps and
+parameters are CUDA torch tensors (float32, contiguous):
+x, y [n, 256, 512] (Gauss), p [n, 5] = (o0, o2, o4 deg/day, U m/s, eta km^2/s).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from .sft import SFT_OK, SFTError, load
+
+H, W = 256, 512
+
+
+class sfs_config(C.Structure):
+    _fields_ = [("channels", C.c_int32), ("modes", C.c_int32), ("blocks", C.c_int32),
+                ("max_batch", C.c_int32), ("seed", C.c_uint64)]
+
+
+_SIGS = {
+    "sfs_create": (C.c_int, [C.POINTER(sfs_config), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sfs_destroy": (C.c_int, [C.c_void_p]),
+    "sfs_num_params": (C.c_int64, [C.c_void_p]),
+    "sfs_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sfs_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sfs_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sfs_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                C.POINTER(C.c_float), C.c_void_p]),
+    "sfs_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                 C.c_double, C.c_double, C.POINTER(C.c_float)]),
+    "sfs_rel_l2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sfs_flux": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sfs_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                               C.POINTER(C.c_int64)]),
+}
+
+_bound = False
+
+
+def _lib():
+    global _bound
+    lib = load()
+    if not _bound:
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _bound = True
+    return lib
+
+
+def _dev(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.float32):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Surrogate:
+    """One network with its optimizer state and work buffers."""
+
+    def __init__(self, channels=64, modes=48, blocks=4, max_batch=32, seed=0, stream=None):
+        self.lib = _lib()
+        cfg = sfs_config(channels, modes, blocks, max_batch, seed)
+        h = C.c_void_p()
+        s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        st = self.lib.sfs_create(C.byref(cfg), s, C.byref(h))
+        if st != SFT_OK:
+            raise SFTError(st, self.lib.sft_last_error(None).decode())
+        self.h = h
+        self.channels, self.modes, self.blocks, self.max_batch = channels, modes, blocks, max_batch
+
+    def _check(self, st):
+        if st != SFT_OK:
+            raise SFTError(st, self.lib.sft_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sfs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        return int(self.lib.sfs_num_params(self.h))
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.num_params()
+        self._check(self.lib.sfs_set_params(self.h, C.c_void_p(a.ctypes.data)))
+
+    def get_params(self):
+        a = np.empty(self.num_params(), dtype=np.float32)
+        self._check(self.lib.sfs_get_params(self.h, C.c_void_p(a.ctypes.data)))
+        return a
+
+    def forward(self, x, p, out):
+        self._check(self.lib.sfs_forward(self.h, _dev(x), _dev(p), x.shape[0], _dev(out)))
+        return out
+
+    def loss_grad(self, x, p, y):
+        g = np.empty(self.num_params(), dtype=np.float32)
+        loss = C.c_float()
+        self._check(self.lib.sfs_loss_grad(self.h, _dev(x), _dev(p), _dev(y), x.shape[0], C.byref(loss),
+                                           C.c_void_p(g.ctypes.data)))
+        return float(loss.value), g
+
+    def train_step(self, x, p, y, lr, wd=1e-4, want_loss=False):
+        loss = C.c_float()
+        self._check(self.lib.sfs_train_step(self.h, _dev(x), _dev(p), _dev(y), x.shape[0], float(lr),
+                                            float(wd), C.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def rel_l2(self, a, b):
+        out = np.empty(a.shape[0], dtype=np.float64)
+        self._check(self.lib.sfs_rel_l2(self.h, _dev(a), _dev(b), a.shape[0], C.c_void_p(out.ctypes.data)))
+        return out
+
+    def flux(self, maps):
+        """(signed, unsigned) FP64 flux of each map, in chunks of max_batch."""
+        n = maps.shape[0]
+        out = np.empty((n, 2), dtype=np.float64)
+        for c0 in range(0, n, self.max_batch):
+            c1 = min(n, c0 + self.max_batch)
+            o = np.empty(2 * (c1 - c0), dtype=np.float64)
+            self._check(self.lib.sfs_flux(self.h, _dev(maps[c0:c1]), c1 - c0, C.c_void_p(o.ctypes.data)))
+            out[c0:c1] = o.reshape(-1, 2)
+        return out[:, 0], out[:, 1]
+
+    def counters(self):
+        g, f, k = C.c_int64(), C.c_double(), C.c_int64()
+        self._check(self.lib.sfs_counters(self.h, C.byref(g), C.byref(f), C.byref(k)))
+        return {"gemm_launches": g.value, "gemm_flops": f.value, "kernel_launches": k.value}
+
+
+def flat_from_reference(P, blocks):
+    """Flatten a reference parameter dict in the order of include/sfs.h."""
+    parts = [P["We"], P["be"], P["Wd"], P["bd"]]
+    for l in range(blocks):
+        parts += [P["w%d" % l], P["W1_%d" % l], P["b1_%d" % l], P["W2_%d" % l], P["b2_%d" % l]]
+    return np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1) for a in parts]).astype(np.float32)
+
+
+def unflatten_like(flat, P, blocks):
+    """Inverse of flat_from_reference (for comparing gradients)."""
+    out, o = {}, 0
+    order = ["We", "be", "Wd", "bd"]
+    for l in range(blocks):
+        order += ["w%d" % l, "W1_%d" % l, "b1_%d" % l, "W2_%d" % l, "b2_%d" % l]
+    for k in order:
+        n = P[k].size
+        out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(P[k].shape)
+        o += n
+    return out

@@ -51,3 +51,13 @@ def test_noalloc_rejects_oversized_maps_before_any_cuda_call(lib):
     assert b"scratch" in lib.sft_last_error(None)
     assert lib.sft_flux_diagnostics_noalloc(fake, 64, 7, 0, 60.0, None, C.byref(out)) == sft.SFT_ERR_ARG
     assert lib.sft_flux_diagnostics_noalloc(None, 64, 128, 0, 60.0, None, C.byref(out)) == sft.SFT_ERR_ARG
+
+
+def test_surrogate_header_exported_and_bound(lib):
+    from paper_2501_06377_gb300 import surrogate
+    names = sft.header_functions(sft.HEADER.replace("sft.h", "sfs.h"))
+    names = [n for n in names if n.startswith("sfs_")]
+    assert len(names) >= 10
+    raw = C.CDLL(sft.LIB_PATH)
+    assert all(hasattr(raw, n) for n in names)
+    assert set(names) == set(surrogate._SIGS)
