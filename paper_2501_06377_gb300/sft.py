@@ -102,12 +102,12 @@ _SIGS = {
 }
 
 
-def header_functions(path=HEADER):
-    """Names of the functions declared in include/sft.h."""
+def header_functions(path=HEADER, prefix="sft_"):
+    """Names of the functions a header (include/sft.h by default) declares."""
     with open(path) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sft_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"[a-z0-9_]+)\s*\(", text)))
 
 
 def load(path=LIB_PATH):

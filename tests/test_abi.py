@@ -55,8 +55,7 @@ def test_noalloc_rejects_oversized_maps_before_any_cuda_call(lib):
 
 def test_surrogate_header_exported_and_bound(lib):
     from paper_2501_06377_gb300 import surrogate
-    names = sft.header_functions(sft.HEADER.replace("sft.h", "sfs.h"))
-    names = [n for n in names if n.startswith("sfs_")]
+    names = sft.header_functions(sft.HEADER.replace("sft.h", "sfs.h"), prefix="sfs_")
     assert len(names) >= 10
     raw = C.CDLL(sft.LIB_PATH)
     assert all(hasattr(raw, n) for n in names)
