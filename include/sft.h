@@ -185,7 +185,9 @@ sft_status sft_step(sft_handle h, double t_target_hours, int32_t max_steps, int3
 /*
  * Assimilate observations (Sec. 2.3).  br_obs and mu are maps in the
  * handle's precision: one map per realization (obs_per_realization = 1,
- * concatenated in realization order) or one map shared by every
+ * concatenated in realization order), one map per grid shape
+ * (obs_per_realization = 2, concatenated in shape order, the order of first
+ * appearance in sft_create_grid's shapes), or one map shared by every
  * realization (obs_per_realization = 0; all realizations must then have the
  * same shape).  F = mu^alpha_mu where mu > mu_lim and |lat| < lat_lim, else
  * 0 (Eq. data_assim_f); Delta B = F (B_obs - B) (Eq. data_assim_deltab),

@@ -1117,18 +1117,27 @@ sft_status sft_assimilate(sft_handle h, const void* br_obs, const void* mu, int3
   SFT_CUDA(h, cudaSetDevice(h->device));
   std::vector<int64_t> off(h->n_real, 0);
   int64_t total = 0;
-  if (obs_per_realization) {
+  if (obs_per_realization == 1) {  // one map per realization, in realization order
     for (int r = 0; r < h->n_real; ++r) {
       const ShapeInfo& s = h->shapes[h->reals[r].shape];
       off[r] = total;
       total += (int64_t)s.nt * s.np;
     }
-  } else {
+  } else if (obs_per_realization == 2) {  // one map per grid shape, in shape order
+    std::vector<int64_t> soff(h->shapes.size());
+    for (size_t si = 0; si < h->shapes.size(); ++si) {
+      soff[si] = total;
+      total += (int64_t)h->shapes[si].nt * h->shapes[si].np;
+    }
+    for (int r = 0; r < h->n_real; ++r) off[r] = soff[h->reals[r].shape];
+  } else if (obs_per_realization == 0) {
     for (int r = 1; r < h->n_real; ++r)
       if (h->reals[r].shape != h->reals[0].shape)
         return fail(h, SFT_ERR_ARG, "shared observations need one grid shape for all realizations");
     const ShapeInfo& s = h->shapes[h->reals[0].shape];
     total = (int64_t)s.nt * s.np;
+  } else {
+    return fail(h, SFT_ERR_ARG, "obs_per_realization must be 0, 1 or 2");
   }
   std::vector<double> w(4 * h->n_real);
   for (int r = 0; r < h->n_real; ++r) {

@@ -273,6 +273,8 @@ class Grid:
         return n.value
 
     def assimilate(self, obs, mu, per_realization, params):
+        """per_realization: False/0 = one shared map, True/1 = one map per
+        realization, 2 = one map per grid shape (shape order)."""
         if isinstance(params, AssimParams):
             params = [params] * self.n_real
         po, do, ko = _ptr(obs)
@@ -280,8 +282,8 @@ class Grid:
         if do != dm:
             raise ValueError("obs and mu must both be on the host or both on the device")
         arr = (sft_assim_params * self.n_real)(*[p.to_c() for p in params])
-        self._check(self.lib.sft_assimilate(self.h, C.c_void_p(po), C.c_void_p(pm),
-                                            1 if per_realization else 0, do, arr))
+        mode = int(per_realization) if not isinstance(per_realization, bool) else (1 if per_realization else 0)
+        self._check(self.lib.sft_assimilate(self.h, C.c_void_p(po), C.c_void_p(pm), mode, do, arr))
         del ko, km
 
     def balance_flux(self):
