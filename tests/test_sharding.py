@@ -1,0 +1,98 @@
+"""Multi-process host path on CPU (gloo, world size 2): realization
+sharding, the timing reduction, and failure detection by a rank that never
+reaches the barrier.  No GPU is involved."""
+import os
+import socket
+
+import pytest
+
+from paper_2501_06377_gb300 import sharding as SH
+
+
+def test_lpt_covers_everything_once_and_balances():
+    shapes = [(256, 512)] * 128 + [(512, 1024)] * 96 + [(1440, 2880)] * 32
+    stages = [36] * 128 + [145] * 96 + [1191] * 32
+    costs = SH.shard_costs(shapes, stages)
+    for world in (1, 2, 3, 8):
+        sh = SH.lpt_shards(costs, world)
+        flat = sorted(i for s in sh for i in s)
+        assert flat == list(range(len(costs)))
+        loads = [sum(costs[i] for i in s) for s in sh]
+        lower = max(max(costs), sum(costs) / world)   # no schedule beats this
+        assert max(loads) <= 4.0 / 3.0 * lower + 1e-9
+
+
+def test_requeue_hands_orphans_to_survivors():
+    costs = [5, 3, 3, 2, 2, 2, 1, 1]
+    sh = SH.lpt_shards(costs, 3)
+    new = SH.requeue(sh, costs, failed=[1])
+    assert new[1] == []
+    assert sorted(i for s in new for i in s) == list(range(len(costs)))
+    assert set(sh[0]) <= set(new[0]) and set(sh[2]) <= set(new[2])
+    with pytest.raises(RuntimeError):
+        SH.requeue(sh, costs, failed=[0, 1, 2])
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, mode, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        if mode == "shards":
+            costs = [float(i % 7 + 1) for i in range(50)]
+            mine = SH.lpt_shards(costs, world)[rank]
+            got = [None] * world
+            dist.all_gather_object(got, mine)
+            t = SH.max_over_ranks(1.0 + rank)
+            q.put((rank, got, t))
+        elif mode == "dropout":
+            if rank == 1:
+                q.put((rank, "left"))
+                return   # leaves between steps: never reaches the barrier
+            try:
+                SH.checked_barrier(timeout_s=3.0)
+                q.put((rank, "no error"))
+            except RuntimeError as e:
+                q.put((rank, "detected: " + str(e)[:200]))
+    finally:
+        if mode == "shards":
+            dist.destroy_process_group()
+
+
+def _run(mode):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, mode, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=60) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=30)
+        if p.is_alive():
+            p.kill()
+    return sorted(out, key=lambda x: x[0])
+
+
+def test_two_rank_shards_cover_all_and_max_time():
+    out = _run("shards")
+    for rank, got, t in out:
+        assert sorted(i for s in got for i in s) == list(range(50))
+        assert t == 2.0
+
+
+def test_missing_rank_is_detected_by_the_checked_barrier():
+    out = _run("dropout")
+    assert out[1][1] == "left"
+    assert out[0][1].startswith("detected"), out[0][1]
+    assert "1" in out[0][1]
