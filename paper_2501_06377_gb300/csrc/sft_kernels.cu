@@ -451,6 +451,25 @@ __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpre
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
+// Asynchronous global -> shared copies (per lane, its own slots): 16 bytes
+// when the four columns are contiguous and aligned, else four 4-byte copies.
+__device__ __forceinline__ void async_cols(float4* dst, const float* row, int c0, int np, bool vec) {
+  const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if (vec) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(row + c0) : "memory");
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int c = c0 + e;
+      c = c >= np ? c - np : c;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa + 4 * e), "l"(row + c) : "memory");
+    }
+  }
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Four consecutive longitudes starting at column c0 (periodic), as a float4.
 __device__ __forceinline__ float4 load_cols(const float* row, int c0, int np, bool vec) {
   if (vec) return ldg4(row + c0);
@@ -473,12 +492,13 @@ struct RowCoef {
   float a0, a1, a2, a3, nu, gs;
 };
 
-__device__ __forceinline__ RowCoef row_coef(const RowGeo<float>& g, const Coef<float>& cf, float nudt) {
+__device__ __forceinline__ RowCoef row_coef(const float4 g, const Coef<float>& cf, float nudt) {
+  // g = (cN, cS, cE, .): the first four fields of RowGeo<float>
   const float md = cf.mut * nudt;
   RowCoef k;
-  k.a1 = md * g.cN;
-  k.a2 = md * g.cS;
-  k.a3 = md * g.cE;
+  k.a1 = md * g.x;
+  k.a2 = md * g.y;
+  k.a3 = md * g.z;
   k.a0 = cf.mu - (k.a1 + k.a2 + 2.f * k.a3);
   k.nu = cf.nu;
   k.gs = cf.gsum;
@@ -509,28 +529,37 @@ __device__ __forceinline__ float4 level_update(const RowCoef& k, float4 c, float
 // ahead (pc, pa, pg) so their latency overlaps a whole row of arithmetic.
 struct March {
   float4 Win[fused::K][3];
-  float4 d2m1;      // delta_{j-2} at row t-1
-  float4 g1;        // G at row t-1
-  float4 pc, pa, pg;  // inputs of row t (prefetched during step t-1)
+  float4 d2m1;           // delta_{j-2} at row t-1
+  float4 *rc, *ra, *rg;  // this warp's shared-memory rings (C, A: D rows; G: DG rows)
 };
+
+// Issue the asynchronous copies of row r's inputs into the rings (one commit group).
+__device__ __forceinline__ void march_issue(March& S, int r, int t_end, const float* gA, const float* gC,
+                                            const float* gG, int pitch, int np, int col, bool vec, bool zero_m2,
+                                            int lane) {
+  if (r <= t_end) {
+    const int64_t ro = (int64_t)r * pitch;
+    async_cols(S.rc + (r % fused::D) * fused::LANES + lane, gC + ro, col, np, vec);
+    if (!zero_m2) async_cols(S.ra + (r % fused::D) * fused::LANES + lane, gA + ro, col, np, vec);
+    async_cols(S.rg + (r % fused::DG) * fused::LANES + lane, gG + ro, col, np, vec);
+  }
+  async_commit();  // empty groups past the band keep the group count uniform
+}
 
 template <int P>
 __device__ __forceinline__ void march_row(March& S, int t, int kk, int tmin, int t_end, const float* gA,
                                           const float* gC, const float* gG, const RowGeo<float>* geo,
-                                          const Coef<float> (&cf)[fused::K], float nudt, int pitch, int np,
+                                          const Coef<float>* cf, float nudt, int pitch, int np,
                                           int col, bool vec, bool zero_m2, int J0, int J1, bool fin,
                                           float* oA, float* oC, float* Bs, bool lane_out, int n_out,
-                                          bool& bad) {
+                                          bool& bad, int lane) {
   using namespace fused;
-  // this row's inputs arrived during the previous step
-  S.Win[0][P] = S.pc;
-  const float4 a_t = S.pa, g_t = S.pg;
-  if (t + 1 <= t_end) {  // prefetch row t+1
-    const int64_t rn = (int64_t)(t + 1) * pitch;
-    S.pc = load_cols(gC + rn, col, np, vec);
-    S.pa = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : load_cols(gA + rn, col, np, vec);
-    S.pg = load_cols(gG + rn, col, np, vec);
-  }
+  // request row t+D-1 (into the slots of rows t-1 / t-1-K, already consumed),
+  // then wait until row t has landed: D groups are in flight at most
+  march_issue(S, t + D - 1, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
+  async_wait<D - 1>();
+  S.Win[0][P] = S.rc[(t % D) * LANES + lane];
+  const float4 a_t = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : S.ra[(t % D) * LANES + lane];
   float4 top = make_float4(0.f, 0.f, 0.f, 0.f);  // level K at row t-K
 #pragma unroll
   for (int m = 1; m <= K; ++m) {
@@ -539,16 +568,15 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int tmin, int
       const int sc = ((P - m) % 3 + 3) % 3;       // slot of row t-m in level m-1's window
       const int su = ((P - m - 1) % 3 + 3) % 3;   // row t-m-1
       const int sd = ((P - m + 1) % 3 + 3) % 3;   // row t-m+1
-      const RowCoef k = row_coef(geo[row], cf[m - 1], nudt);
+      const RowCoef k = row_coef(*reinterpret_cast<const float4*>(geo + row), cf[m - 1], nudt);
       const float4 d2 = m == 1 ? S.d2m1 : S.Win[m - 2][sc];
-      const float4 gv = m == 1 ? S.g1 : load_cols(gG + (int64_t)row * pitch, col, np, vec);
+      const float4 gv = S.rg[(row % DG) * LANES + lane];
       const float4 o = level_update(k, S.Win[m - 1][sc], S.Win[m - 1][su], S.Win[m - 1][sd], d2, gv);
       if (m < K) S.Win[m][sc] = o;
       else top = o;
     }
   }
   S.d2m1 = a_t;
-  S.g1 = g_t;
   // leave the pipeline: level kk (and kk-1) at row t - kk
   const int orow = t - kk;
   if (orow >= J0 && orow < J1 && lane_out) {
@@ -607,12 +635,15 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
                   float* __restrict__ polar, int j0, int* __restrict__ status) {
   using namespace fused;
   __shared__ double sm[kThreads / 32];
+  __shared__ Coef<float> s_cf[K];
   const Tile tl = tiles[blockIdx.x];
   const int kind = tl.kind & 3;
   const RealDesc d = rd[tl.r];
   const StepParam p = sp[tl.r];
-  if (j0 > p.s) return;
+  if (j0 > p.s) return;  // uniform over the block
   const int kk = min(K, p.s - j0 + 1);  // levels of this realization in this pass
+  if (threadIdx.x < K) s_cf[threadIdx.x] = coef[p.coef + j0 + min((int)threadIdx.x, kk - 1)];
+  __syncthreads();
   const bool fin = j0 + kk - 1 == p.s;  // the pass ends the realization's super-step
   const float nudt = float(p.nudt);
   const int pitch = d.pitch, np = d.np, nt = d.nt;
@@ -702,28 +733,26 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   const int first_out = strip * STRIP + 4 * (lane - 1);
   const bool lane_out = lane >= 1 && lane <= 30 && first_out < np;
   const int n_out = lane_out ? min(4, np - first_out) : 0;
-  Coef<float> cf[K];
-#pragma unroll
-  for (int m = 0; m < K; ++m) cf[m] = coef[p.coef + j0 + min(m, kk - 1)];
+  const Coef<float>* cf = s_cf;
+  extern __shared__ __align__(16) float4 rings[];
   March S;
+  S.rc = rings + warp * RING_F4;
+  S.ra = S.rc + D * LANES;
+  S.rg = S.ra + D * LANES;
 #pragma unroll
   for (int l = 0; l < K; ++l)
 #pragma unroll
     for (int q = 0; q < 3; ++q) S.Win[l][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  S.d2m1 = S.g1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.d2m1 = make_float4(0.f, 0.f, 0.f, 0.f);
   const RowGeo<float>* grow = geo + d.geo;
   bool bad = false;
   const int tmin = J0 - K;        // first row loaded
   const int t_end = J1 - 1 + kk;  // last row loaded
-  {
-    const int64_t r0 = (int64_t)tmin * pitch;
-    S.pc = load_cols(gC + r0, col, np, vec);
-    S.pa = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : load_cols(gA + r0, col, np, vec);
-    S.pg = load_cols(gG + r0, col, np, vec);
-  }
+  for (int r = tmin; r < tmin + D - 1; ++r)  // D-1 rows of lookahead before the first step
+    march_issue(S, r, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
 #define SFT_MARCH(PH, TT)                                                                         \
   march_row<PH>(S, TT, kk, tmin, t_end, gA, gC, gG, grow, cf, nudt, pitch, np, col, vec, zero_m2, \
-                J0, J1, fin, oA, oC, Bs, lane_out, n_out, bad)
+                J0, J1, fin, oA, oC, Bs, lane_out, n_out, bad, lane)
   // the phase t mod 3 is a template argument: the row loop is unrolled by 3
   int t = tmin;
   const int ph = t % 3;
@@ -749,10 +778,14 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
     ++t;
   }
 #undef SFT_MARCH
+  async_wait<0>();  // no copy outlives the block
   if (bad) atomicOr(status, 1);
 }
 
-cudaError_t prepare_rkl2_fused() { return cudaSuccess; }
+cudaError_t prepare_rkl2_fused() {
+  return cudaFuncSetAttribute(rkl2_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fused::kSmemBytes);
+}
 
 cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
                               const StepParam* sp, const RowGeo<float>* geo, const ShapeConst* shc,
@@ -760,7 +793,7 @@ cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, c
                               const float* Dm1, float* Om2, float* Om1, float* polar, int j0,
                               int* status) {
   if (n_tiles <= 0) return cudaSuccess;
-  rkl2_fused_kernel<<<n_tiles, kThreads, 0, st>>>(tiles, rd, sp, geo, shc, coef, B, G,
+  rkl2_fused_kernel<<<n_tiles, kThreads, fused::kSmemBytes, st>>>(tiles, rd, sp, geo, shc, coef, B, G,
                                                                    Dm2, Dm1, Om2, Om1, polar, j0,
                                                                    status);
   return cudaGetLastError();
