@@ -280,7 +280,10 @@ def run_gpu(args, rank, world, local_rank):
                        "cell_stage_updates_per_s": (st["diff_cell_stages"] + st["adv_cell_stages"])
                        * world / (ms * 1e-3),
                        "rkl2_stages_per_step": st["diff_cell_stages"] / max(st["cell_updates"], 1),
-                       "graph": True, "rkl2_stages_per_launch": g.get_fusion()},
+                       "graph": True, "rkl2_stages_per_launch": g.get_fusion(),
+                       "ms_per_step_split": {"rkl2": st["diff_ms"] / args.steps,
+                                             "advection": st["adv_ms"] / args.steps,
+                                             "rest": (ms - st["diff_ms"] - st["adv_ms"]) / args.steps}},
             "roofline": {"bound": "hbm",
                          "kernel": ("rkl2_fused_kernel (4 RKL2 stages per launch)" if g.get_fusion() == 4
                                     else "rkl2_stage_kernel<float>"),

@@ -127,10 +127,12 @@ constexpr int STRIP = 4 * LANES - 2 * K;   // output columns of one warp strip (
 constexpr int WARPS = 8;         // strips per block
 constexpr int PB = K;            // rows next to each pole owned by the cap blocks
 constexpr int NB = PB + K + 1;   // rows a cap block holds (pole row + PB + K halo rows)
-constexpr int D = 6;             // rows of asynchronous-copy lookahead per warp
-constexpr int DG = D + K;        // G ring depth (levels 1..K read G up to K rows back)
+constexpr int D = 4;             // rows of asynchronous-copy lookahead per warp (a power of 2)
+constexpr int DG = 2 * D;        // G ring depth, a power of 2 >= D + K (level m reads G m rows back)
 constexpr int RING_F4 = (2 * D + DG) * LANES;   // float4 slots of one warp's rings
-constexpr size_t kSmemBytes = sizeof(float) * 4 * RING_F4 * WARPS;
+constexpr int GROWS = BAND + 3 * K;             // geometry rows of one work item (rows tmin-K ..)
+constexpr size_t kSmemBytes = sizeof(float) * 4 * (RING_F4 + 2 * GROWS) * WARPS;
+static_assert((D & (D - 1)) == 0 && (DG & (DG - 1)) == 0 && DG >= D + K, "ring sizes");
 // A grid shape can use the fused path when the interior band is non-empty.
 inline bool shape_ok(int nt, int np) { return nt >= 2 * NB + 2 && np >= 16; }
 }  // namespace fused

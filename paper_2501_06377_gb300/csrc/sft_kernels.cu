@@ -423,20 +423,22 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
 // Interior: one warp owns a strip of 128 longitudes (a float4 per lane) and
 // marches down a band of rows.  For every RKL2 level (the two inputs
 // delta_{j-2}, delta_{j-1} and the K levels it computes) the lane keeps a
-// rolling window of three rows in registers; at each row step it loads one
+// rolling window of three rows in registers; at each row step it takes one
 // new row of the inputs and computes level m at the row m above, so level K
-// leaves the pipeline K rows behind the loads.  phi neighbours come from
-// warp shuffles.  Lanes 0 and 31 are the K-point phi halo and the first and
-// last K rows of the band the theta halo: their values go stale from the
-// edge inward, one point per level, and are never stored.  No shared
-// memory, no barriers.
+// leaves the pipeline K rows behind the loads.  The inputs stream through
+// per-warp shared-memory rings (cp.async, D rows ahead); phi neighbours come
+// from warp shuffles.  Lanes 0 and 31 are the K-point phi halo and the first
+// and last K rows of the band the theta halo: their values go stale from the
+// edge inward, one point per level, and are never stored.  No block barrier
+// after the start.
 // Caps: the NB = PB + K + 1 rows next to each pole, full ring width, in an
 // L2-resident global scratch, with the FP64 ring sum of App. A done by the
 // block at every level (the only place that needs the whole ring).
 // Interior bands start at row PB+1 = K+1, so their halo never reaches a pole.
 // HBM traffic per pass: read delta_{j-2}, delta_{j-1}, G, write two
 // increments: 20 B per cell per K stages instead of 16 B per stage.
-// The per-point arithmetic is written exactly as in rkl2_stage_kernel.
+// The cap blocks use the per-point arithmetic of rkl2_stage_kernel; the
+// interior folds it into per-row coefficients (other rounding, same stage).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -447,7 +449,6 @@ __device__ __forceinline__ float rkl2_point(const RowGeo<float>& g, const Coef<f
   return cf.mu * c + cf.nu * d2 + mutdt * L + cf.gsum * gv;
 }
 
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
@@ -470,67 +471,63 @@ __device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_g
 template <int N>
 __device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Four consecutive longitudes starting at column c0 (periodic), as a float4.
-__device__ __forceinline__ float4 load_cols(const float* row, int c0, int np, bool vec) {
-  if (vec) return ldg4(row + c0);
-  float v[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    int c = c0 + e;
-    c = c >= np ? c - np : c;
-    v[e] = __ldg(row + c);
-  }
-  return make_float4(v[0], v[1], v[2], v[3]);
-}
-
 // One level update of a lane's 4 points; l/r neighbours across lanes.
 // The 5-point operator and the increment-form RKL2 combination are folded
-// into per-row coefficients:  o = a0 c + a1 up + a2 dn + a3 (l + r)
-// + nu d2 + gsum G  with a1..a3 = mu~ nu dt (cN, cS, cE) and
-// a0 = mu - mu~ nu dt (cN + cS + 2 cE)  (the same stage, other rounding).
-struct RowCoef {
-  float a0, a1, a2, a3, nu, gs;
+// into per-(row, level) coefficients
+//   o = a0 c + a1 up + a2 dn + a3 (l + r) + nu d2 + gsum G,
+//   a1..a3 = mu~ nu dt (cN, cS, cE),  a0 = mu + mu~ nu dt cC,
+//   cC = -(cN + cS + 2 cE)
+// (the same stage as rkl2_point, other rounding), evaluated on (x, y) and
+// (z, w) pairs with the packed f32x2 FMA: the same IEEE operations per
+// element as the scalar forms.
+struct LevelK {  // per-level constants, each duplicated into a pair
+  float2 mu, md, nu, gs;
 };
 
-__device__ __forceinline__ RowCoef row_coef(const float4 g, const Coef<float>& cf, float nudt) {
-  // g = (cN, cS, cE, .): the first four fields of RowGeo<float>
-  const float md = cf.mut * nudt;
-  RowCoef k;
-  k.a1 = md * g.x;
-  k.a2 = md * g.y;
-  k.a3 = md * g.z;
-  k.a0 = cf.mu - (k.a1 + k.a2 + 2.f * k.a3);
-  k.nu = cf.nu;
-  k.gs = cf.gsum;
-  return k;
-}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
-__device__ __forceinline__ float point2(const RowCoef& k, float c, float up, float dn, float l, float r,
-                                        float d2, float gv) {
-  return fmaf(k.a0, c, fmaf(k.a1, up, fmaf(k.a2, dn, fmaf(k.a3, l + r, fmaf(k.nu, d2, k.gs * gv)))));
-}
-
-__device__ __forceinline__ float4 level_update(const RowCoef& k, float4 c, float4 up, float4 dn, float4 d2,
-                                               float4 gv) {
+__device__ __forceinline__ float4 level_update(const LevelK& q, float4 g0, float4 g1, float4 c, float4 up,
+                                               float4 dn, float4 d2, float4 gv) {
+  // g0 = (cN, cN, cS, cS), g1 = (cE, cE, cC, cC) of the row
+  const float2 a1 = __fmul2_rn(q.md, lo2(g0));
+  const float2 a2 = __fmul2_rn(q.md, hi2(g0));
+  const float2 a3 = __fmul2_rn(q.md, lo2(g1));
+  const float2 a0 = __ffma2_rn(q.md, hi2(g1), q.mu);
   const float l = __shfl_up_sync(0xffffffffu, c.w, 1);
   const float r = __shfl_down_sync(0xffffffffu, c.x, 1);
-  float4 o;
-  o.x = point2(k, c.x, up.x, dn.x, l, c.y, d2.x, gv.x);
-  o.y = point2(k, c.y, up.y, dn.y, c.x, c.z, d2.y, gv.y);
-  o.z = point2(k, c.z, up.z, dn.z, c.y, c.w, d2.z, gv.z);
-  o.w = point2(k, c.w, up.w, dn.w, c.z, r, d2.w, gv.w);
-  return o;
+  const float2 h01 = make_float2(l + c.y, c.x + c.z);
+  const float2 h23 = make_float2(c.y + c.w, c.z + r);
+  float2 o01 = __fmul2_rn(q.gs, lo2(gv));
+  float2 o23 = __fmul2_rn(q.gs, hi2(gv));
+  o01 = __ffma2_rn(q.nu, lo2(d2), o01);
+  o23 = __ffma2_rn(q.nu, hi2(d2), o23);
+  o01 = __ffma2_rn(a3, h01, o01);
+  o23 = __ffma2_rn(a3, h23, o23);
+  o01 = __ffma2_rn(a2, lo2(dn), o01);
+  o23 = __ffma2_rn(a2, hi2(dn), o23);
+  o01 = __ffma2_rn(a1, lo2(up), o01);
+  o23 = __ffma2_rn(a1, hi2(up), o23);
+  o01 = __ffma2_rn(a0, lo2(c), o01);
+  o23 = __ffma2_rn(a0, hi2(c), o23);
+  return make_float4(o01.x, o01.y, o23.x, o23.y);
 }
 
 // Lane state of the interior march.  Win[l][slot] holds level l (0..K-1) at
 // the row whose index mod 3 is slot; level l's window holds rows t-l-2..t-l.
 // The level j-2 input is only needed pointwise one row later (d2m1), level K
-// only at its output step, and the next row's inputs are prefetched one row
-// ahead (pc, pa, pg) so their latency overlaps a whole row of arithmetic.
+// only at its output step.  The inputs arrive through per-warp shared-memory
+// rings filled D rows ahead by cp.async (each lane copies its own float4, so
+// a lane only ever reads what it copied itself); G keeps K more rows because
+// level m reads it m rows behind the loads.  The band's row geometry sits in
+// shared memory as coefficient pairs, staged once per work item.
 struct March {
   float4 Win[fused::K][3];
-  float4 d2m1;           // delta_{j-2} at row t-1
-  float4 *rc, *ra, *rg;  // this warp's shared-memory rings (C, A: D rows; G: DG rows)
+  float4 d2m1;               // delta_{j-2} at row t-1
+  float4 *rc, *ra, *rg;      // rings: C, A (D rows), G (DG rows)
+  const float4* geo;         // 2 float4 per row; row r at 2 (r - gbase)
+  int gbase;
+  LevelK lv[fused::K];
 };
 
 // Issue the asynchronous copies of row r's inputs into the rings (one commit group).
@@ -539,55 +536,62 @@ __device__ __forceinline__ void march_issue(March& S, int r, int t_end, const fl
                                             int lane) {
   if (r <= t_end) {
     const int64_t ro = (int64_t)r * pitch;
-    async_cols(S.rc + (r % fused::D) * fused::LANES + lane, gC + ro, col, np, vec);
-    if (!zero_m2) async_cols(S.ra + (r % fused::D) * fused::LANES + lane, gA + ro, col, np, vec);
-    async_cols(S.rg + (r % fused::DG) * fused::LANES + lane, gG + ro, col, np, vec);
+    const int sl = (r & (fused::D - 1)) * fused::LANES + lane;
+    async_cols(S.rc + sl, gC + ro, col, np, vec);
+    if (!zero_m2) async_cols(S.ra + sl, gA + ro, col, np, vec);
+    async_cols(S.rg + (r & (fused::DG - 1)) * fused::LANES + lane, gG + ro, col, np, vec);
   }
   async_commit();  // empty groups past the band keep the group count uniform
 }
 
-template <int P>
-__device__ __forceinline__ void march_row(March& S, int t, int kk, int tmin, int t_end, const float* gA,
-                                          const float* gC, const float* gG, const RowGeo<float>* geo,
-                                          const Coef<float>* cf, float nudt, int pitch, int np,
-                                          int col, bool vec, bool zero_m2, int J0, int J1, bool fin,
-                                          float* oA, float* oC, float* Bs, bool lane_out, int n_out,
-                                          bool& bad, int lane) {
+// One row step t (phase P = t mod 3).  FULL: all K levels run (kk == K).
+// Rows above the first loaded one (t - m < tmin during the first K steps)
+// are computed from stale ring slots and zero windows; they only feed levels
+// at rows that never reach an output (level m is needed from row tmin + m).
+template <int P, bool FULL>
+__device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, const float* gA,
+                                          const float* gC, const float* gG, int pitch, int np, int col,
+                                          bool vec, bool zero_m2, int J0, bool fin, float* oA, float* oC,
+                                          float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
   using namespace fused;
   // request row t+D-1 (into the slots of rows t-1 / t-1-K, already consumed),
   // then wait until row t has landed: D groups are in flight at most
   march_issue(S, t + D - 1, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
   async_wait<D - 1>();
-  S.Win[0][P] = S.rc[(t % D) * LANES + lane];
-  const float4 a_t = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : S.ra[(t % D) * LANES + lane];
+  const int cs = (t & (D - 1)) * LANES + lane;
+  S.Win[0][P] = S.rc[cs];
+  const float4 a_t = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : S.ra[cs];
   float4 top = make_float4(0.f, 0.f, 0.f, 0.f);  // level K at row t-K
 #pragma unroll
   for (int m = 1; m <= K; ++m) {
-    if (m <= kk && t - m >= tmin) {  // rows above the first loaded one are never needed
+    if (FULL || m <= kk) {
       const int row = t - m;
       const int sc = ((P - m) % 3 + 3) % 3;       // slot of row t-m in level m-1's window
       const int su = ((P - m - 1) % 3 + 3) % 3;   // row t-m-1
       const int sd = ((P - m + 1) % 3 + 3) % 3;   // row t-m+1
-      const RowCoef k = row_coef(*reinterpret_cast<const float4*>(geo + row), cf[m - 1], nudt);
+      const float4* gr = S.geo + 2 * (row - S.gbase);
       const float4 d2 = m == 1 ? S.d2m1 : S.Win[m - 2][sc];
-      const float4 gv = S.rg[(row % DG) * LANES + lane];
-      const float4 o = level_update(k, S.Win[m - 1][sc], S.Win[m - 1][su], S.Win[m - 1][sd], d2, gv);
+      const float4 gv = S.rg[(row & (DG - 1)) * LANES + lane];
+      const float4 o = level_update(S.lv[m - 1], gr[0], gr[1], S.Win[m - 1][sc], S.Win[m - 1][su],
+                                    S.Win[m - 1][sd], d2, gv);
       if (m < K) S.Win[m][sc] = o;
       else top = o;
     }
   }
   S.d2m1 = a_t;
-  // leave the pipeline: level kk (and kk-1) at row t - kk
-  const int orow = t - kk;
-  if (orow >= J0 && orow < J1 && lane_out) {
+  // leave the pipeline: level kk (and kk-1) at row t - kk (always < J1)
+  const int orow = t - (FULL ? K : kk);
+  if (orow >= J0 && lane_out) {
     // slots are compile-time (unrolled m, template P) so the state stays in registers
     float4 lk = top, lk1 = S.Win[K - 1][((P - K) % 3 + 3) % 3];
+    if (!FULL) {
 #pragma unroll
-    for (int m = 1; m < K; ++m)
-      if (m == kk) {
-        lk = S.Win[m][((P - m) % 3 + 3) % 3];
-        lk1 = S.Win[m - 1][((P - m) % 3 + 3) % 3];
-      }
+      for (int m = 1; m < K; ++m)
+        if (m == kk) {
+          lk = S.Win[m][((P - m) % 3 + 3) % 3];
+          lk1 = S.Win[m - 1][((P - m) % 3 + 3) % 3];
+        }
+    }
     const int64_t go = (int64_t)orow * pitch + col;
     if (fin) {
       float4 b = n_out == 4 && vec ? ld4(Bs + go) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -622,6 +626,44 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int tmin, int
       }
     }
   }
+}
+
+// The row loop of one work item: rows tmin..t_end, unrolled by 3 so that the
+// window phase t mod 3 is a template argument.
+template <bool FULL>
+__device__ __forceinline__ void march_band(March& S, int tmin, int t_end, int kk, const float* gA,
+                                           const float* gC, const float* gG, int pitch, int np, int col,
+                                           bool vec, bool zero_m2, int J0, bool fin, float* oA, float* oC,
+                                           float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
+  for (int r = tmin; r < tmin + fused::D - 1; ++r)  // D-1 rows of lookahead before the first step
+    march_issue(S, r, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
+#define SFT_MARCH(PH, TT)                                                                        \
+  march_row<PH, FULL>(S, TT, kk, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, J0, fin, oA, oC, \
+                      Bs, lane_out, n_out, bad, lane)
+  int t = tmin;
+  const int ph = t % 3;
+  if (ph == 1) {
+    SFT_MARCH(1, t);
+    ++t;
+  }
+  if (ph != 0 && t <= t_end) {
+    SFT_MARCH(2, t);
+    ++t;
+  }
+  for (; t + 2 <= t_end; t += 3) {
+    SFT_MARCH(0, t);
+    SFT_MARCH(1, t + 1);
+    SFT_MARCH(2, t + 2);
+  }
+  if (t <= t_end) {
+    SFT_MARCH(0, t);
+    ++t;
+  }
+  if (t <= t_end) {
+    SFT_MARCH(1, t);
+    ++t;
+  }
+#undef SFT_MARCH
 }
 
 }  // namespace
@@ -733,51 +775,45 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   const int first_out = strip * STRIP + 4 * (lane - 1);
   const bool lane_out = lane >= 1 && lane <= 30 && first_out < np;
   const int n_out = lane_out ? min(4, np - first_out) : 0;
-  const Coef<float>* cf = s_cf;
   extern __shared__ __align__(16) float4 rings[];
+  const int tmin = J0 - K;        // first row loaded
+  const int t_end = J1 - 1 + kk;  // last row loaded
   March S;
   S.rc = rings + warp * RING_F4;
   S.ra = S.rc + D * LANES;
   S.rg = S.ra + D * LANES;
+  // band geometry as coefficient pairs, rows tmin-K .. tmin-K+GROWS-1 (clamped)
+  float4* sg = rings + WARPS * RING_F4 + warp * 2 * GROWS;
+  S.geo = sg;
+  S.gbase = tmin - K;
+  const RowGeo<float>* grow = geo + d.geo;
+  for (int i = lane; i < GROWS; i += LANES) {
+    const int row = min(max(S.gbase + i, 0), nt - 1);
+    const float cN = grow[row].cN, cS = grow[row].cS, cE = grow[row].cE;
+    const float cC = -(cN + cS + 2.f * cE);
+    sg[2 * i] = make_float4(cN, cN, cS, cS);
+    sg[2 * i + 1] = make_float4(cE, cE, cC, cC);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const Coef<float> c = s_cf[m];
+    const float md = c.mut * nudt;
+    S.lv[m] = LevelK{make_float2(c.mu, c.mu), make_float2(md, md), make_float2(c.nu, c.nu),
+                     make_float2(c.gsum, c.gsum)};
+  }
 #pragma unroll
   for (int l = 0; l < K; ++l)
 #pragma unroll
     for (int q = 0; q < 3; ++q) S.Win[l][q] = make_float4(0.f, 0.f, 0.f, 0.f);
   S.d2m1 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const RowGeo<float>* grow = geo + d.geo;
   bool bad = false;
-  const int tmin = J0 - K;        // first row loaded
-  const int t_end = J1 - 1 + kk;  // last row loaded
-  for (int r = tmin; r < tmin + D - 1; ++r)  // D-1 rows of lookahead before the first step
-    march_issue(S, r, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
-#define SFT_MARCH(PH, TT)                                                                         \
-  march_row<PH>(S, TT, kk, tmin, t_end, gA, gC, gG, grow, cf, nudt, pitch, np, col, vec, zero_m2, \
-                J0, J1, fin, oA, oC, Bs, lane_out, n_out, bad, lane)
-  // the phase t mod 3 is a template argument: the row loop is unrolled by 3
-  int t = tmin;
-  const int ph = t % 3;
-  if (ph == 1) {
-    SFT_MARCH(1, t);
-    ++t;
-  }
-  if (ph != 0 && t <= t_end) {
-    SFT_MARCH(2, t);
-    ++t;
-  }
-  for (; t + 2 <= t_end; t += 3) {
-    SFT_MARCH(0, t);
-    SFT_MARCH(1, t + 1);
-    SFT_MARCH(2, t + 2);
-  }
-  if (t <= t_end) {
-    SFT_MARCH(0, t);
-    ++t;
-  }
-  if (t <= t_end) {
-    SFT_MARCH(1, t);
-    ++t;
-  }
-#undef SFT_MARCH
+  if (kk == K)
+    march_band<true>(S, tmin, t_end, kk, gA, gC, gG, pitch, np, col, vec, zero_m2, J0, fin, oA, oC, Bs,
+                     lane_out, n_out, bad, lane);
+  else
+    march_band<false>(S, tmin, t_end, kk, gA, gC, gG, pitch, np, col, vec, zero_m2, J0, fin, oA, oC, Bs,
+                      lane_out, n_out, bad, lane);
   async_wait<0>();  // no copy outlives the block
   if (bad) atomicOr(status, 1);
 }

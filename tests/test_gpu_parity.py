@@ -293,9 +293,9 @@ def test_error_codes():
     [(129, 256), (64, 136), (129, 256)],
 ])
 def test_fused_rkl2_matches_single_stage_launches(shapes):
-    """Four RKL2 stages per launch (shared-memory tiles with a 4-point halo,
-    full-ring cap blocks) against one launch per stage: the same per-point
-    formulas, so the maps agree to FP32 rounding."""
+    """Four RKL2 stages per launch (register march over bands with a 4-point
+    halo, full-ring cap blocks) against one launch per stage: the same stages
+    in another rounding order, so the maps agree to FP32 rounding."""
     outs = {}
     for k in (1, 4):
         g, params, maps = _batch(shapes, "fp32", seed=31)
