@@ -893,46 +893,67 @@ reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __res
   double mn = INFINITY, mx = -INFINITY, amn = INFINITY;
   const double* w = aa.wpar ? aa.wpar + 4 * tl.r : nullptr;
   const int64_t obase = aa.obs_off ? aa.obs_off[tl.r] : 0;
+  T tmn = T(INFINITY), tmx = T(-INFINITY), tamn = T(INFINITY);
   for (int j = tl.j0; j < tl.j1; ++j) {
     const RowGeoD gd = geod[d.geo + j];
     const bool pole = (j == 0) || (j == d.nt - 1);
     const T* row = b + (int64_t)j * d.pitch;
-    for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
-      const T bv = row[k];
-      if (mode == RED_DIAG) {
-        const double x = double(bv);
-        if (!isfinite(x)) {
+    if (mode == RED_DIAG) {
+      // Row constants (area, cos, sin, latitude) multiply this thread's row
+      // sums once: per cell only sum x, sum max(x, 0), sum x cos(phi) and
+      // sum x sin(phi) run in FP64 (min / max are exact in T).
+      double rs = 0.0, rp = 0.0, rc = 0.0, rn = 0.0;
+      for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+        const T bv = row[k];
+        if (!isfinite(bv)) {
           acc[10] += 1.0;
           continue;
         }
-        const double ab = gd.area * x;
-        acc[0] += ab;
-        if (x > 0.0) acc[1] += ab;
-        if (x < 0.0) acc[2] += ab;
-        if (gd.lat >= lat_cut - 1e-12) { acc[3] += ab; acc[5] += gd.area; }
-        if (gd.lat <= -lat_cut + 1e-12) { acc[4] += ab; acc[6] += gd.area; }
-        acc[7] += ab * gd.cos_t;
-        acc[8] += ab * gd.sin_t * cosp[d.col + k];
-        acc[9] += ab * gd.sin_t * sinp[d.col + k];
-        mn = fmin(mn, x);
-        mx = fmax(mx, x);
-        amn = fmin(amn, fabs(x));
-      } else {
-        T x;
-        if (mode == RED_ASSIM) {
-          const int kk = pole ? 0 : k;
-          const int64_t oi = obase + (int64_t)j * d.np + kk;
-          const T F = assim_weight<T>(ldT<T>(aa.mu, oi), gd.lat, w);
-          x = F * (ldT<T>(aa.obs, oi) - bv);
-        } else {
-          x = bv;
-        }
-        const double ax = gd.area * double(x);
-        if (x > T(0)) acc[0] += ax;
-        if (x < T(0)) acc[1] += ax;
+        const double x = double(bv);
+        rs += x;
+        rp += bv > T(0) ? x : 0.0;
+        rc = fma(x, cosp[d.col + k], rc);
+        rn = fma(x, sinp[d.col + k], rn);
+        tmn = bv < tmn ? bv : tmn;
+        tmx = bv > tmx ? bv : tmx;
+        const T ab = bv < T(0) ? -bv : bv;
+        tamn = ab < tamn ? ab : tamn;
       }
+      acc[0] += gd.area * rs;
+      acc[1] += gd.area * rp;
+      acc[2] += gd.area * (rs - rp);
+      if (gd.lat >= lat_cut - 1e-12) {
+        acc[3] += gd.area * rs;
+        if (threadIdx.x == 0) acc[5] += gd.area * d.np;
+      }
+      if (gd.lat <= -lat_cut + 1e-12) {
+        acc[4] += gd.area * rs;
+        if (threadIdx.x == 0) acc[6] += gd.area * d.np;
+      }
+      acc[7] += gd.area * gd.cos_t * rs;
+      acc[8] += gd.area * gd.sin_t * rc;
+      acc[9] += gd.area * gd.sin_t * rn;
+      continue;
+    }
+    for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+      const T bv = row[k];
+      T x;
+      if (mode == RED_ASSIM) {
+        const int kk = pole ? 0 : k;
+        const int64_t oi = obase + (int64_t)j * d.np + kk;
+        const T F = assim_weight<T>(ldT<T>(aa.mu, oi), gd.lat, w);
+        x = F * (ldT<T>(aa.obs, oi) - bv);
+      } else {
+        x = bv;
+      }
+      const double ax = gd.area * double(x);
+      if (x > T(0)) acc[0] += ax;
+      if (x < T(0)) acc[1] += ax;
     }
   }
+  mn = double(tmn);
+  mx = double(tmx);
+  amn = double(tamn);
   double* out = partials + (int64_t)blockIdx.x * kDiagFields;
   const int nf = mode == RED_DIAG ? 11 : 2;
   for (int f = 0; f < nf; ++f) {
