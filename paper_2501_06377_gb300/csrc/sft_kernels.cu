@@ -698,15 +698,33 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   const bool zero_m2 = j0 == 2;  // delta_0 = 0
 
   if (kind != 0) {
+    // Every loop below goes row by row and gives each thread CU columns at a
+    // time: their loads are all issued before the stores, so CU scratch (L2)
+    // round trips are in flight per thread instead of one.
+    constexpr int CU = 8;
     const bool north = kind == 1;
     const int base = north ? 0 : nt - NB;  // global row of local row 0
     float* prv = polar + d.poff + (north ? 0 : 2 * NB * pitch);  // level m-2, updated to m
     float* cur = prv + NB * pitch;                                // level m-1
-    for (int idx = threadIdx.x; idx < NB * np; idx += kThreads) {
-      const int i = idx / np, k = idx - i * np;
-      const int64_t go = (int64_t)(base + i) * pitch + k, lo = (int64_t)i * pitch + k;
-      cur[lo] = gC[go];
-      prv[lo] = zero_m2 ? 0.f : gA[go];
+    for (int i = 0; i < NB; ++i) {
+      const int64_t go = (int64_t)(base + i) * pitch, lo = (int64_t)i * pitch;
+      for (int k0 = threadIdx.x; k0 < np; k0 += CU * kThreads) {
+        float vc[CU], va[CU];
+#pragma unroll
+        for (int q = 0; q < CU; ++q) {
+          const int k = min(k0 + q * kThreads, np - 1);  // columns past np repeat np-1, not stored
+          vc[q] = gC[go + k];
+          va[q] = zero_m2 ? 0.f : gA[go + k];
+        }
+#pragma unroll
+        for (int q = 0; q < CU; ++q) {
+          const int k = k0 + q * kThreads;
+          if (k < np) {
+            cur[lo + k] = vc[q];
+            prv[lo + k] = va[q];
+          }
+        }
+      }
     }
     __syncthreads();
     const int ip = north ? 0 : NB - 1;  // pole row (local)
@@ -722,20 +740,35 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
       double acc = 0.0;
       for (int k = threadIdx.x; k < np; k += blockDim.x) acc += double(cur[(int64_t)ia * pitch + k]) - yp;
       const double Lp = shc[d.shape].pole_diff * block_sum(acc, sm);
-      const int nrow = i_hi - i_lo + 1;
-      for (int idx = threadIdx.x; idx < nrow * np; idx += kThreads) {
-        const int q = idx / np, k = idx - q * np, i = i_lo + q;
+      for (int i = i_lo; i <= i_hi; ++i) {
         const float* cr = cur + (int64_t)i * pitch;
+        float* pr = prv + (int64_t)i * pitch;
+        const float* gr = gG + (int64_t)(base + i) * pitch;
         const RowGeo<float> g = geo[d.geo + base + i];
-        const int64_t lo = (int64_t)i * pitch + k;
-        prv[lo] = rkl2_point(g, cf, mutdt, cr[k], cr[k - pitch], cr[k + pitch],
-                             cr[k == 0 ? np - 1 : k - 1], cr[k == np - 1 ? 0 : k + 1], prv[lo],
-                             gG[(int64_t)(base + i) * pitch + k]);
+        for (int k0 = threadIdx.x; k0 < np; k0 += CU * kThreads) {
+          float vc[CU], vu[CU], vd[CU], vl[CU], vr[CU], vp[CU], vg[CU];
+#pragma unroll
+          for (int q = 0; q < CU; ++q) {
+            const int k = min(k0 + q * kThreads, np - 1);
+            vc[q] = cr[k];
+            vu[q] = cr[k - pitch];
+            vd[q] = cr[k + pitch];
+            vl[q] = cr[k == 0 ? np - 1 : k - 1];
+            vr[q] = cr[k == np - 1 ? 0 : k + 1];
+            vp[q] = pr[k];
+            vg[q] = gr[k];
+          }
+#pragma unroll
+          for (int q = 0; q < CU; ++q) {
+            const int k = k0 + q * kThreads;
+            if (k < np) pr[k] = rkl2_point(g, cf, mutdt, vc[q], vu[q], vd[q], vl[q], vr[q], vp[q], vg[q]);
+          }
+        }
       }
       pole_last = double(cf.mu) * yp + double(cf.nu) * pp + double(cf.mut) * double(nudt) * Lp +
                   double(cf.gsum) * gp;
-      const float vp = float(pole_last);
-      for (int k = threadIdx.x; k < np; k += kThreads) prv[(int64_t)ip * pitch + k] = vp;
+      const float vpole = float(pole_last);
+      for (int k = threadIdx.x; k < np; k += kThreads) prv[(int64_t)ip * pitch + k] = vpole;
       __syncthreads();
       float* t = cur;
       cur = prv;
@@ -743,16 +776,29 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
     }
     const int o_lo = north ? 0 : NB - 1 - PB, o_hi = north ? PB : NB - 1;
     bool bad = false;
-    for (int idx = threadIdx.x; idx < (o_hi - o_lo + 1) * np; idx += kThreads) {
-      const int q = idx / np, k = idx - q * np, i = o_lo + q;
-      const int64_t go = (int64_t)(base + i) * pitch + k, lo = (int64_t)i * pitch + k;
-      if (fin) {
-        const float v = i == ip ? float(double(Bs[go]) + pole_last) : Bs[go] + cur[lo];
-        bad |= !isfinite(v);
-        Bs[go] = v;
-      } else {
-        oC[go] = cur[lo];
-        oA[go] = prv[lo];
+    for (int i = o_lo; i <= o_hi; ++i) {
+      const int64_t go = (int64_t)(base + i) * pitch, lo = (int64_t)i * pitch;
+      for (int k0 = threadIdx.x; k0 < np; k0 += CU * kThreads) {
+        float vc[CU], va[CU];
+#pragma unroll
+        for (int q = 0; q < CU; ++q) {
+          const int k = min(k0 + q * kThreads, np - 1);
+          vc[q] = cur[lo + k];
+          va[q] = fin ? Bs[go + k] : prv[lo + k];
+        }
+#pragma unroll
+        for (int q = 0; q < CU; ++q) {
+          const int k = k0 + q * kThreads;
+          if (k >= np) continue;
+          if (fin) {
+            const float v = i == ip ? float(double(va[q]) + pole_last) : va[q] + vc[q];
+            bad |= !isfinite(v);
+            Bs[go + k] = v;
+          } else {
+            oC[go + k] = vc[q];
+            oA[go + k] = va[q];
+          }
+        }
       }
     }
     if (bad) atomicOr(status, 1);
