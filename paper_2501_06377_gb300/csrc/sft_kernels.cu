@@ -548,12 +548,13 @@ __device__ __forceinline__ void march_issue(March& S, int r, int t_end, const fl
 // Rows above the first loaded one (t - m < tmin during the first K steps)
 // are computed from stale ring slots and zero windows; they only feed levels
 // at rows that never reach an output (level m is needed from row tmin + m).
-template <int P, bool FULL>
+template <int P, bool FULL, bool VEC>
 __device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, const float* gA,
                                           const float* gC, const float* gG, int pitch, int np, int col,
-                                          bool vec, bool zero_m2, int J0, bool fin, float* oA, float* oC,
+                                          bool zero_m2, int J0, bool fin, float* oA, float* oC,
                                           float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
   using namespace fused;
+  constexpr bool vec = VEC;
   // request row t+D-1 (into the slots of rows t-1 / t-1-K, already consumed),
   // then wait until row t has landed: D groups are in flight at most
   march_issue(S, t + D - 1, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
@@ -630,16 +631,17 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, co
 
 // The row loop of one work item: rows tmin..t_end, unrolled by 3 so that the
 // window phase t mod 3 is a template argument.
-template <bool FULL>
+template <bool FULL, bool VEC>
 __device__ __forceinline__ void march_band(March& S, int tmin, int t_end, int kk, const float* gA,
                                            const float* gC, const float* gG, int pitch, int np, int col,
-                                           bool vec, bool zero_m2, int J0, bool fin, float* oA, float* oC,
+                                           bool zero_m2, int J0, bool fin, float* oA, float* oC,
                                            float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
+  constexpr bool vec = VEC;
   for (int r = tmin; r < tmin + fused::D - 1; ++r)  // D-1 rows of lookahead before the first step
     march_issue(S, r, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
 #define SFT_MARCH(PH, TT)                                                                        \
-  march_row<PH, FULL>(S, TT, kk, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, J0, fin, oA, oC, \
-                      Bs, lane_out, n_out, bad, lane)
+  march_row<PH, FULL, VEC>(S, TT, kk, t_end, gA, gC, gG, pitch, np, col, zero_m2, J0, fin, oA, oC, \
+                           Bs, lane_out, n_out, bad, lane)
   int t = tmin;
   const int ph = t % 3;
   if (ph == 1) {
@@ -854,12 +856,19 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
     for (int q = 0; q < 3; ++q) S.Win[l][q] = make_float4(0.f, 0.f, 0.f, 0.f);
   S.d2m1 = make_float4(0.f, 0.f, 0.f, 0.f);
   bool bad = false;
-  if (kk == K)
-    march_band<true>(S, tmin, t_end, kk, gA, gC, gG, pitch, np, col, vec, zero_m2, J0, fin, oA, oC, Bs,
-                     lane_out, n_out, bad, lane);
-  else
-    march_band<false>(S, tmin, t_end, kk, gA, gC, gG, pitch, np, col, vec, zero_m2, J0, fin, oA, oC, Bs,
-                      lane_out, n_out, bad, lane);
+  // (kk == K, np % 4 == 0) is the hot instance; the others serve the last
+  // pass of a realization and grids whose rows are not float4-aligned
+#define SFT_BAND(F, V)                                                                              \
+  march_band<F, V>(S, tmin, t_end, kk, gA, gC, gG, pitch, np, col, zero_m2, J0, fin, oA, oC, Bs, \
+                   lane_out, n_out, bad, lane)
+  if (vec) {
+    if (kk == K) SFT_BAND(true, true);
+    else SFT_BAND(false, true);
+  } else {
+    if (kk == K) SFT_BAND(true, false);
+    else SFT_BAND(false, false);
+  }
+#undef SFT_BAND
   async_wait<0>();  // no copy outlives the block
   if (bad) atomicOr(status, 1);
 }
