@@ -125,9 +125,12 @@ typedef struct {
   double diff_cell_stages;   /* ntheta*nphi x RKL2 stages executed */
   int64_t kernel_launches;   /* library kernels launched (graph nodes included) */
   int64_t graph_launches;    /* CUDA graph launches */
-  double diff_ms;            /* with profiling on: device time of the RKL2 stage kernels */
+  double diff_ms;            /* with profiling on: device time of the RKL2 stages (stage 1 to the
+                                last stage, both launch chains of the fused passes) */
   double adv_ms;             /* with profiling on: device time of the advection stage kernels */
-  int64_t diff_launches;     /* with profiling on: RKL2 stage kernels timed */
+  int64_t diff_launches;     /* with profiling on: RKL2 passes timed (stage 1, then one per
+                                fused pass of K stages whatever the number of launch chains;
+                                one per stage on the single-stage path) */
   int64_t adv_launches;      /* with profiling on: advection stage kernels timed */
   double diff_bytes;         /* algorithmic HBM bytes of the timed RKL2 stage kernels */
   double adv_bytes;          /* algorithmic HBM bytes of the timed advection stage kernels */

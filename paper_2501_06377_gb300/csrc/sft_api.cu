@@ -62,8 +62,14 @@ struct RealInfo {
 
 struct Config {
   bool fused = false;            // built for the fused RKL2 path
-  Tile* d_ftiles = nullptr;      // fused-kernel tiles (caps first, then interior)
-  std::vector<int> fused_tiles;  // [j0] = fused tiles launched by the pass starting at stage j0
+  Tile* d_ftiles = nullptr;      // fused-kernel tiles of every chain (per realization: caps, then interior)
+  // The fused passes run as n_chains independent launch chains on their own
+  // streams (realizations dealt alternately from the stage-sorted order), so
+  // one chain's launch fills the SMs while the other's drains.
+  int n_chains = 1;
+  int fbase[2] = {0, 0};                // first tile of each chain in d_ftiles
+  std::vector<int> fused_tiles[2];      // [chain][j0] = tiles launched by the pass starting at stage j0
+  int64_t fused_launches = 0;           // non-empty fused launches per step
   std::vector<double> dt;        // per wave member (wave order)
   std::vector<int> s;            // per wave member
   std::vector<int> tr;           // tile rows per shape at build time
@@ -139,6 +145,8 @@ struct sft_grid {
   bool profiling = false;
   uint64_t use_counter = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t side = nullptr;                  // second chain of fused RKL2 passes
+  cudaEvent_t fork = nullptr, join = nullptr;   // ordering events (no timing)
   sft_stats stats{};
 };
 
@@ -325,6 +333,9 @@ void free_handle(sft_handle h) {
   cudaFree(h->d_obs);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -420,17 +431,23 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
   if (c->fused) {
     // fused passes start at stages 2, 2+K, 2+2K, ...; stage 1 uses the
     // single-stage kernel (it forms G = dt L(Y_0)).
+    c->n_chains = order.size() >= 2 ? 2 : 1;
     std::vector<Tile> ft;
-    std::vector<int> fend;
-    for (int i : order) {
-      append_fused_tiles(h, w.reals[i], ft);
-      fend.push_back((int)ft.size());
-    }
-    c->fused_tiles.assign(c->smax + 1, 0);
-    for (int j0 = 2; j0 <= c->smax; j0 += fused::K) {
-      int n = 0;
-      while (n < (int)order.size() && s[order[n]] >= j0) ++n;
-      c->fused_tiles[j0] = n == 0 ? 0 : fend[n - 1];
+    for (int ch = 0; ch < c->n_chains; ++ch) {
+      c->fbase[ch] = (int)ft.size();
+      std::vector<int> mem, fend;  // chain members (descending s) and their tile ends
+      for (size_t q = ch; q < order.size(); q += c->n_chains) mem.push_back(order[q]);
+      for (int i : mem) {
+        append_fused_tiles(h, w.reals[i], ft);
+        fend.push_back((int)ft.size() - c->fbase[ch]);
+      }
+      c->fused_tiles[ch].assign(c->smax + 1, 0);
+      for (int j0 = 2; j0 <= c->smax; j0 += fused::K) {
+        int n = 0;
+        while (n < (int)mem.size() && s[mem[n]] >= j0) ++n;
+        c->fused_tiles[ch][j0] = n == 0 ? 0 : fend[n - 1];
+        if (n > 0) c->fused_launches += 1;
+      }
     }
     c->diff_words = 0.0;
     for (int i : order) {
@@ -535,15 +552,26 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
                                      h->d_status));
     float* P[4] = {ptr<float>(h->work[1]), ptr<float>(h->work[2]), ptr<float>(h->work[3]),
                    ptr<float>(h->work[4])};
-    int in = 0;  // input pair (P[in], P[in+1]) = (delta_{j0-2}, delta_{j0-1})
-    for (int j0 = 2; j0 <= c.smax; j0 += fused::K) {
-      const int out = 2 - in;
-      SFT_CUDA(h, launch_rkl2_fused(c.fused_tiles[j0], st, c.d_ftiles, h->d_desc, c.d_sp,
-                                    ptr<const RowGeo<float>>(h->d_geo), h->d_shc,
-                                    ptr<const Coef<float>>(c.d_coef), ptr<float>(h->state),
-                                    ptr<const float>(h->work[0]), P[in], P[in + 1], P[out],
-                                    P[out + 1], ptr<float>(h->polar), j0, h->d_status));
-      in = out;
+    if (c.n_chains == 2) {  // fork: the side chain starts after stage 1
+      SFT_CUDA(h, cudaEventRecord(h->fork, st));
+      SFT_CUDA(h, cudaStreamWaitEvent(h->side, h->fork, 0));
+    }
+    for (int ch = 0; ch < c.n_chains; ++ch) {
+      const cudaStream_t cs = ch == 0 ? st : h->side;
+      int in = 0;  // input pair (P[in], P[in+1]) = (delta_{j0-2}, delta_{j0-1})
+      for (int j0 = 2; j0 <= c.smax; j0 += fused::K) {
+        const int out = 2 - in;
+        SFT_CUDA(h, launch_rkl2_fused(c.fused_tiles[ch][j0], cs, c.d_ftiles + c.fbase[ch], h->d_desc,
+                                      c.d_sp, ptr<const RowGeo<float>>(h->d_geo), h->d_shc,
+                                      ptr<const Coef<float>>(c.d_coef), ptr<float>(h->state),
+                                      ptr<const float>(h->work[0]), P[in], P[in + 1], P[out],
+                                      P[out + 1], ptr<float>(h->polar), j0, h->d_status));
+        in = out;
+      }
+    }
+    if (c.n_chains == 2) {  // join
+      SFT_CUDA(h, cudaEventRecord(h->join, h->side));
+      SFT_CUDA(h, cudaStreamWaitEvent(st, h->join, 0));
     }
   } else {
     for (int j = 1; j <= c.smax; ++j) {
@@ -627,8 +655,10 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     if (st != SFT_OK) return st;
   }
   const int n_adv = c->n_adv_tiles > 0 ? adv_stage_count(h) : 0;
+  // RKL2 passes (one fused pass = K stages, over both chains) and launches
   const int n_diff = c->fused ? (c->smax >= 1 ? 1 + (c->smax - 1 + fused::K - 1) / fused::K : 0) : c->smax;
-  h->stats.kernel_launches += n_adv + n_diff;
+  const int64_t n_diff_launches = c->fused ? (c->smax >= 1 ? 1 + c->fused_launches : 0) : c->smax;
+  h->stats.kernel_launches += n_adv + n_diff_launches;
   h->stats.realization_steps += c->realization_steps;
   h->stats.cell_updates += c->cell_updates;
   h->stats.adv_cell_stages += c->cells_adv * (adv_stage_count(h) == 2 ? 1 : adv_stage_count(h));
@@ -991,6 +1021,9 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   CREATE_CUDA(cudaMalloc(&h->d_wpar, (size_t)n_real * 4 * sizeof(double)));
   CREATE_CUDA(cudaMalloc(&h->d_obs_off, (size_t)n_real * sizeof(int64_t)));
   for (auto& e : h->ev) CREATE_CUDA(cudaEventCreate(&e));
+  CREATE_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  CREATE_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+  CREATE_CUDA(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
   CREATE_CUDA(cudaStreamSynchronize(h->stream));
 #undef CREATE_CUDA
   *out = h;
