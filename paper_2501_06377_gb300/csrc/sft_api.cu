@@ -60,6 +60,8 @@ struct RealInfo {
   double dt_euler = 0.0;  // hours (inf when nu == 0)
 };
 
+constexpr int kMaxChains = 2;  // concurrent launch chains of the fused RKL2 passes
+
 struct Config {
   bool fused = false;            // built for the fused RKL2 path
   Tile* d_ftiles = nullptr;      // fused-kernel tiles of every chain (per realization: caps, then interior)
@@ -67,8 +69,8 @@ struct Config {
   // streams (realizations dealt alternately from the stage-sorted order), so
   // one chain's launch fills the SMs while the other's drains.
   int n_chains = 1;
-  int fbase[2] = {0, 0};                // first tile of each chain in d_ftiles
-  std::vector<int> fused_tiles[2];      // [chain][j0] = tiles launched by the pass starting at stage j0
+  int fbase[kMaxChains] = {};                 // first tile of each chain in d_ftiles
+  std::vector<int> fused_tiles[kMaxChains];   // [chain][j0] = tiles launched by the pass starting at stage j0
   int64_t fused_launches = 0;           // non-empty fused launches per step
   std::vector<double> dt;        // per wave member (wave order)
   std::vector<int> s;            // per wave member
@@ -145,8 +147,9 @@ struct sft_grid {
   bool profiling = false;
   uint64_t use_counter = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaStream_t side = nullptr;                  // second chain of fused RKL2 passes
-  cudaEvent_t fork = nullptr, join = nullptr;   // ordering events (no timing)
+  cudaStream_t side[kMaxChains] = {};           // chains 1.. of the fused RKL2 passes
+  cudaEvent_t fork = nullptr;                   // ordering events (no timing)
+  cudaEvent_t join[kMaxChains] = {};
   sft_stats stats{};
 };
 
@@ -334,8 +337,10 @@ void free_handle(sft_handle h) {
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->fork) cudaEventDestroy(h->fork);
-  if (h->join) cudaEventDestroy(h->join);
-  if (h->side) cudaStreamDestroy(h->side);
+  for (auto& e : h->join)
+    if (e) cudaEventDestroy(e);
+  for (auto& q : h->side)
+    if (q) cudaStreamDestroy(q);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -431,7 +436,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
   if (c->fused) {
     // fused passes start at stages 2, 2+K, 2+2K, ...; stage 1 uses the
     // single-stage kernel (it forms G = dt L(Y_0)).
-    c->n_chains = order.size() >= 2 ? 2 : 1;
+    c->n_chains = std::max(1, std::min<int>(kMaxChains, (int)order.size()));
     std::vector<Tile> ft;
     for (int ch = 0; ch < c->n_chains; ++ch) {
       c->fbase[ch] = (int)ft.size();
@@ -552,12 +557,12 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
                                      h->d_status));
     float* P[4] = {ptr<float>(h->work[1]), ptr<float>(h->work[2]), ptr<float>(h->work[3]),
                    ptr<float>(h->work[4])};
-    if (c.n_chains == 2) {  // fork: the side chain starts after stage 1
+    if (c.n_chains > 1) {  // fork: the side chains start after stage 1
       SFT_CUDA(h, cudaEventRecord(h->fork, st));
-      SFT_CUDA(h, cudaStreamWaitEvent(h->side, h->fork, 0));
+      for (int ch = 1; ch < c.n_chains; ++ch) SFT_CUDA(h, cudaStreamWaitEvent(h->side[ch], h->fork, 0));
     }
     for (int ch = 0; ch < c.n_chains; ++ch) {
-      const cudaStream_t cs = ch == 0 ? st : h->side;
+      const cudaStream_t cs = ch == 0 ? st : h->side[ch];
       int in = 0;  // input pair (P[in], P[in+1]) = (delta_{j0-2}, delta_{j0-1})
       for (int j0 = 2; j0 <= c.smax; j0 += fused::K) {
         const int out = 2 - in;
@@ -569,9 +574,9 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
         in = out;
       }
     }
-    if (c.n_chains == 2) {  // join
-      SFT_CUDA(h, cudaEventRecord(h->join, h->side));
-      SFT_CUDA(h, cudaStreamWaitEvent(st, h->join, 0));
+    for (int ch = 1; ch < c.n_chains; ++ch) {  // join
+      SFT_CUDA(h, cudaEventRecord(h->join[ch], h->side[ch]));
+      SFT_CUDA(h, cudaStreamWaitEvent(st, h->join[ch], 0));
     }
   } else {
     for (int j = 1; j <= c.smax; ++j) {
@@ -1021,9 +1026,11 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   CREATE_CUDA(cudaMalloc(&h->d_wpar, (size_t)n_real * 4 * sizeof(double)));
   CREATE_CUDA(cudaMalloc(&h->d_obs_off, (size_t)n_real * sizeof(int64_t)));
   for (auto& e : h->ev) CREATE_CUDA(cudaEventCreate(&e));
-  CREATE_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   CREATE_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
-  CREATE_CUDA(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+  for (int ch = 1; ch < kMaxChains; ++ch) {
+    CREATE_CUDA(cudaStreamCreateWithFlags(&h->side[ch], cudaStreamNonBlocking));
+    CREATE_CUDA(cudaEventCreateWithFlags(&h->join[ch], cudaEventDisableTiming));
+  }
   CREATE_CUDA(cudaStreamSynchronize(h->stream));
 #undef CREATE_CUDA
   *out = h;

@@ -120,15 +120,17 @@ cudaError_t launch_adv_stage(int n_tiles, cudaStream_t st, const Tile* tiles, co
                              AdvStage<T> s);
 // Fused RKL2: K stages per launch (see rkl2_fused_kernel in sft_kernels.cu).
 namespace fused {
+constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
 constexpr int K = 4;             // RKL2 stages per pass
 constexpr int BAND = 64;         // rows of one interior band (a warp marches through it)
 constexpr int LANES = 32;
-constexpr int STRIP = 4 * LANES - 2 * K;   // output columns of one warp strip (lanes 1..30)
+constexpr int HL = (K + 3) / 4;  // phi-halo lanes on each side of a strip (4 columns each, >= K)
+constexpr int STRIP = 4 * (LANES - 2 * HL);  // output columns of one warp strip (lanes HL..31-HL)
 constexpr int WARPS = 8;         // strips per block
 constexpr int PB = K;            // rows next to each pole owned by the cap blocks
 constexpr int NB = PB + K + 1;   // rows a cap block holds (pole row + PB + K halo rows)
 constexpr int D = 4;             // rows of asynchronous-copy lookahead per warp (a power of 2)
-constexpr int DG = 2 * D;        // G ring depth, a power of 2 >= D + K (level m reads G m rows back)
+constexpr int DG = pow2_at_least(D + K);  // G ring depth: level m reads G m rows back
 constexpr int RING_F4 = (2 * D + DG) * LANES;   // float4 slots of one warp's rings
 constexpr int GROWS = BAND + 3 * K;             // geometry rows of one work item (rows tmin-K ..)
 constexpr size_t kSmemBytes = sizeof(float) * 4 * (RING_F4 + 2 * GROWS) * WARPS;

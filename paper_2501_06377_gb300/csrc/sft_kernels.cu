@@ -427,9 +427,10 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
 // new row of the inputs and computes level m at the row m above, so level K
 // leaves the pipeline K rows behind the loads.  The inputs stream through
 // per-warp shared-memory rings (cp.async, D rows ahead); phi neighbours come
-// from warp shuffles.  Lanes 0 and 31 are the K-point phi halo and the first
-// and last K rows of the band the theta halo: their values go stale from the
-// edge inward, one point per level, and are never stored.  No block barrier
+// from warp shuffles.  The HL lanes at each edge (4 HL >= K columns) are the
+// phi halo and the first and last K rows of the band the theta halo: their
+// values go stale from the edge inward, one point per level, and are never
+// stored.  No block barrier
 // after the start.
 // Caps: the NB = PB + K + 1 rows next to each pole, full ring width, in an
 // L2-resident global scratch, with the FP64 ring sum of App. A done by the
@@ -527,7 +528,7 @@ struct March {
   float4 *rc, *ra, *rg;      // rings: C, A (D rows), G (DG rows)
   const float4* geo;         // 2 float4 per row; row r at 2 (r - gbase)
   int gbase;
-  LevelK lv[fused::K];
+  LevelK lv[fused::K];       // per-level constants (registers)
 };
 
 // Issue the asynchronous copies of row r's inputs into the rings (one commit group).
@@ -816,12 +817,12 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   const int strip = item % n_strips;
   const int J0 = PB + 1 + (item / n_strips) * BAND;
   const int J1 = min(J0 + BAND, nt - 1 - PB);
-  int col = (strip * STRIP - K + 4 * lane) % np;  // first of the lane's 4 columns, periodic
+  int col = (strip * STRIP - 4 * HL + 4 * lane) % np;  // first of the lane's 4 columns, periodic
   col = col < 0 ? col + np : col;
   const bool vec = (np & 3) == 0;
-  // output: lanes 1..30, columns strip*STRIP .. +STRIP-1 that are < np
-  const int first_out = strip * STRIP + 4 * (lane - 1);
-  const bool lane_out = lane >= 1 && lane <= 30 && first_out < np;
+  // output: lanes HL..31-HL, columns strip*STRIP .. +STRIP-1 that are < np
+  const int first_out = strip * STRIP + 4 * (lane - HL);
+  const bool lane_out = lane >= HL && lane < LANES - HL && first_out < np;
   const int n_out = lane_out ? min(4, np - first_out) : 0;
   extern __shared__ __align__(16) float4 rings[];
   const int tmin = J0 - K;        // first row loaded
