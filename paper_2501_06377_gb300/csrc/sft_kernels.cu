@@ -114,6 +114,12 @@ __device__ __forceinline__ T uw_flux(T v, T blo, T bhi, T auw) {
   return v * T(0.5) * ((T(1) - uw) * bhi + (T(1) + uw) * blo);
 }
 
+// The one division of a WENO half-flux: FP32 takes the hardware-approximate
+// quotient (__fdividef, a few ulp: far inside the FP32 bar of 1e-5 max|Br|),
+// FP64 the IEEE quotient.
+__device__ __forceinline__ float weno_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double weno_div(double a, double b) { return a / b; }
+
 // WENO3-CS(h) face flux (App. B) on a uniform grid, from LM_{i-2}, LM_{i-1},
 // LM_i and LP_{i-1}, LP_i, LP_{i+1}.  Weight algebra is written as
 // w0/(w0+w1) = 1 / (1 + 2 ((eps+b0)/(eps+b1))^2) with linear weights 1/3, 2/3.
@@ -122,7 +128,7 @@ __device__ __forceinline__ T weno_half(T p0, T p1, T b0, T b1, T eps) {
   const T q0 = eps + b0, q1 = eps + b1;
   const T a0 = q1 * q1;            // (1/3)/q0^2 scaled by 3 q0^2 q1^2
   const T a1 = T(2) * q0 * q0;     // (2/3)/q1^2 scaled the same way
-  return (a0 * p0 + a1 * p1) / (a0 + a1);
+  return weno_div(a0 * p0 + a1 * p1, a0 + a1);
 }
 
 template <typename T>
