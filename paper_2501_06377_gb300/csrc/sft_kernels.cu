@@ -537,18 +537,21 @@ struct March {
   LevelK lv[fused::K];       // per-level constants (registers)
 };
 
-// Issue the asynchronous copies of row r's inputs into the rings (one commit group).
+// Issue the asynchronous copies of row r's inputs into the rings (one commit
+// group; empty past the band's last row t_end, which keeps the group count
+// uniform).
+template <bool VEC>
 __device__ __forceinline__ void march_issue(March& S, int r, int t_end, const float* gA, const float* gC,
-                                            const float* gG, int pitch, int np, int col, bool vec, bool zero_m2,
+                                            const float* gG, int pitch, int np, int col, bool zero_m2,
                                             int lane) {
   if (r <= t_end) {
     const int64_t ro = (int64_t)r * pitch;
     const int sl = (r & (fused::D - 1)) * fused::LANES + lane;
-    async_cols(S.rc + sl, gC + ro, col, np, vec);
-    if (!zero_m2) async_cols(S.ra + sl, gA + ro, col, np, vec);
-    async_cols(S.rg + (r & (fused::DG - 1)) * fused::LANES + lane, gG + ro, col, np, vec);
+    async_cols(S.rc + sl, gC + ro, col, np, VEC);
+    if (!zero_m2) async_cols(S.ra + sl, gA + ro, col, np, VEC);
+    async_cols(S.rg + (r & (fused::DG - 1)) * fused::LANES + lane, gG + ro, col, np, VEC);
   }
-  async_commit();  // empty groups past the band keep the group count uniform
+  async_commit();
 }
 
 // One row step t (phase P = t mod 3).  FULL: all K levels run (kk == K).
@@ -561,31 +564,32 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, co
                                           bool zero_m2, int J0, bool fin, float* oA, float* oC,
                                           float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
   using namespace fused;
-  constexpr bool vec = VEC;
   // request row t+D-1 (into the slots of rows t-1 / t-1-K, already consumed),
   // then wait until row t has landed: D groups are in flight at most
-  march_issue(S, t + D - 1, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
+  march_issue<VEC>(S, t + D - 1, t_end, gA, gC, gG, pitch, np, col, zero_m2, lane);
   async_wait<D - 1>();
   const int cs = (t & (D - 1)) * LANES + lane;
   S.Win[0][P] = S.rc[cs];
   const float4 a_t = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : S.ra[cs];
   float4 top = make_float4(0.f, 0.f, 0.f, 0.f);  // level K at row t-K
+  const float4* gp = S.geo + 2 * (t - S.gbase);   // geometry of row t; level m reads row t-m
+  const int tg = t & (DG - 1);                    // G ring slot of row t
 #pragma unroll
   for (int m = 1; m <= K; ++m) {
     if (FULL || m <= kk) {
-      const int row = t - m;
       const int sc = ((P - m) % 3 + 3) % 3;       // slot of row t-m in level m-1's window
       const int su = ((P - m - 1) % 3 + 3) % 3;   // row t-m-1
       const int sd = ((P - m + 1) % 3 + 3) % 3;   // row t-m+1
-      const float4* gr = S.geo + 2 * (row - S.gbase);
+      const float4* gr = gp - 2 * m;
       const float4 d2 = m == 1 ? S.d2m1 : S.Win[m - 2][sc];
-      const float4 gv = S.rg[(row & (DG - 1)) * LANES + lane];
+      const float4 gv = S.rg[((tg - m) & (DG - 1)) * LANES + lane];
       const float4 o = level_update(S.lv[m - 1], gr[0], gr[1], S.Win[m - 1][sc], S.Win[m - 1][su],
                                     S.Win[m - 1][sd], d2, gv);
       if (m < K) S.Win[m][sc] = o;
       else top = o;
     }
   }
+  constexpr bool vec = VEC;
   S.d2m1 = a_t;
   // leave the pipeline: level kk (and kk-1) at row t - kk (always < J1)
   const int orow = t - (FULL ? K : kk);
@@ -643,9 +647,8 @@ __device__ __forceinline__ void march_band(March& S, int tmin, int t_end, int kk
                                            const float* gC, const float* gG, int pitch, int np, int col,
                                            bool zero_m2, int J0, bool fin, float* oA, float* oC,
                                            float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
-  constexpr bool vec = VEC;
-  for (int r = tmin; r < tmin + fused::D - 1; ++r)  // D-1 rows of lookahead before the first step
-    march_issue(S, r, t_end, gA, gC, gG, pitch, np, col, vec, zero_m2, lane);
+    for (int r = tmin; r < tmin + fused::D - 1; ++r)  // D-1 rows of lookahead before the first step
+    march_issue<VEC>(S, r, t_end, gA, gC, gG, pitch, np, col, zero_m2, lane);
 #define SFT_MARCH(PH, TT)                                                                        \
   march_row<PH, FULL, VEC>(S, TT, kk, t_end, gA, gC, gG, pitch, np, col, zero_m2, J0, fin, oA, oC, \
                            Bs, lane_out, n_out, bad, lane)
