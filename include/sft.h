@@ -222,14 +222,17 @@ sft_status sft_reset_stats(sft_handle h);
 sft_status sft_set_profiling(sft_handle h, int32_t profile);
 
 /* use_graphs != 0 (default): sft_step replays one captured CUDA graph per
- * distinct step configuration; 0: plain launches. */
+ * distinct step configuration (captured on the configuration's second use;
+ * its first use launches directly); 0: plain launches. */
 sft_status sft_set_graphs(sft_handle h, int32_t use_graphs);
 
 /* RKL2 stages per kernel launch: 1 (one launch per stage) or 4 (temporal
- * blocking: four stages per pass through HBM, shared-memory tiles with a
- * four-point halo and full-ring cap blocks).  The fused path needs FP32 and
- * every grid with ntheta >= 20 and nphi >= 16; it is the default when
- * available.  Both paths evaluate the same per-point formulas. */
+ * blocking: four stages per pass through HBM; bands of rows marched by
+ * warps with a four-point halo, full-ring cap blocks).  The fused path
+ * needs FP32 and every grid with ntheta >= 20 and nphi >= 16; it is the
+ * default when available.  Both paths compute the same stages (the fused
+ * interior folds the stencil into per-row coefficients: another rounding
+ * order, agreement to FP32 rounding). */
 sft_status sft_set_fusion(sft_handle h, int32_t stages_per_pass);
 
 /* Current RKL2 stages per launch (1 or 4). */

@@ -7,7 +7,8 @@
 // memory and fed to the tensor cores with ldmatrix; batched (strides, a
 // zero stride shares an operand), transposes by layout flags, split-K for
 // the weight gradients (K = batch x tokens), and a split-BF16 mode (hi*hi +
-// hi*lo + lo*hi) for the fixed rotation layer that must stay ~FP32-accurate.
+// hi*lo + lo*hi) for products that must stay ~FP32-accurate.  The fixed
+// rotation layer is an FFT per map row (rot_fft_kernel), not a GEMM.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -27,7 +28,6 @@ namespace {
 
 constexpr int H = 256, W = 512, PATCH = 4, HT = H / PATCH, WT = W / PATCH, KE = 48;
 constexpr int NTOK = HT * WT;           // tokens per map
-constexpr int MR = W / 2 + 1;           // rotation modes
 constexpr float SCALE = 100.0f;         // map normalisation (G)
 constexpr double PI = 3.14159265358979323846;
 
@@ -265,20 +265,64 @@ __global__ void rot_angle_kernel(const float* __restrict__ p, int rows, double* 
   }
 }
 
-// Y = X * exp(-i k alpha_row) for the rotation layer; X, Y [rows][2*MR].
-__global__ void rot_phase_kernel(const float* __restrict__ X, const double* __restrict__ alpha, int rows,
-                                 float* __restrict__ Y) {
-  const long long n = (long long)rows * MR;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int row = (int)(e / MR), k = (int)(e % MR);
-    const double ang = k * alpha[row];
-    const double red = ang - (2.0 * PI) * rint(ang * (1.0 / (2.0 * PI)));  // in [-pi, pi]
-    float s, c;
-    sincosf((float)red, &s, &c);
-    const float re = X[(long long)row * 2 * MR + k], im = X[(long long)row * 2 * MR + MR + k];
-    Y[(long long)row * 2 * MR + k] = re * c + im * s;
-    Y[(long long)row * 2 * MR + MR + k] = im * c - re * s;
+// Layer R by FFT, one block of 256 threads per map row: the 512-point DFT of
+// the real row (radix-2 in shared memory: decimation in time from a
+// bit-reversed load), Y_k = X_k exp(-i k alpha_row) on modes 0..256, the
+// Hermitian extension Z_{512-k} = conj(Y_k) (the Nyquist mode keeps its real
+// part only, as the truncated synthesis G does), and the inverse transform
+// (decimation in frequency, conjugate twiddles) scaled by 1/512.  The same map
+// as r = phase(x F^T) G^T, in FP32 with O(log n) rounding.
+// tw[j] = exp(-2 pi i j / 512), j < 256.
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(256) rot_fft_kernel(const float* __restrict__ x, const double* __restrict__ alpha,
+                                                      const float2* __restrict__ tw, float* __restrict__ r) {
+  static_assert(W == 512, "rot_fft_kernel is written for 512-point rows");
+  __shared__ float2 s[W];
+  const int row = blockIdx.x, t = threadIdx.x;
+  const float* xr = x + (long long)row * W;
+  s[__brev(t) >> 23] = make_float2(xr[t], 0.f);
+  s[__brev(t + 256) >> 23] = make_float2(xr[t + 256], 0.f);
+  __syncthreads();
+  for (int half = 1; half < W; half <<= 1) {  // DIT stages
+    const int pos = t & (half - 1), i0 = ((t - pos) << 1) + pos, i1 = i0 + half;
+    const float2 u = s[i0], v = cmul(s[i1], tw[pos * (256 / half)]);
+    s[i0] = make_float2(u.x + v.x, u.y + v.y);
+    s[i1] = make_float2(u.x - v.x, u.y - v.y);
+    __syncthreads();
   }
+  // phase on k = t (and k = 256 by thread 0); Z_{512-k} = conj(Y_k) lands in
+  // slots 257..511, which no thread reads
+  const double a = alpha[row];
+  for (int k = t; k <= W / 2; k += 256) {
+    const double ang = k * a;
+    const double red = ang - (2.0 * PI) * rint(ang * (1.0 / (2.0 * PI)));  // in [-pi, pi]
+    float sn, cs;
+    sincosf((float)red, &sn, &cs);
+    const float2 X = s[k];
+    const float2 Y = make_float2(X.x * cs + X.y * sn, X.y * cs - X.x * sn);
+    if (k == W / 2) {
+      s[k] = make_float2(Y.x, 0.f);
+    } else {
+      s[k] = Y;
+      if (k > 0) s[W - k] = make_float2(Y.x, -Y.y);
+    }
+  }
+  __syncthreads();
+  for (int half = W / 2; half >= 1; half >>= 1) {  // DIF stages, conjugate twiddles
+    const int pos = t & (half - 1), i0 = ((t - pos) << 1) + pos, i1 = i0 + half;
+    const float2 u = s[i0], v = s[i1];
+    const float2 w = tw[pos * (256 / half)];
+    s[i0] = make_float2(u.x + v.x, u.y + v.y);
+    s[i1] = cmul(make_float2(u.x - v.x, u.y - v.y), make_float2(w.x, -w.y));
+    __syncthreads();
+  }
+  float* rr = r + (long long)row * W;
+  constexpr float inv = 1.0f / W;
+  rr[t] = s[__brev(t) >> 23].x * inv;
+  rr[t + 256] = s[__brev(t + 256) >> 23].x * inv;
 }
 
 // E[token][48]: 4x4 patches of x/s and r/s, normalised parameters, cos/sin of
@@ -560,9 +604,10 @@ struct sfs_net {
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
   int t = 0;
   // fixed matrices
-  float *Fr = nullptr, *Gr = nullptr, *Fm = nullptr, *Gm = nullptr, *ones = nullptr;
+  float *Fm = nullptr, *Gm = nullptr, *ones = nullptr;
+  float2* tw = nullptr;  // FFT twiddles exp(-2 pi i j / W), j < W/2
   // activations
-  float *R = nullptr, *Xs = nullptr, *Ys = nullptr, *E = nullptr, *D = nullptr, *XN = nullptr;
+  float *R = nullptr, *E = nullptr, *D = nullptr, *XN = nullptr;
   std::vector<float*> Hs, Hh, U, Z, A;
   float *Yh = nullptr;
   // gradients of activations
@@ -678,16 +723,12 @@ struct Rng {
 sft_status forward(sfs_handle h, const float* x, const float* p, int nb) {
   const int C = h->C, M = h->M;
   const long long ntok = (long long)nb * NTOK;
-  // rotation layer: X = x F_r^T, phase, r = Y G_r^T  (split BF16, ~FP32 accuracy)
-  sft_status st = gemm(h, nb * H, 2 * MR, W, x, W, 0, 0, h->Fr, W, 0, 1, h->Xs, 2 * MR, 0, 1.f, 0.f, nullptr, 1, true);
-  if (st != SFT_OK) return st;
+  // rotation layer r = phase(x F^T) G^T, by FFT per map row (FP32)
   rot_angle_kernel<<<grid_for((long long)nb * H), 256, 0, h->stream>>>(p, nb * H, h->alpha);
-  rot_phase_kernel<<<grid_for((long long)nb * H * MR), 256, 0, h->stream>>>(h->Xs, h->alpha, nb * H, h->Ys);
-  st = gemm(h, nb * H, W, 2 * MR, h->Ys, 2 * MR, 0, 0, h->Gr, 2 * MR, 0, 1, h->R, W, 0, 1.f, 0.f, nullptr, 1, true);
-  if (st != SFT_OK) return st;
+  rot_fft_kernel<<<nb * H, 256, 0, h->stream>>>(x, h->alpha, h->tw, h->R);
   embed_kernel<<<grid_for(ntok), 256, 0, h->stream>>>(x, h->R, p, nb, h->E);
   h->kernels += 3;
-  st = gemm(h, (int)ntok, C, KE, h->E, KE, 0, 0, h->P + h->oWe, C, 0, 0, h->Hs[0], C, 0, 1.f, 0.f, h->P + h->obe, 1);
+  sft_status st = gemm(h, (int)ntok, C, KE, h->E, KE, 0, 0, h->P + h->oWe, C, 0, 0, h->Hs[0], C, 0, 1.f, 0.f, h->P + h->obe, 1);
   if (st != SFT_OK) return st;
   for (int l = 0; l < h->L; ++l) {
     float* hcur = h->Hs[l];
@@ -873,12 +914,14 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
   // fixed matrices
   {
     std::vector<float> F, G;
-    dft_host(W, MR, F, G);
-    CR(dalloc(h, &h->Fr, (long long)F.size()));
-    CR(dalloc(h, &h->Gr, (long long)G.size()));
-    if (cudaMemcpy(h->Fr, F.data(), F.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(h->Gr, G.data(), G.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-      return bail(fail("dft upload failed"));
+    std::vector<float2> tw(W / 2);
+    for (int j = 0; j < W / 2; ++j) {
+      const double a = -2.0 * PI * j / W;
+      tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    CR(dalloc(h, &h->tw, (long long)tw.size()));
+    if (cudaMemcpy(h->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail("twiddle upload failed"));
     dft_host(WT, M, F, G);
     CR(dalloc(h, &h->Fm, (long long)F.size()));
     CR(dalloc(h, &h->Gm, (long long)G.size()));
@@ -891,8 +934,6 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
   fill_kernel<<<grid_for(ntok), 256, 0, h->stream>>>(h->ones, ntok, 1.f);
   CR(dalloc(h, &h->R, nb * H * W));
   CR(dalloc(h, &h->XN, nb * H * W));
-  CR(dalloc(h, &h->Xs, nb * H * 2 * MR));
-  CR(dalloc(h, &h->Ys, nb * H * 2 * MR));
   CR(dalloc(h, &h->E, ntok * KE));
   CR(dalloc(h, &h->D, ntok * 16));
   h->Hs.assign(L + 1, nullptr);

@@ -82,6 +82,7 @@ struct Config {
   void* d_coef = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t last_use = 0;
+  int uses = 0;  // steps run with this configuration (graphs are captured from the second)
   double cells_adv = 0, cell_stages_diff = 0, cell_updates = 0, diff_words = 0;
   int64_t launches = 0;
   int realization_steps = 0;
@@ -637,8 +638,12 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     if (st != SFT_OK) return st;
   }
   c->last_use = ++h->use_counter;
+  c->uses += 1;
   const bool ev = h->profiling;
-  if (h->use_graphs) {
+  // A configuration used once (a shortened last step, a one-off member
+  // subset) launches eagerly; capture and instantiation pay off from its
+  // second use on.
+  if (h->use_graphs && c->uses >= 2) {
     if (!c->exec) {
       cudaGraph_t g = nullptr;
       SFT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
