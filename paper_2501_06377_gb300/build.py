@@ -1,6 +1,6 @@
 """Build libsft.so in-tree with nvcc for sm_103a (GB300).
 
-The two translation units compile in parallel; the library is rebuilt only
+The translation units compile in parallel; the library is rebuilt only
 when a source, the header or the flags change (a stamp file records their
 hash).
 """
@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsft.so")
-SOURCES = ["sft_api.cu", "sft_kernels.cu", "sft_noalloc.cu", "sfs.cu"]
+SOURCES = ["sft_api.cu", "sft_kernels.cu", "sft_noalloc.cu", "sfs.cu", "sfs_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -32,7 +32,8 @@ def _nvcc() -> str:
 def _stamp() -> str:
     h = hashlib.sha256()
     h.update(" ".join(FLAGS).encode())
-    for name in sorted(os.listdir(CSRC)) + ["../../include/sft.h"]:
+    headers = ["../../include/" + f for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h")]
+    for name in sorted(os.listdir(CSRC)) + headers:
         p = os.path.normpath(os.path.join(CSRC, name))
         if os.path.isfile(p):
             h.update(name.encode())

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "sfs.h"
+#include "sfs_fused.cuh"
 
 namespace sft {
 void set_global_error(const std::string& msg);
@@ -624,6 +625,13 @@ struct sfs_net {
   int64_t gemms = 0, kernels = 0;
   double flops = 0.0;
   std::vector<void*> allocs;
+  // fused inference forward (C = 64, M = 48, L <= 4): BF16 weight image,
+  // rebuilt when the parameters change (pver counts the changes)
+  bool fused = false;
+  unsigned char* img = nullptr;
+  long long pver = 0, img_pver = -1;
+  int n_sm = 0;
+  sfs_fused::ParamOffsets po{};
 };
 
 namespace {
@@ -762,6 +770,30 @@ sft_status forward(sfs_handle h, const float* x, const float* p, int nb) {
   flux_kernel<<<dim3(64, nb), 256, 0, h->stream>>>(h->XN, h->area, h->msum);
   center_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
   h->kernels += 3;
+  SFS_CUDA(cudaGetLastError());
+  return SFT_OK;
+}
+
+// Inference forward of the fused kernel (sfs_fused.cu): rotation by FFT,
+// then one persistent kernel for embedding, blocks and decoder, then the
+// flux-free centring.
+sft_status forward_fused(sfs_handle h, const float* x, const float* p, int nb) {
+  rot_angle_kernel<<<grid_for((long long)nb * H), 256, 0, h->stream>>>(p, nb * H, h->alpha);
+  rot_fft_kernel<<<nb * H, 256, 0, h->stream>>>(x, h->alpha, h->tw, h->R);
+  h->kernels += 2;
+  if (h->img_pver != h->pver) {
+    SFS_CUDA(sfs_fused::build_image(h->P, h->po, h->L, h->Fm, h->Gm, h->img, h->stream));
+    h->img_pver = h->pver;
+    h->kernels += 1;
+  }
+  SFS_CUDA(sfs_fused::forward(h->img, h->L, h->P, h->po, x, h->R, p, nb, h->XN, h->n_sm, h->stream));
+  h->kernels += 1;
+  h->flops += 2.0 * nb * NTOK *
+              ((double)KE * h->C + h->L * (2.0 * 2 * h->M * h->C + 2.0 * 2 * h->C * h->C) + 16.0 * h->C);
+  SFS_CUDA(cudaMemsetAsync(h->msum, 0, 2 * nb * sizeof(double), h->stream));
+  flux_kernel<<<dim3(64, nb), 256, 0, h->stream>>>(h->XN, h->area, h->msum);
+  center_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
+  h->kernels += 2;
   SFS_CUDA(cudaGetLastError());
   return SFT_OK;
 }
@@ -974,6 +1006,26 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
   }
   if (cudaMallocHost(&h->hsums, 2 * nb * sizeof(double)) != cudaSuccess) return bail(fail("pinned alloc failed"));
   if (cudaMallocHost(&h->hlsum, 3 * nb * sizeof(double)) != cudaSuccess) return bail(fail("pinned alloc failed"));
+  h->fused = C == sfs_fused::kChannels && M == sfs_fused::kModes && L <= sfs_fused::kMaxBlocks;
+  if (h->fused) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return bail(fail("device query failed"));
+    if (sfs_fused::prepare(L) != cudaSuccess) return bail(fail("fused forward: shared-memory limit not granted"));
+    CR(dalloc(h, &h->img, (long long)sfs_fused::image_bytes(L)));
+    h->po.We = h->oWe;
+    h->po.be = h->obe;
+    h->po.Wd = h->oWd;
+    h->po.bd = h->obd;
+    for (int l = 0; l < L; ++l) {
+      h->po.w[l] = h->ow[l];
+      h->po.W1[l] = h->oW1[l];
+      h->po.b1[l] = h->ob1[l];
+      h->po.W2[l] = h->oW2[l];
+      h->po.b2[l] = h->ob2[l];
+    }
+  }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(fail("create sync failed"));
 #undef CR
   *out = h;
@@ -1000,6 +1052,7 @@ sft_status sfs_set_params(sfs_handle h, const float* host_params) {
   SFS_CUDA(cudaMemsetAsync(h->Vo, 0, h->np * sizeof(float), h->stream));
   SFS_CUDA(cudaStreamSynchronize(h->stream));
   h->t = 0;
+  h->pver += 1;
   return SFT_OK;
 }
 
@@ -1014,7 +1067,7 @@ sft_status sfs_forward(sfs_handle h, const float* x, const float* p, int32_t n, 
   sft_status st = check_batch(h, x, p, n);
   if (st != SFT_OK) return st;
   if (!y) return fail("NULL output", SFT_ERR_ARG);
-  st = forward(h, x, p, n);
+  st = h->fused ? forward_fused(h, x, p, n) : forward(h, x, p, n);
   if (st != SFT_OK) return st;
   SFS_CUDA(cudaMemcpyAsync(y, h->XN, (size_t)n * H * W * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
   return SFT_OK;
@@ -1050,6 +1103,7 @@ sft_status sfs_train_step(sfs_handle h, const float* x, const float* p, const fl
   adamw_kernel<<<grid_for(h->np), 256, 0, h->stream>>>(h->P, h->G, h->Mo, h->Vo, h->np, (float)lr, (float)wd, bc1,
                                                        bc2);
   h->kernels += 1;
+  h->pver += 1;
   SFS_CUDA(cudaGetLastError());
   if (loss) {
     SFS_CUDA(cudaMemcpyAsync(h->hlsum, h->lsum, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

@@ -125,3 +125,55 @@ def test_training_reduces_loss(torch_mod):
     for _ in range(40):
         last = net.train_step(xc, pc, yc, lr=2e-3, want_loss=True)
     assert last < 0.5 * first, (first, last)
+
+
+PROD = dict(channels=64, modes=48, blocks=4)   # the configuration of the fused inference kernel
+
+
+def test_fused_forward_matches_reference(torch_mod):
+    """sfs_forward of the production configuration runs the fused persistent
+    kernel (weights resident in shared memory): same bar as the unfused path."""
+    from paper_2501_06377_gb300.surrogate import Surrogate, flat_from_reference
+    P = S.init_params(C=PROD["channels"], M=PROD["modes"], L=PROD["blocks"], seed=4)
+    P["Wd"] *= 50.0
+    net = Surrogate(max_batch=4, **PROD)
+    net.set_params(flat_from_reference(P, PROD["blocks"]))
+    x, p, _ = _inputs(3, seed=5)
+    out = torch_mod.empty((3, S.H, S.W), device="cuda")
+    c0 = net.counters()
+    net.forward(_cuda(torch_mod, x), _cuda(torch_mod, p), out)
+    c1 = net.counters()
+    # the fused path: no GEMM launch, a handful of kernels (rotation, image,
+    # network, centring) instead of the unfused path's dozens
+    assert c1["gemm_launches"] == c0["gemm_launches"]
+    assert c1["kernel_launches"] - c0["kernel_launches"] <= 7
+    xr = x.astype(np.float32).astype(np.float64)
+    pr = p.astype(np.float32).astype(np.float64)
+    ref = S.forward(P, xr, pr, L=PROD["blocks"], M=PROD["modes"])
+    r = S.rotate(xr, S.rotation_angles(pr))
+    got = out.cpu().numpy()
+    corr_err = np.linalg.norm((got - r) - (ref - r)) / np.linalg.norm(ref - r)
+    assert corr_err <= 1e-2, corr_err
+    # flux-free correction: the output keeps each map's total flux
+    A = S.cell_areas()[None, :, None]
+    drift = np.abs((A * (got - xr)).sum(axis=(1, 2))) / (A * np.abs(xr)).sum(axis=(1, 2))
+    assert drift.max() <= 1e-6, drift
+
+
+def test_fused_forward_follows_training_updates(torch_mod):
+    """After AdamW steps the fused kernel's weight image is rebuilt: the loss of
+    its output equals the loss the (unfused) training forward reports."""
+    from paper_2501_06377_gb300.surrogate import Surrogate
+    net = Surrogate(max_batch=4, seed=3, **PROD)
+    x, p, y = _inputs(4, seed=7)
+    xc, pc, yc = _cuda(torch_mod, x), _cuda(torch_mod, p), _cuda(torch_mod, y)
+    out = torch_mod.empty_like(xc)
+    net.forward(xc, pc, out)
+    for _ in range(3):
+        net.train_step(xc, pc, yc, 1e-3)
+    net.forward(xc, pc, out)
+    o = out.cpu().numpy().astype(np.float64)
+    yy = y.astype(np.float32).astype(np.float64)
+    loss_fused = float(np.mean(((o - yy) ** 2).sum(axis=(1, 2)) / (yy ** 2).sum(axis=(1, 2))))
+    loss_train, _ = net.loss_grad(xc, pc, yc)
+    assert loss_fused == pytest.approx(loss_train, rel=2e-3), (loss_fused, loss_train)
