@@ -30,6 +30,7 @@ namespace {
 constexpr int H = 256, W = 512, PATCH = 4, HT = H / PATCH, WT = W / PATCH, KE = 48;
 constexpr int NTOK = HT * WT;           // tokens per map
 constexpr float SCALE = 100.0f;         // map normalisation (G)
+constexpr int kRedBlocks = 64;          // blocks per map of the per-map reductions
 constexpr double PI = 3.14159265358979323846;
 
 // ---------------------------------------------------------------------------
@@ -461,7 +462,7 @@ __global__ void center_kernel(float* __restrict__ xn, const float* __restrict__ 
   }
 }
 
-// Per map m: out[3m] += sum (x - y)^2, out[3m+1] += sum y^2, out[3m+2] += sum (x - y).
+// Per map m, block partials of sum (x - y)^2, sum y^2, sum (x - y) (three per block).
 __global__ void loss_sums_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                  double* __restrict__ out) {
   __shared__ double s0[256], s1[256], s2[256];
@@ -487,16 +488,17 @@ __global__ void loss_sums_kernel(const float* __restrict__ x, const float* __res
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    atomicAdd(&out[3 * m], s0[0]);
-    atomicAdd(&out[3 * m + 1], s1[0]);
-    atomicAdd(&out[3 * m + 2], s2[0]);
+  if (threadIdx.x == 0) {  // this block's partials; fold_map_sums adds them in a fixed order
+    double* q = out + ((long long)m * gridDim.x + blockIdx.x) * 3;
+    q[0] = s0[0];
+    q[1] = s1[0];
+    q[2] = s2[0];
   }
 }
 
 __global__ void sumsq_kernel(const float* __restrict__ a, const float* __restrict__ b, int nb,
                              double* __restrict__ out) {
-  // out[2*m] += sum (a-b)^2, out[2*m+1] += sum b^2 for map m (b may be null: then a^2 only)
+  // block partials of sum (a-b)^2 and sum b^2 for map m (b may be null: then a^2 only)
   __shared__ double s0[256], s1[256];
   const int m = blockIdx.y;
   double x0 = 0.0, x1 = 0.0;
@@ -518,8 +520,9 @@ __global__ void sumsq_kernel(const float* __restrict__ a, const float* __restric
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&out[2 * m], s0[0]);
-    atomicAdd(&out[2 * m + 1], s1[0]);
+    double* q = out + ((long long)m * gridDim.x + blockIdx.x) * 2;
+    q[0] = s0[0];
+    q[1] = s1[0];
   }
   (void)nb;
 }
@@ -541,7 +544,7 @@ __global__ void loss_grad_kernel(const float* __restrict__ xn, const float* __re
   }
 }
 
-// Per map m: out[2m] += sum A B, out[2m+1] += sum A |B| (FP64) with the
+// Per map m: block partials of sum A B and sum A |B| (FP64) with the
 // 256 x 512 grid's area weights (sin th_j dth dph; the pole rows share the
 // cap area 2 pi (1 - cos(dth/2)) over their nphi entries).
 __global__ void flux_kernel(const float* __restrict__ a, const double* __restrict__ area,
@@ -567,9 +570,20 @@ __global__ void flux_kernel(const float* __restrict__ a, const double* __restric
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&out[2 * m], s0[0]);
-    atomicAdd(&out[2 * m + 1], s1[0]);
+    double* q = out + ((long long)m * gridDim.x + blockIdx.x) * 2;
+    q[0] = s0[0];
+    q[1] = s1[0];
   }
+}
+
+// out[m][f] = sum over the nblk block partials of map m, in block order
+// (deterministic, unlike atomics).
+__global__ void fold_map_sums(const double* __restrict__ part, int nblk, int k, double* __restrict__ out) {
+  const int m = blockIdx.x, f = threadIdx.x;
+  if (f >= k) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += part[((long long)m * nblk + b) * k + f];
+  out[(long long)m * k + f] = acc;
 }
 
 __global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -620,6 +634,7 @@ struct sfs_net {
   double* alpha = nullptr;  // per (map, row) rotation angle
   double area_total = 0.0;  // sum of the weights over the whole map
   double* msum = nullptr;   // per map: sum A delta (output centring)
+  double* mpart = nullptr;  // per map and reduction block: partial sums (kRedBlocks x 3)
   double* lsum = nullptr;   // per map: loss sums
   double* hlsum = nullptr;
   int64_t gemms = 0, kernels = 0;
@@ -766,10 +781,10 @@ sft_status forward(sfs_handle h, const float* x, const float* p, int nb) {
   if (st != SFT_OK) return st;
   // x_next = r + s (delta - <delta>_A): the correction carries no net flux
   unpatch_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->D, nb, h->XN);
-  SFS_CUDA(cudaMemsetAsync(h->msum, 0, 2 * nb * sizeof(double), h->stream));
-  flux_kernel<<<dim3(64, nb), 256, 0, h->stream>>>(h->XN, h->area, h->msum);
+  flux_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, h->area, h->mpart);
+  fold_map_sums<<<nb, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->msum);
   center_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
-  h->kernels += 3;
+  h->kernels += 4;
   SFS_CUDA(cudaGetLastError());
   return SFT_OK;
 }
@@ -790,10 +805,10 @@ sft_status forward_fused(sfs_handle h, const float* x, const float* p, int nb) {
   h->kernels += 1;
   h->flops += 2.0 * nb * NTOK *
               ((double)KE * h->C + h->L * (2.0 * 2 * h->M * h->C + 2.0 * 2 * h->C * h->C) + 16.0 * h->C);
-  SFS_CUDA(cudaMemsetAsync(h->msum, 0, 2 * nb * sizeof(double), h->stream));
-  flux_kernel<<<dim3(64, nb), 256, 0, h->stream>>>(h->XN, h->area, h->msum);
+  flux_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, h->area, h->mpart);
+  fold_map_sums<<<nb, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->msum);
   center_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
-  h->kernels += 2;
+  h->kernels += 3;
   SFS_CUDA(cudaGetLastError());
   return SFT_OK;
 }
@@ -802,11 +817,11 @@ sft_status forward_fused(sfs_handle h, const float* x, const float* p, int nb) {
 sft_status backward(sfs_handle h, const float* y, int nb) {
   const int C = h->C, M = h->M;
   const long long ntok = (long long)nb * NTOK;
-  SFS_CUDA(cudaMemsetAsync(h->lsum, 0, 3 * nb * sizeof(double), h->stream));
-  loss_sums_kernel<<<dim3(64, nb), 256, 0, h->stream>>>(h->XN, y, h->lsum);
+  loss_sums_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, y, h->mpart);
+  fold_map_sums<<<nb, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 3, h->lsum);
   loss_grad_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, y, h->lsum, h->area,
                                                                           h->area_total, nb, h->dD);
-  h->kernels += 2;
+  h->kernels += 3;
   SFS_CUDA(cudaGetLastError());
   // decoder
   sft_status st = gemm_wgrad(h, C, 16, (int)ntok, h->Hs[h->L], C, 1, h->dD, 16, 0, h->G + h->oWd);
@@ -993,6 +1008,7 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
   CR(dalloc(h, &h->sums, 2 * nb));
   CR(dalloc(h, &h->alpha, nb * H));
   CR(dalloc(h, &h->msum, 2 * nb));
+  CR(dalloc(h, &h->mpart, nb * kRedBlocks * 3));
   CR(dalloc(h, &h->lsum, 3 * nb));
   {
     std::vector<double> ar(H);
@@ -1117,9 +1133,9 @@ sft_status sfs_rel_l2(sfs_handle h, const float* a, const float* b, int32_t n, d
   sft_status st = check_batch(h, a, b, n);
   if (st != SFT_OK) return st;
   if (!out) return fail("NULL output", SFT_ERR_ARG);
-  SFS_CUDA(cudaMemsetAsync(h->sums, 0, 2 * n * sizeof(double), h->stream));
-  sumsq_kernel<<<dim3(64, n), 256, 0, h->stream>>>(a, b, n, h->sums);
-  h->kernels += 1;
+  sumsq_kernel<<<dim3(kRedBlocks, n), 256, 0, h->stream>>>(a, b, n, h->mpart);
+  fold_map_sums<<<n, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->sums);
+  h->kernels += 2;
   SFS_CUDA(cudaGetLastError());
   SFS_CUDA(cudaMemcpyAsync(h->hsums, h->sums, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   SFS_CUDA(cudaStreamSynchronize(h->stream));
@@ -1131,9 +1147,9 @@ sft_status sfs_flux(sfs_handle h, const float* maps, int32_t n, double* out) {
   sft_status st = check_batch(h, maps, maps, n);
   if (st != SFT_OK) return st;
   if (!out) return fail("NULL output", SFT_ERR_ARG);
-  SFS_CUDA(cudaMemsetAsync(h->sums, 0, 2 * n * sizeof(double), h->stream));
-  flux_kernel<<<dim3(64, n), 256, 0, h->stream>>>(maps, h->area, h->sums);
-  h->kernels += 1;
+  flux_kernel<<<dim3(kRedBlocks, n), 256, 0, h->stream>>>(maps, h->area, h->mpart);
+  fold_map_sums<<<n, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->sums);
+  h->kernels += 2;
   SFS_CUDA(cudaGetLastError());
   SFS_CUDA(cudaMemcpyAsync(out, h->sums, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   SFS_CUDA(cudaStreamSynchronize(h->stream));

@@ -60,7 +60,8 @@ struct RealInfo {
   double dt_euler = 0.0;  // hours (inf when nu == 0)
 };
 
-constexpr int kMaxChains = 2;  // concurrent launch chains of the fused RKL2 passes
+constexpr int kMaxChains = 2;   // concurrent launch chains of the fused RKL2 passes
+constexpr int kMaxConfigs = 24; // cached step configurations (tile tables, graphs) per wave
 
 struct Config {
   bool fused = false;            // built for the fused RKL2 path
@@ -298,13 +299,16 @@ void rkl2_coefs(int s, std::vector<Coef<T>>& out) {
 
 template <typename T> T* ptr(void* p) { return static_cast<T*>(p); }
 
-void free_config(Config& c) {
+// Configuration buffers are stream-ordered allocations of the handle's
+// stream: freeing an evicted configuration waits for no other work (a graph
+// still in flight is released by the runtime when it completes).
+void free_config(Config& c, cudaStream_t st) {
   if (c.exec) cudaGraphExecDestroy(c.exec);
-  cudaFree(c.d_ftiles);
+  if (c.d_ftiles) cudaFreeAsync(c.d_ftiles, st);
   c.d_ftiles = nullptr;
-  cudaFree(c.d_tiles);
-  cudaFree(c.d_sp);
-  cudaFree(c.d_coef);
+  if (c.d_tiles) cudaFreeAsync(c.d_tiles, st);
+  if (c.d_sp) cudaFreeAsync(c.d_sp, st);
+  if (c.d_coef) cudaFreeAsync(c.d_coef, st);
   c.exec = nullptr;
   c.d_tiles = nullptr;
   c.d_sp = nullptr;
@@ -315,7 +319,8 @@ void free_handle(sft_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& w : h->waves)
-    for (auto& c : w.configs) free_config(*c);
+    for (auto& c : w.configs) free_config(*c, h->stream);
+  if (h->stream) cudaStreamSynchronize(h->stream);
   cudaFree(h->state);
   for (auto& w : h->work) cudaFree(w);
   cudaFree(h->polar);
@@ -461,7 +466,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
       if (s[i] > 0) c->diff_words += (double)sh.nt * sh.np * (3.0 + 5.0 * ((s[i] - 1 + fused::K - 1) / fused::K));
     }
     if (!ft.empty()) {
-      SFT_CUDA(h, cudaMalloc(&c->d_ftiles, ft.size() * sizeof(Tile)));
+      SFT_CUDA(h, cudaMallocAsync(reinterpret_cast<void**>(&c->d_ftiles), ft.size() * sizeof(Tile), h->stream));
       SFT_CUDA(h, cudaMemcpyAsync(c->d_ftiles, ft.data(), ft.size() * sizeof(Tile),
                                   cudaMemcpyHostToDevice, h->stream));
     }
@@ -474,25 +479,26 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     c->stage_tiles[j] = n == 0 ? 0 : tile_end[n - 1];
   }
   if (!tiles.empty()) {
-    SFT_CUDA(h, cudaMalloc(&c->d_tiles, tiles.size() * sizeof(Tile)));
+    SFT_CUDA(h, cudaMallocAsync(reinterpret_cast<void**>(&c->d_tiles), tiles.size() * sizeof(Tile), h->stream));
     SFT_CUDA(h, cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(Tile),
                                 cudaMemcpyHostToDevice, h->stream));
   }
-  SFT_CUDA(h, cudaMalloc(&c->d_sp, sp.size() * sizeof(StepParam)));
+  SFT_CUDA(h, cudaMallocAsync(reinterpret_cast<void**>(&c->d_sp), sp.size() * sizeof(StepParam), h->stream));
   SFT_CUDA(h, cudaMemcpyAsync(c->d_sp, sp.data(), sp.size() * sizeof(StepParam),
                               cudaMemcpyHostToDevice, h->stream));
   if (coefs.empty()) coefs.push_back(Coef<T>{});
-  SFT_CUDA(h, cudaMalloc(&c->d_coef, coefs.size() * sizeof(Coef<T>)));
+  SFT_CUDA(h, cudaMallocAsync(&c->d_coef, coefs.size() * sizeof(Coef<T>), h->stream));
   SFT_CUDA(h, cudaMemcpyAsync(c->d_coef, coefs.data(), coefs.size() * sizeof(Coef<T>),
                               cudaMemcpyHostToDevice, h->stream));
-  SFT_CUDA(h, cudaStreamSynchronize(h->stream));  // host vectors die at return
-  // keep at most 8 configurations per wave
-  if (w.configs.size() >= 8) {
+  // (pageable-source async copies are staged before they return: the host
+  // vectors may die at return without a synchronisation)
+  // keep at most kMaxConfigs configurations per wave
+  if ((int)w.configs.size() >= kMaxConfigs) {
     auto it = std::min_element(w.configs.begin(), w.configs.end(),
                                [](const std::unique_ptr<Config>& a, const std::unique_ptr<Config>& b) {
                                  return a->last_use < b->last_use;
                                });
-    free_config(**it);
+    free_config(**it, h->stream);
     w.configs.erase(it);
   }
   *out = c.get();
@@ -1120,7 +1126,7 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
   // stale configurations refer to the old parameters
   SFT_CUDA(h, cudaStreamSynchronize(h->stream));
   for (auto& w : h->waves) {
-    for (auto& c : w.configs) free_config(*c);
+    for (auto& c : w.configs) free_config(*c, h->stream);
     w.configs.clear();
   }
   sft_status st = h->prec == SFT_FP32 ? set_flows_t<float>(h, params) : set_flows_t<double>(h, params);

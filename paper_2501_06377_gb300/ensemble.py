@@ -10,7 +10,8 @@ which member takes which path:
   of them (sfs_forward); a proposal is rejected when its FP64 total-flux
   drift |sum A (B_new - B_old)| / sum A |B_old| exceeds ``drift_tol``
   (sfs_flux), and for a seeded spot-check subset the plain
-  solver's own day is computed and the proposal rejected when their
+  solver's own day is computed (queued on the grid's stream before the
+  proposals, so the two run at once) and the proposal rejected when their
   relative L2 difference exceeds ``l2_tol`` (sfs_rel_l2).  Rejected members
   advance with the plain solver (the spot-checked ones take the solver's
   result they already have).
@@ -140,21 +141,30 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
     t0 = time.perf_counter()
     phi_old, abs_old = _fluxes(net, S)
     for day in range(days):
-        propose(net, S, P, prop)
-        phi_new, abs_new = _fluxes(net, prop)
-        drift = np.abs(phi_new - phi_old) / np.maximum(abs_old, 1e-300)
-        bad = drift > drift_tol
+        t_day0, t_day1 = day * DAY, (day + 1) * DAY
         chk = rng.choice(n, size=min(spot, n), replace=False)
-        # plain solver for the spot-checked and drift-rejected members only
         run = np.zeros(n, dtype=bool)
         run[chk] = True
-        run |= bad
-        t_day0, t_day1 = day * DAY, (day + 1) * DAY
+        # the plain solver's day for the spot-checked members is queued first
+        # (sft_step returns without waiting) so that it runs on the grid's
+        # stream while the surrogate proposes on its own
         for i in range(n):
             if run[i]:
                 g.set_state(i, S[i])
             g.set_time(t_day0 if run[i] else t_day1, i)
         g.step(t_day1)
+        propose(net, S, P, prop)
+        phi_new, abs_new = _fluxes(net, prop)
+        drift = np.abs(phi_new - phi_old) / np.maximum(abs_old, 1e-300)
+        bad = drift > drift_tol
+        extra = bad & ~run
+        if extra.any():  # drift-rejected members outside the spot check: their own plain day
+            for i in range(n):
+                if extra[i]:
+                    g.set_state(i, S[i])
+                g.set_time(t_day0 if extra[i] else t_day1, i)
+            g.step(t_day1)
+            run |= extra
         plain = torch.empty((int(run.sum()), H, W), device="cuda")
         idx = np.flatnonzero(run)
         for q, i in enumerate(idx):

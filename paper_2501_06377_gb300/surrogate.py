@@ -120,8 +120,15 @@ class Surrogate:
         return float(loss.value) if want_loss else None
 
     def rel_l2(self, a, b):
-        out = np.empty(a.shape[0], dtype=np.float64)
-        self._check(self.lib.sfs_rel_l2(self.h, _dev(a), _dev(b), a.shape[0], C.c_void_p(out.ctypes.data)))
+        """||a - b|| / ||b|| per map, in chunks of max_batch."""
+        n = a.shape[0]
+        out = np.empty(n, dtype=np.float64)
+        for c0 in range(0, n, self.max_batch):
+            c1 = min(n, c0 + self.max_batch)
+            o = np.empty(c1 - c0, dtype=np.float64)
+            self._check(self.lib.sfs_rel_l2(self.h, _dev(a[c0:c1]), _dev(b[c0:c1]), c1 - c0,
+                                            C.c_void_p(o.ctypes.data)))
+            out[c0:c1] = o
         return out
 
     def flux(self, maps):
