@@ -15,6 +15,7 @@
 //            and imaginary rows of its modes)
 //   G3  u  = h + Gm Yh                     warp w: tokens 16w..
 //   G4  z  = u W1 + b1, a = gelu(z)        A operand from G3's registers
+//                                          (hardware tanh: see gelu2)
 //   G5  h  = u + a W2 + b2                 A operand from G4's registers
 //   G6  d  = h Wd + bd  -> unpatched delta rows
 // The accumulators of two adjacent 8-column tiles are exactly the A fragment
@@ -88,9 +89,23 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.b32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ float gelu(float z) {  // tanh form, as the unfused path
-  const float c = 0.7978845608028654f;
-  return 0.5f * z * (1.f + tanhf(c * (z + 0.044715f * z * z * z)));
+// tanh-form GELU of a pair, 0.5 z (1 + tanh(c z (1 + 0.044715 z^2))), with the
+// hardware tanh approximation (tanh.approx.f32, ~2^-11 relative: the result
+// is rounded to BF16, 2^-8, right after) and packed f32x2 arithmetic.  The
+// training path keeps the accurate tanhf.
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;\n" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  const float2 c = make_float2(0.7978845608028654f, 0.7978845608028654f);
+  const float2 k = make_float2(0.044715f, 0.044715f), one = make_float2(1.f, 1.f), half = make_float2(0.5f, 0.5f);
+  const float2 z2 = __fmul2_rn(z, z);
+  const float2 arg = __fmul2_rn(__fmul2_rn(c, z), __ffma2_rn(k, z2, one));
+  const float2 t = make_float2(tanh_hw(arg.x), tanh_hw(arg.y));
+  return __fmul2_rn(__fmul2_rn(half, z), __fadd2_rn(one, t));
 }
 
 // A fragments (k steps of 16) from accumulators over 2*KS tiles of 8 columns
@@ -267,11 +282,13 @@ fused_forward_kernel(const unsigned char* __restrict__ img, SpecPtrs ws, const f
         const float* b1 = bias + 80 + l * 2 * C;
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
-          const int c = 8 * n + 2 * t;
-          z[n][0] = gelu(z[n][0] + b1[c]);
-          z[n][1] = gelu(z[n][1] + b1[c + 1]);
-          z[n][2] = gelu(z[n][2] + b1[c]);
-          z[n][3] = gelu(z[n][3] + b1[c + 1]);
+          const float2 bb = *reinterpret_cast<const float2*>(b1 + 8 * n + 2 * t);
+          const float2 lo = gelu2(__fadd2_rn(make_float2(z[n][0], z[n][1]), bb));
+          const float2 hi = gelu2(__fadd2_rn(make_float2(z[n][2], z[n][3]), bb));
+          z[n][0] = lo.x;
+          z[n][1] = lo.y;
+          z[n][2] = hi.x;
+          z[n][3] = hi.y;
         }
         acc_to_a<8>(z, za);
       }
