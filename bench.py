@@ -474,7 +474,7 @@ def main():
     ap.add_argument("--pairs", type=int, default=20000)
     ap.add_argument("--members", type=int, default=512)
     ap.add_argument("--days", type=int, default=27)
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=16)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

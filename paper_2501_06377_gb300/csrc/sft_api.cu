@@ -150,6 +150,7 @@ struct sft_grid {
   uint64_t use_counter = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t side[kMaxChains] = {};           // chains 1.. of the fused RKL2 passes
+  int n_sm = 152;                               // streaming multiprocessors of the device
   cudaEvent_t fork = nullptr;                   // ordering events (no timing)
   cudaEvent_t join[kMaxChains] = {};
   sft_stats stats{};
@@ -442,7 +443,15 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
   if (c->fused) {
     // fused passes start at stages 2, 2+K, 2+2K, ...; stage 1 uses the
     // single-stage kernel (it forms G = dt L(Y_0)).
-    c->n_chains = std::max(1, std::min<int>(kMaxChains, (int)order.size()));
+    // a second chain pays off only when a pass fills the GPU several times
+    // over; small batches keep one chain (half the launches)
+    size_t pass_tiles = 0;
+    {
+      std::vector<Tile> tmp;
+      for (int i : order) append_fused_tiles(h, w.reals[i], tmp);
+      pass_tiles = tmp.size();
+    }
+    c->n_chains = pass_tiles >= (size_t)4 * h->n_sm ? std::min<int>(kMaxChains, (int)order.size()) : 1;
     std::vector<Tile> ft;
     for (int ch = 0; ch < c->n_chains; ++ch) {
       c->fbase[ch] = (int)ft.size();
@@ -1037,6 +1046,7 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   CREATE_CUDA(cudaMalloc(&h->d_wpar, (size_t)n_real * 4 * sizeof(double)));
   CREATE_CUDA(cudaMalloc(&h->d_obs_off, (size_t)n_real * sizeof(int64_t)));
   for (auto& e : h->ev) CREATE_CUDA(cudaEventCreate(&e));
+  CREATE_CUDA(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device));
   CREATE_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
   for (int ch = 1; ch < kMaxChains; ++ch) {
     CREATE_CUDA(cudaStreamCreateWithFlags(&h->side[ch], cudaStreamNonBlocking));
