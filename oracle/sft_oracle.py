@@ -143,12 +143,29 @@ def weno3_face_flux(LMm2, LMm1, LM0, LPm1, LP0, LPp1, eps_w):
     return up + um
 
 
-def llf_split(B, v_minus, v_plus, alpha):
+def llf_split(B, v_minus, v_plus, alpha, a=None):
     """Local Lax-Friedrichs splitting of App. B:
-    LP_i = B_i (v_{i+1/2} - alpha_i)/2, LM_i = B_i (v_{i-1/2} + alpha_i)/2."""
-    LP = 0.5 * B * (v_plus - alpha)
-    LM = 0.5 * B * (v_minus + alpha)
+    LP_i = B_i (v_{i+1/2} - alpha_i)/2, LM_i = B_i (v_{i-1/2} + alpha_i)/2.
+    With flow attenuation (Eq. flow_attenuation) the advective part carries
+    the cell's factor a_i: LP_i = (v_{i+1/2} a_i B_i - alpha_i B_i)/2,
+    LM_i = (v_{i-1/2} a_i B_i + alpha_i B_i)/2."""
+    if a is None:
+        LP = 0.5 * B * (v_plus - alpha)
+        LM = 0.5 * B * (v_minus + alpha)
+    else:
+        LP = 0.5 * (v_plus * a * B - alpha * B)
+        LM = 0.5 * (v_minus * a * B + alpha * B)
     return LP, LM
+
+
+def attenuation_factor(B, b0):
+    """Eq. (flow_attenuation): the flow is scaled by 1 - tanh(|B_r| / B_0).
+    Reading: the factor is taken where the flow meets the field, i.e. every
+    flux term v B_i of cell i becomes v a_i B_i (the flux function
+    f(B) = v (1 - tanh(|B|/B_0)) B); b0 = None or 0 switches it off."""
+    if not b0:
+        return None
+    return 1.0 - np.tanh(np.abs(B) / b0)
 
 
 def _theta_face_is_upwind(nt):
@@ -161,12 +178,14 @@ def _theta_face_is_upwind(nt):
     return up
 
 
-def theta_face_fluxes(g: Grid, B, vt, space="weno3", eps_w="h", alpha_uw=1.0):
-    """F_theta at every theta face f+1/2 (shape (nt-1, np))."""
+def theta_face_fluxes(g: Grid, B, vt, space="weno3", eps_w="h", alpha_uw=1.0, a=None):
+    """F_theta at every theta face f+1/2 (shape (nt-1, np)); a = the flow
+    attenuation factor per cell (None: off)."""
     nt = g.nt
     Ft = np.empty((nt - 1, g.np))
     f = np.arange(nt - 1)
-    uw_flux = upwind_face_flux(vt[:, None], B[:-1, :], B[1:, :], alpha_uw)
+    aB = B if a is None else a * B
+    uw_flux = upwind_face_flux(vt[:, None], aB[:-1, :], aB[1:, :], alpha_uw)
     if space == "upwind":
         return uw_flux
     eps = g.dth if eps_w == "h" else float(eps_w)
@@ -177,7 +196,8 @@ def theta_face_fluxes(g: Grid, B, vt, space="weno3", eps_w="h", alpha_uw=1.0):
     alpha = np.array([av[max(ii - 3, 0):min(ii + 2, nt - 2) + 1].max() for ii in i])
     LP = np.zeros_like(B)
     LM = np.zeros_like(B)
-    LP[i], LM[i] = llf_split(B[i], vt[i - 1][:, None], vt[i][:, None], alpha[:, None])
+    LP[i], LM[i] = llf_split(B[i], vt[i - 1][:, None], vt[i][:, None], alpha[:, None],
+                             None if a is None else a[i])
     Ft[:] = uw_flux
     fw = f[~_theta_face_is_upwind(nt)]
     iw = fw + 1   # face f is F_{i-1/2} with i = f + 1
@@ -186,16 +206,16 @@ def theta_face_fluxes(g: Grid, B, vt, space="weno3", eps_w="h", alpha_uw=1.0):
     return Ft
 
 
-def phi_face_fluxes(g: Grid, B, vp, space="weno3", eps_w="h", alpha_uw=1.0):
+def phi_face_fluxes(g: Grid, B, vp, space="weno3", eps_w="h", alpha_uw=1.0, a=None):
     """F_phi at faces k-1/2 of every row (shape (nt, np)); periodic in phi.
     v_phi is uniform along a row for the analytic flows, so alpha_i = |v|."""
     v = vp[:, None] * np.ones((1, g.np))
-    Bm1 = np.roll(B, 1, axis=1)
     if space == "upwind":
-        return upwind_face_flux(v, Bm1, B, alpha_uw)
+        aB = B if a is None else a * B
+        return upwind_face_flux(v, np.roll(aB, 1, axis=1), aB, alpha_uw)
     eps = g.dph if eps_w == "h" else float(eps_w)
     alpha = np.abs(v)
-    LP, LM = llf_split(B, v, v, alpha)
+    LP, LM = llf_split(B, v, v, alpha, a)
 
     def sh(a, s):   # a_{k+s}
         return np.roll(a, -s, axis=1)
@@ -204,11 +224,15 @@ def phi_face_fluxes(g: Grid, B, vp, space="weno3", eps_w="h", alpha_uw=1.0):
                            sh(LP, -1), LP, sh(LP, 1), eps)
 
 
-def advection_operator(g: Grid, B, vt, vp, space="weno3", eps_w="h", alpha_uw=1.0):
+def advection_operator(g: Grid, B, vt, vp, space="weno3", eps_w="h", alpha_uw=1.0, b0=None):
     """F_A(B) = div_s(B v) by the conservative finite difference of
-    Sec. 3.6.1 with the polar finite-volume caps of App. A."""
-    Ft = theta_face_fluxes(g, B, vt, space, eps_w, alpha_uw)
-    Fp = phi_face_fluxes(g, B, vp, space, eps_w, alpha_uw)
+    Sec. 3.6.1 with the polar finite-volume caps of App. A; b0 > 0 attenuates
+    the flow by Eq. (flow_attenuation) (the LLF bound alpha = max |v| and the
+    time-step limit keep the unattenuated flow: attenuation only slows it,
+    and |d f/d B| <= |v| for the attenuated flux)."""
+    a = attenuation_factor(B, b0)
+    Ft = theta_face_fluxes(g, B, vt, space, eps_w, alpha_uw, a)
+    Fp = phi_face_fluxes(g, B, vp, space, eps_w, alpha_uw, a)
     out = np.zeros_like(B)
     j = np.arange(1, g.nt - 1)
     st = g.sin_t[j][:, None]
@@ -548,6 +572,7 @@ class Params:
     alpha_uw: float = 1.0
     safety: float = 0.9
     eps_w: object = "h"
+    atten_b0: float = 0.0        # Eq. (flow_attenuation) saturation field (G); 0 = off
 
 
 @dataclass
@@ -574,7 +599,7 @@ class Realization:
 
     def FA(self, B):
         p = self.p
-        return advection_operator(self.g, B, self.vt, self.vp, p.adv_space, p.eps_w, p.alpha_uw)
+        return advection_operator(self.g, B, self.vt, self.vp, p.adv_space, p.eps_w, p.alpha_uw, p.atten_b0)
 
     def L(self, B):
         return diffusion_operator(self.g, B, self.nu_hh)

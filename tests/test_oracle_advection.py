@@ -195,3 +195,53 @@ def test_flow_profiles_closed_forms():
     np.testing.assert_allclose(vt, -15.0 * np.sin(2 * g.theta_h) * O.M_S_TO_RS_HR, rtol=1e-12, atol=1e-20)
     # poleward: negative (toward theta = 0) in the north, positive in the south
     assert vt[: (g.nt - 1) // 2].max() < 0 < vt[(g.nt - 1) // 2:].min()
+
+
+# --------------------------------------------------------------------------
+# Eq. (flow_attenuation): v -> v [1 - tanh(|B_r| / B_0)]
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("space", ["weno3", "upwind"])
+def test_attenuation_off_in_the_weak_field_limit(space):
+    """B_0 -> infinity: the factor is 1 and the operator is the plain one."""
+    g = O.Grid(33, 64)
+    B = I.initial_map(33, 64, seed=3)
+    vt, vp = O.flow_profiles(g, 46.0, -262.0, -379.0, 22.0, 11.0, -28.0)
+    plain = O.advection_operator(g, B, vt, vp, space)
+    att = O.advection_operator(g, B, vt, vp, space, b0=1e300)
+    assert np.abs(att - plain).max() <= 1e-14 * np.abs(plain).max()
+
+
+@pytest.mark.parametrize("space", ["weno3", "upwind"])
+def test_attenuated_operator_conserves_total_flux(space):
+    g = O.Grid(40, 96)
+    B = I.initial_map(40, 96, seed=7)
+    vt, vp = O.flow_profiles(g, 46.0, -262.0, -379.0, 22.0, 11.0, -28.0)
+    FA = O.advection_operator(g, B, vt, vp, space, b0=200.0)
+    assert abs((g.area * FA).sum()) <= 1e-14 * (g.area * np.abs(FA)).sum()
+    assert np.abs(FA - O.advection_operator(g, B, vt, vp, space)).max() > 1e-3 * np.abs(FA).max()
+
+
+def test_attenuation_of_a_uniform_magnitude_field_scales_the_flow():
+    """With |B| = c everywhere the factor is the constant 1 - tanh(c/B_0): the
+    upwind operator equals the plain one with the flow scaled by it."""
+    g = O.Grid(33, 64)
+    rng = np.random.default_rng(5)
+    B = np.where(rng.random((33, 64)) < 0.5, -1.0, 1.0) * 700.0
+    B[0, :] = 700.0
+    B[-1, :] = -700.0
+    vt, vp = O.flow_profiles(g, 46.0, -262.0, -379.0, 22.0, 11.0, -28.0)
+    a = 1.0 - math.tanh(700.0 / 500.0)
+    att = O.advection_operator(g, B, vt, vp, "upwind", b0=500.0)
+    scaled = O.advection_operator(g, B, a * vt, a * vp, "upwind")
+    assert np.abs(att - scaled).max() <= 1e-13 * np.abs(scaled).max()
+
+
+def test_saturated_field_is_frozen_under_upwind():
+    """|B| >= 20 B_0 gives tanh = 1 in FP64: the attenuated flow is zero and
+    the upwind flux vanishes identically (an active region that does not move)."""
+    g = O.Grid(33, 64)
+    B = 1e4 * (1.0 + I.initial_map(33, 64, seed=9) ** 2 / 1e6)
+    B[0, :] = B[0, 0]
+    B[-1, :] = B[-1, 0]
+    vt, vp = O.flow_profiles(g, 46.0, -262.0, -379.0, 22.0, 11.0, -28.0)
+    assert np.all(O.advection_operator(g, B, vt, vp, "upwind", b0=500.0) == 0.0)
