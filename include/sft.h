@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define SFT_ABI_VERSION 1
+#define SFT_ABI_VERSION 2
 
 typedef struct sft_grid* sft_handle;
 
@@ -93,6 +93,10 @@ typedef struct {
   int32_t adv_time;   /* SFT_TIME_* (must be the same for all realizations) */
   int32_t diffusion;  /* SFT_DIFF_* (must be the same for all realizations) */
   int32_t advection;  /* 1 = advection on, 0 = off (then dt is limited only by the target) */
+  double atten_b0;    /* Eq. (flow_attenuation): the flow is scaled by 1 - tanh(|B_r| / atten_b0)
+                         where it meets the field (each flux term v B_i becomes v a_i B_i; the
+                         LLF bound and the CFL limit keep the unattenuated flow), G; 0 = off,
+                         otherwise > 0 (the paper's default is 500 G) */
 } sft_flow_params;
 
 /* Assimilation weight and balance options (Sec. 2.3). */

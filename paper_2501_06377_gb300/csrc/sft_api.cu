@@ -428,6 +428,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     p.s = s[i];
     p.weno = ri.fp.adv_space == SFT_ADV_WENO3_CSH ? 1 : 0;
     p.adv = ri.fp.advection ? 1 : 0;
+    p.inv_b0 = ri.fp.atten_b0 > 0.0 ? 1.0 / ri.fp.atten_b0 : 0.0;
     p.coef = (int)coefs.size();
     if (s[i] > 0) rkl2_coefs<T>(s[i], coefs);
     else coefs.push_back(Coef<T>{});
@@ -1132,6 +1133,8 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
       return fail(h, SFT_ERR_ARG, "bad diffusion");
     if (!(p.nu >= 0.0) || !(p.cfl_safety > 0.0) || !std::isfinite(p.d0 + p.d2 + p.d4 + p.m1 + p.m3 + p.m5))
       return fail(h, SFT_ERR_ARG, "bad flow parameters (nu >= 0, cfl_safety > 0, finite)");
+    if (!(p.atten_b0 >= 0.0) || !std::isfinite(p.atten_b0))
+      return fail(h, SFT_ERR_ARG, "atten_b0 must be 0 (off) or a finite positive field");
   }
   // stale configurations refer to the old parameters
   SFT_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -77,6 +77,7 @@ struct StepParam {
   double eps_t;     // WENO eps in the theta sweep
   double eps_p;     // WENO eps in the phi sweep
   double alpha_uw;  // UW/CD factor
+  double inv_b0;    // 1 / B_0 of Eq. (flow_attenuation); 0 = no attenuation
   int32_t s;        // RKL2 stages (0 = no diffusion)
   int32_t coef;     // index of this realization's stage-0 coefficients
   int32_t weno;     // 1 = WENO3-CS(h), 0 = UW

@@ -283,6 +283,79 @@ rkl2_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   }
 }
 
+// The divergence part of one advection stage for a thread's N points of row
+// j: o = b R_j - c dt F_A.  ATT: Eq. (flow_attenuation) -- every flux term
+// v B_i carries the cell's factor a_i = 1 - tanh(|B_i| / B_0) (the upwind
+// flux and the advective part of the LLF split); the dissipative alpha B
+// term keeps the unattenuated bound.
+template <typename T, int N, bool ATT>
+__device__ __forceinline__ void adv_divergence(const StepParam& p, const RowGeo<T>& g, const RowFlow<T> (&fl)[5],
+                                               const T (&R)[5][N], const T (&e)[N + 4], int j, int nt, T sb,
+                                               T cdt, T auw, T (&o)[N]) {
+  const T ib0 = T(p.inv_b0);
+  auto att = [&](T x) -> T { return ATT ? T(1) - tanh(fabs(x) * ib0) : T(1); };
+  const bool weno = p.weno != 0;
+  // phi faces k-1/2, k = kc .. kc+N
+  T F[N + 1];
+  const T v = fl[2].vp;
+  if (weno) {
+    const T eps = T(p.eps_p);
+    const T av = fabs(v);
+    if (ATT) {
+      T lm[N + 4], lp[N + 4];
+#pragma unroll
+      for (int i = 0; i < N + 4; ++i) {
+        const T vab = v * att(e[i]) * e[i];
+        lm[i] = T(0.5) * (vab + av * e[i]);
+        lp[i] = T(0.5) * (vab - av * e[i]);
+      }
+#pragma unroll
+      for (int i = 0; i <= N; ++i) F[i] = weno_flux(lm[i], lm[i + 1], lm[i + 2], lp[i + 1], lp[i + 2], lp[i + 3], eps);
+    } else {
+      const T hp = T(0.5) * (v + av), hm = T(0.5) * (v - av);
+#pragma unroll
+      for (int i = 0; i <= N; ++i)
+        F[i] = weno_flux(hp * e[i], hp * e[i + 1], hp * e[i + 2], hm * e[i + 1], hm * e[i + 2], hm * e[i + 3], eps);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i <= N; ++i)
+      F[i] = ATT ? uw_flux(v, att(e[i + 1]) * e[i + 1], att(e[i + 2]) * e[i + 2], auw)
+                 : uw_flux(v, e[i + 1], e[i + 2], auw);
+  }
+  // theta faces j-1/2 (f = j-1) and j+1/2 (f = j)
+  const bool wdn = weno && (j - 1 >= 2) && (j - 1 <= nt - 4);
+  const bool wup = weno && (j >= 2) && (j <= nt - 4);
+  const T eps = T(p.eps_t);
+  // LLF parts of cell m of the five-row window: LM uses v at its lower face, LP at its upper
+  auto LM = [&](int m, T b) -> T {
+    return ATT ? T(0.5) * (fl[m].vdn * att(b) * b + fl[m].alpha * b) : T(0.5) * b * (fl[m].vdn + fl[m].alpha);
+  };
+  auto LP = [&](int m, T b) -> T {
+    return ATT ? T(0.5) * (fl[m].vup * att(b) * b - fl[m].alpha * b) : T(0.5) * b * (fl[m].vup - fl[m].alpha);
+  };
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T Fdn, Fup;
+    if (wdn) {
+      Fdn = weno_flux(LM(0, R[0][i]), LM(1, R[1][i]), LM(2, R[2][i]), LP(1, R[1][i]), LP(2, R[2][i]),
+                      LP(3, R[3][i]), eps);
+    } else {
+      Fdn = ATT ? uw_flux(fl[2].vdn, att(R[1][i]) * R[1][i], att(R[2][i]) * R[2][i], auw)
+                : uw_flux(fl[2].vdn, R[1][i], R[2][i], auw);
+    }
+    if (wup) {
+      Fup = weno_flux(LM(1, R[1][i]), LM(2, R[2][i]), LM(3, R[3][i]), LP(2, R[2][i]), LP(3, R[3][i]),
+                      LP(4, R[4][i]), eps);
+    } else {
+      Fup = ATT ? uw_flux(fl[2].vup, att(R[2][i]) * R[2][i], att(R[3][i]) * R[3][i], auw)
+                : uw_flux(fl[2].vup, R[2][i], R[3][i], auw);
+    }
+    const T div = (g.sup * Fup - g.sdn * Fdn) * g.inv_sdth + (F[i + 1] - F[i]) * g.inv_sdph;
+    o[i] = sb * R[2][i] - cdt * div;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Advection stage: out = a fn + b fin - c dt F_A(fin).
 // F_A(B)_{j,k} = (sin th_{j+1/2} F_{j+1/2} - sin th_{j-1/2} F_{j-1/2}) / (sin th_j dth)
@@ -322,8 +395,12 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
     const T v = north ? flow[d.flow + 1].vdn : flow[d.flow + nt - 2].vup;
     double acc = 0.0;
     if (s.c != T(0)) {
-      for (int k = threadIdx.x; k < np; k += blockDim.x)
-        acc += double(north ? uw_flux(v, bp, ba[k], auw) : uw_flux(v, ba[k], bp, auw));
+      const T ib0 = T(p.inv_b0);
+      const T ap = p.inv_b0 != 0.0 ? (T(1) - tanh(fabs(bp) * ib0)) * bp : bp;  // attenuated pole flux term
+      for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const T bk = p.inv_b0 != 0.0 ? (T(1) - tanh(fabs(ba[k]) * ib0)) * ba[k] : ba[k];
+        acc += double(north ? uw_flux(v, ap, bk, auw) : uw_flux(v, bk, ap, auw));
+      }
     }
     const double fnp = fn ? double(fn[po]) : 0.0;  // read before the barrier
     const double div = (north ? 1.0 : -1.0) * shc[d.shape].pole_adv * block_sum(acc, sm);
@@ -367,52 +444,8 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
       jj = jj < 1 ? 1 : (jj > nt - 2 ? nt - 2 : jj);
       fl[m] = flow[d.flow + jj];
     }
-    const bool weno = p.weno != 0;
-    // phi faces k-1/2, k = kc .. kc+N
-    T F[N + 1];
-    const T v = fl[2].vp;
-    if (weno) {
-      const T eps = T(p.eps_p);
-      const T av = fabs(v);
-      const T hp = T(0.5) * (v + av), hm = T(0.5) * (v - av);
-#pragma unroll
-      for (int i = 0; i <= N; ++i)
-        F[i] = weno_flux(hp * e[i], hp * e[i + 1], hp * e[i + 2], hm * e[i + 1], hm * e[i + 2],
-                         hm * e[i + 3], eps);
-    } else {
-#pragma unroll
-      for (int i = 0; i <= N; ++i) F[i] = uw_flux(v, e[i + 1], e[i + 2], auw);
-    }
-    // theta faces j-1/2 (f = j-1) and j+1/2 (f = j)
-    const bool wdn = weno && (j - 1 >= 2) && (j - 1 <= nt - 4);
-    const bool wup = weno && (j >= 2) && (j <= nt - 4);
-    const T eps = T(p.eps_t);
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      T Fdn, Fup;
-      if (wdn) {
-        Fdn = weno_flux(T(0.5) * R[0][i] * (fl[0].vdn + fl[0].alpha),
-                        T(0.5) * R[1][i] * (fl[1].vdn + fl[1].alpha),
-                        T(0.5) * R[2][i] * (fl[2].vdn + fl[2].alpha),
-                        T(0.5) * R[1][i] * (fl[1].vup - fl[1].alpha),
-                        T(0.5) * R[2][i] * (fl[2].vup - fl[2].alpha),
-                        T(0.5) * R[3][i] * (fl[3].vup - fl[3].alpha), eps);
-      } else {
-        Fdn = uw_flux(fl[2].vdn, R[1][i], R[2][i], auw);
-      }
-      if (wup) {
-        Fup = weno_flux(T(0.5) * R[1][i] * (fl[1].vdn + fl[1].alpha),
-                        T(0.5) * R[2][i] * (fl[2].vdn + fl[2].alpha),
-                        T(0.5) * R[3][i] * (fl[3].vdn + fl[3].alpha),
-                        T(0.5) * R[2][i] * (fl[2].vup - fl[2].alpha),
-                        T(0.5) * R[3][i] * (fl[3].vup - fl[3].alpha),
-                        T(0.5) * R[4][i] * (fl[4].vup - fl[4].alpha), eps);
-      } else {
-        Fup = uw_flux(fl[2].vup, R[2][i], R[3][i], auw);
-      }
-      const T div = (g.sup * Fup - g.sdn * Fdn) * g.inv_sdth + (F[i + 1] - F[i]) * g.inv_sdph;
-      o[i] = s.b * R[2][i] - cdt * div;
-    }
+    if (p.inv_b0 != 0.0) adv_divergence<T, N, true>(p, g, fl, R, e, j, nt, s.b, cdt, auw, o);
+    else adv_divergence<T, N, false>(p, g, fl, R, e, j, nt, s.b, cdt, auw, o);
   }
   if (fn != nullptr && s.a != T(0)) {
     T f0[N];

@@ -44,7 +44,7 @@ class sft_flow_params(C.Structure):
                 ("m1", C.c_double), ("m3", C.c_double), ("m5", C.c_double),
                 ("nu", C.c_double), ("alpha_uw", C.c_double), ("cfl_safety", C.c_double),
                 ("eps_w", C.c_double), ("adv_space", C.c_int32), ("adv_time", C.c_int32),
-                ("diffusion", C.c_int32), ("advection", C.c_int32)]
+                ("diffusion", C.c_int32), ("advection", C.c_int32), ("atten_b0", C.c_double)]
 
 
 class sft_assim_params(C.Structure):
@@ -160,12 +160,13 @@ class FlowParams:
     adv_time: str = "ssprk43"
     diffusion: str = "rkl2"
     advection: bool = True
+    atten_b0: float = 0.0   # Eq. (flow_attenuation) saturation field in G; 0 = off
 
     def to_c(self):
         return sft_flow_params(self.d0, self.d2, self.d4, self.m1, self.m3, self.m5, self.nu,
                                self.alpha_uw, self.cfl_safety, self.eps_w,
                                ADV_SPACE[self.adv_space], ADV_TIME[self.adv_time],
-                               DIFFUSION[self.diffusion], 1 if self.advection else 0)
+                               DIFFUSION[self.diffusion], 1 if self.advection else 0, self.atten_b0)
 
 
 @dataclass

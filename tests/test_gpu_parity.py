@@ -317,3 +317,24 @@ def test_fused_path_unavailable_for_small_grids_and_fp64():
         g.set_fusion(4)
     g2 = Grid([(64, 64)], "fp64")
     assert g2.get_fusion() == 1
+
+
+@pytest.mark.parametrize("prec,space", [("fp64", "weno3"), ("fp64", "upwind"), ("fp32", "weno3")])
+def test_flow_attenuation_matches_oracle(prec, space):
+    """Eq. (flow_attenuation) with B_0 = 150 G and 400 G on active-region maps
+    (300-1000 G pairs), beside a realization without attenuation in the same
+    launches; the attenuation visibly changes the result."""
+    shapes = [(41, 96), (41, 96), (33, 70)]
+    draws = I.draw_realization_params(len(shapes), seed=8)
+    params = [params_from_draw(d, adv_space=space, atten_b0=b0) for d, b0 in zip(draws, (150.0, 0.0, 400.0))]
+    g = Grid(shapes, prec)
+    maps = [I.initial_map(*s, seed=20 + r) for r, s in enumerate(shapes)]
+    for r, m in enumerate(maps):
+        g.set_state(r, m)
+    g.set_flows(params)
+    g.step(12.0)
+    for r, s in enumerate(shapes):
+        ref = oracle_run(s, params[r], maps[r], 12.0)
+        assert rel_linf(g.get_state(r), ref.B) <= TOL[prec], (r, rel_linf(g.get_state(r), ref.B))
+    plain = oracle_run(shapes[0], params_from_draw(draws[0], adv_space=space), maps[0], 12.0)
+    assert rel_linf(g.get_state(0), plain.B) > 100 * TOL[prec]
