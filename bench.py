@@ -129,11 +129,11 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def make_inputs(nreal, rank):
+def make_inputs(nreal, rank, atten_b0=0.0):
     import sft_inputs as I
     from paper_2501_06377_gb300.sft import FlowParams
     draws = I.draw_realization_params(nreal, seed=3 + 1000 * rank)
-    params = [FlowParams(*d) for d in draws]
+    params = [FlowParams(*d, atten_b0=atten_b0) for d in draws]
     maps = [I.initial_map(NT, NP, seed=1 + i + 100 * rank).astype(np.float32) for i in range(8)]
     return params, maps
 
@@ -256,7 +256,7 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     stream = torch.cuda.Stream()
     nreal = args.nreal
-    params, maps = make_inputs(nreal, rank)
+    params, maps = make_inputs(nreal, rank, args.atten_b0)
     g = Grid([(NT, NP)] * nreal, "fp32", stream=stream)
     for r in range(nreal):
         g.set_state(r, maps[r % len(maps)])
@@ -344,6 +344,7 @@ def run_gpu(args, rank, world, local_rank):
                        * world / (ms * 1e-3),
                        "rkl2_stages_per_step": st["diff_cell_stages"] / max(st["cell_updates"], 1),
                        "graph": True, "rkl2_stages_per_launch": g.get_fusion(),
+                       "flow_attenuation_b0": args.atten_b0,
                        "ms_per_step_split": {"rkl2": st["diff_ms"] / args.steps,
                                              "advection": st["adv_ms"] / args.steps,
                                              "rest": (ms - st["diff_ms"] - st["adv_ms"]) / args.steps}},
@@ -469,6 +470,8 @@ def main():
     ap.add_argument("--nreal", type=int, default=NREAL,
                     help="realizations per GPU (smaller only for profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--atten-b0", type=float, default=0.0,
+                    help="flow attenuation saturation field in G (Eq. flow_attenuation); 0 = off")
     ap.add_argument("--surrogate", action="store_true",
                     help="learned-surrogate ensemble evaluation instead of the solver benchmark")
     ap.add_argument("--pairs", type=int, default=20000)
