@@ -573,6 +573,7 @@ class Params:
     safety: float = 0.9
     eps_w: object = "h"
     atten_b0: float = 0.0        # Eq. (flow_attenuation) saturation field (G); 0 = off
+    splitting: str = "lie"       # "lie" (Eq. num_opsplit_nostrang) | "strang" (Eq. num_opsplit_strang)
 
 
 @dataclass
@@ -604,22 +605,37 @@ class Realization:
     def L(self, B):
         return diffusion_operator(self.g, B, self.nu_hh)
 
-    def lie_step(self, dt):
-        """Eq. (num_opsplit_nostrang): B* = A(B^n, dt), B** = D(B*, dt)."""
-        B = self.B
-        if self.p.advection:
-            B = ADV_TIME[self.p.adv_time](B, dt, self.FA)
+    def _A(self, B, dt):
+        return ADV_TIME[self.p.adv_time](B, dt, self.FA) if self.p.advection else B
+
+    def _D(self, B, dt):
         if self.p.diffusion == "rkl2":
-            B = rkl2_advance(B, dt, self.L, rkl2_stage_count(dt, self.dt_euler))
-        elif self.p.diffusion == "fe":
-            B = fe_diffusion_advance(B, dt, self.L, self.dt_euler)
-        self.B = B
+            return rkl2_advance(B, dt, self.L, rkl2_stage_count(dt, self.dt_euler))
+        if self.p.diffusion == "fe":
+            return fe_diffusion_advance(B, dt, self.L, self.dt_euler)
+        return B
+
+    def lie_step(self, dt):
+        """One time step (Sec. 3.5).  Eq. (num_opsplit_nostrang):
+        B* = A(B^n, dt), B** = D(B*, dt).  Eq. (num_opsplit_strang) with the
+        source S the identity (assimilation follows the advance):
+        B* = A(B^n, dt/2), B** = D(B*, dt), B^{n+1} = A(B**, dt/2)."""
+        if self.p.splitting == "strang":
+            self.B = self._A(self._D(self._A(self.B, 0.5 * dt), dt), 0.5 * dt)
+        else:
+            self.B = self._D(self._A(self.B, dt), dt)
+
+    def flow_dt_limit(self):
+        """The step the flow allows: its CFL limit, twice that with Strang
+        splitting (each advection advance is dt/2, Sec. 3.5)."""
+        return 2.0 * self.dt_adv if self.p.splitting == "strang" else self.dt_adv
 
     def next_dt(self, t_target):
         """Sec. 3.4: start from the time remaining to the target (the next
         output / assimilation time) and reduce it to the stable flow step."""
         remaining = t_target - self.t
-        return remaining if remaining <= self.dt_adv else self.dt_adv
+        lim = self.flow_dt_limit()
+        return remaining if remaining <= lim else lim
 
     def advance(self, t_target, max_steps=None):
         n = 0
