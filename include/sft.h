@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define SFT_ABI_VERSION 2
+#define SFT_ABI_VERSION 3
 
 typedef struct sft_grid* sft_handle;
 
@@ -75,6 +75,10 @@ enum { SFT_ADV_WENO3_CSH = 0, SFT_ADV_UPWIND = 1 };
 enum { SFT_TIME_SSPRK43 = 0, SFT_TIME_SSPRK33 = 1, SFT_TIME_FE = 2 };
 /* diffusion time scheme (Sec. 3.7.2) */
 enum { SFT_DIFF_RKL2 = 0, SFT_DIFF_OFF = 1 };
+/* operator splitting of one step (Sec. 3.5): Lie, Eq. (num_opsplit_nostrang):
+ * A(dt) then D(dt); Strang, Eq. (num_opsplit_strang) with the source the
+ * identity: A(dt/2), D(dt), A(dt/2) -- the flow then allows twice the step */
+enum { SFT_SPLIT_LIE = 0, SFT_SPLIT_STRANG = 1 };
 
 typedef struct {
   int32_t ntheta; /* >= 5, poles included */
@@ -97,6 +101,8 @@ typedef struct {
                          where it meets the field (each flux term v B_i becomes v a_i B_i; the
                          LLF bound and the CFL limit keep the unattenuated flow), G; 0 = off,
                          otherwise > 0 (the paper's default is 500 G) */
+  int32_t splitting;  /* SFT_SPLIT_* (must be the same for all realizations) */
+  int32_t reserved;   /* 0 */
 } sft_flow_params;
 
 /* Assimilation weight and balance options (Sec. 2.3). */
@@ -253,8 +259,10 @@ int32_t sft_get_tile_rows(sft_handle h, int32_t shape_id);
 /* Number of realizations per wave for the handle's HBM budget. */
 int32_t sft_wave_size(sft_handle h);
 
-/* The flow CFL limit (hours) and RKL2 stage count for a step of dt hours of
- * realization r, as sft_step would use them.  Host-only computation. */
+/* The flow CFL limit of one advection advance (hours; a Strang step may be
+ * twice as long, its two advances being half steps) and the RKL2 stage count
+ * for a step of dt hours of realization r, as sft_step would use them.
+ * Host-only computation. */
 sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cfl, double* dt_euler,
                          int32_t* stages);
 

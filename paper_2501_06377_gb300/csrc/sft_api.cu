@@ -145,10 +145,11 @@ struct sft_grid {
   int geo_rows = 0, flow_rows = 0, col_entries = 0;
   // step machinery
   bool flows_set = false;
+  bool strang = false;         // Strang splitting (Sec. 3.5): A(dt/2) D(dt) A(dt/2)
   bool use_graphs = true;
   bool profiling = false;
   uint64_t use_counter = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {};      // advection, RKL2, second (Strang) advection phases
   cudaStream_t side[kMaxChains] = {};           // chains 1.. of the fused RKL2 passes
   int n_sm = 152;                               // streaming multiprocessors of the device
   cudaEvent_t fork = nullptr;                   // ordering events (no timing)
@@ -421,6 +422,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     tile_end.push_back((int)tiles.size());
     StepParam& p = sp[r];
     p.dt = dt[i];
+    p.dt_adv = h->strang ? 0.5 * dt[i] : dt[i];
     p.nudt = ri.nu * dt[i];
     p.eps_t = ri.fp.eps_w > 0.0 ? ri.fp.eps_w : sh.dth;
     p.eps_p = ri.fp.eps_w > 0.0 ? ri.fp.eps_w : sh.dph;
@@ -523,6 +525,43 @@ cudaError_t record(cudaEvent_t e, cudaStream_t st, bool capturing) {
   return capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
 }
 
+// One advection advance (the SSPRK / FE stages) of every realization, by
+// StepParam::dt_adv.
+template <typename T>
+sft_status enqueue_adv(sft_handle h, Config& c, cudaStream_t st) {
+  if (c.n_adv_tiles <= 0) return SFT_OK;
+  T* B = ptr<T>(h->state);
+  T* W0 = ptr<T>(h->work[0]);
+  T* W1 = ptr<T>(h->work[1]);
+  const auto* geo = ptr<const RowGeo<T>>(h->d_geo);
+  const auto* flow = ptr<const RowFlow<T>>(h->d_flow);
+  const int adv_time = h->reals.empty() ? SFT_TIME_SSPRK43 : h->reals[0].fp.adv_time;
+  std::vector<AdvStage<T>> stages;
+  auto S = [&](const T* fin, int finw, const T* fn, int fnw, T* out, int outw, double a, double b, double cc) {
+    stages.push_back(AdvStage<T>{fin, fn, out, finw, fnw, outw, T(a), T(b), T(cc)});
+  };
+  if (adv_time == SFT_TIME_SSPRK43) {
+    S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 0.5);
+    S(W0, 1, nullptr, 0, W1, 1, 0.0, 1.0, 0.5);
+    S(W1, 1, B, 0, W0, 1, 2.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0);
+    S(W0, 1, nullptr, 0, B, 0, 0.0, 1.0, 0.5);
+  } else if (adv_time == SFT_TIME_SSPRK33) {
+    S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 1.0);
+    S(W0, 1, B, 0, W1, 1, 0.75, 0.25, 0.25);
+    S(W1, 1, B, 0, B, 0, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0);
+  } else {
+    S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 1.0);
+    S(W0, 1, nullptr, 0, B, 0, 0.0, 1.0, 0.0);  // copy back
+  }
+  for (auto& s : stages) {
+    SFT_CUDA(h, launch_adv_stage<T>(c.n_adv_tiles, st, c.d_tiles, h->d_desc, c.d_sp, geo, flow, h->d_shc, B, W0,
+                                    W1, s));
+  }
+  return SFT_OK;
+}
+
+// The launches of one step: advection, then the RKL2 stages (Lie); with
+// Strang splitting a second advection advance follows (each by dt/2).
 template <typename T>
 sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool capturing) {
   const cudaStream_t st = h->stream;
@@ -531,36 +570,10 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
   T* W1 = ptr<T>(h->work[1]);
   T* W2 = ptr<T>(h->work[2]);
   const auto* geo = ptr<const RowGeo<T>>(h->d_geo);
-  const auto* flow = ptr<const RowFlow<T>>(h->d_flow);
-  int adv_time = SFT_TIME_SSPRK43;
-  for (const auto& ri : h->reals) {
-    adv_time = ri.fp.adv_time;
-    break;
-  }
   if (record_events) SFT_CUDA(h, record(h->ev[0], st, capturing));
-  if (c.n_adv_tiles > 0) {
-    std::vector<AdvStage<T>> stages;
-    auto S = [&](const T* fin, int finw, const T* fn, int fnw, T* out, int outw, double a, double b,
-                 double cc) {
-      stages.push_back(AdvStage<T>{fin, fn, out, finw, fnw, outw, T(a), T(b), T(cc)});
-    };
-    if (adv_time == SFT_TIME_SSPRK43) {
-      S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 0.5);
-      S(W0, 1, nullptr, 0, W1, 1, 0.0, 1.0, 0.5);
-      S(W1, 1, B, 0, W0, 1, 2.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0);
-      S(W0, 1, nullptr, 0, B, 0, 0.0, 1.0, 0.5);
-    } else if (adv_time == SFT_TIME_SSPRK33) {
-      S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 1.0);
-      S(W0, 1, B, 0, W1, 1, 0.75, 0.25, 0.25);
-      S(W1, 1, B, 0, B, 0, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0);
-    } else {
-      S(B, 0, nullptr, 0, W0, 1, 0.0, 1.0, 1.0);
-      S(W0, 1, nullptr, 0, B, 0, 0.0, 1.0, 0.0);  // copy back
-    }
-    for (auto& s : stages) {
-      SFT_CUDA(h, launch_adv_stage<T>(c.n_adv_tiles, st, c.d_tiles, h->d_desc, c.d_sp, geo, flow,
-                                      h->d_shc, B, W0, W1, s));
-    }
+  {
+    sft_status sa = enqueue_adv<T>(h, c, st);
+    if (sa != SFT_OK) return sa;
   }
   if (record_events) {
     SFT_CUDA(h, record(h->ev[1], st, capturing));
@@ -603,6 +616,12 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
     }
   }
   if (record_events) SFT_CUDA(h, record(h->ev[3], st, capturing));
+  if (h->strang) {
+    if (record_events) SFT_CUDA(h, record(h->ev[4], st, capturing));
+    sft_status sa = enqueue_adv<T>(h, c, st);
+    if (sa != SFT_OK) return sa;
+    if (record_events) SFT_CUDA(h, record(h->ev[5], st, capturing));
+  }
   return SFT_OK;
 }
 
@@ -629,7 +648,8 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     const double rem = t_target - ri.t;
     if (!(rem > 0.0)) continue;
     // Sec. 3.4: the remaining time, cut to the flow limit
-    dt[i] = rem <= ri.dt_cfl ? rem : ri.dt_cfl;
+    const double lim = h->strang ? 2.0 * ri.dt_cfl : ri.dt_cfl;  // Strang: two dt/2 advances
+    dt[i] = rem <= lim ? rem : lim;
     s[i] = ri.fp.diffusion == SFT_DIFF_RKL2 ? rkl2_stages(dt[i], ri.dt_euler) : 0;
     *any = true;
   }
@@ -680,21 +700,27 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     sft_status st = enqueue_step<T>(h, *c, ev, false);
     if (st != SFT_OK) return st;
   }
-  const int n_adv = c->n_adv_tiles > 0 ? adv_stage_count(h) : 0;
+  const int n_adv = (c->n_adv_tiles > 0 ? adv_stage_count(h) : 0) * (h->strang ? 2 : 1);
   // RKL2 passes (one fused pass = K stages, over both chains) and launches
   const int n_diff = c->fused ? (c->smax >= 1 ? 1 + (c->smax - 1 + fused::K - 1) / fused::K : 0) : c->smax;
   const int64_t n_diff_launches = c->fused ? (c->smax >= 1 ? 1 + c->fused_launches : 0) : c->smax;
   h->stats.kernel_launches += n_adv + n_diff_launches;
   h->stats.realization_steps += c->realization_steps;
   h->stats.cell_updates += c->cell_updates;
-  h->stats.adv_cell_stages += c->cells_adv * (adv_stage_count(h) == 2 ? 1 : adv_stage_count(h));
+  h->stats.adv_cell_stages +=
+      c->cells_adv * (adv_stage_count(h) == 2 ? 1 : adv_stage_count(h)) * (h->strang ? 2 : 1);
   (void)0;
   h->stats.diff_cell_stages += c->cell_stages_diff;
   if (ev) {
-    SFT_CUDA(h, cudaEventSynchronize(h->ev[3]));
+    SFT_CUDA(h, cudaEventSynchronize(h->ev[h->strang ? 5 : 3]));
     float a = 0.f, d = 0.f;
     SFT_CUDA(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
     SFT_CUDA(h, cudaEventElapsedTime(&d, h->ev[2], h->ev[3]));
+    if (h->strang) {
+      float a2 = 0.f;
+      SFT_CUDA(h, cudaEventElapsedTime(&a2, h->ev[4], h->ev[5]));
+      a += a2;
+    }
     h->stats.adv_ms += a;
     h->stats.diff_ms += d;
     h->stats.adv_launches += n_adv;
@@ -707,7 +733,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     // SSPRK(4,3): 2 + 2 + 3 + 2 = 9 words; SSPRK(3,3): 2 + 3 + 3 = 8; FE + copy: 4.
     h->stats.diff_bytes += eb * c->diff_words;
     const int na = adv_stage_count(h);
-    h->stats.adv_bytes += (na == 4 ? 9.0 : (na == 3 ? 8.0 : 4.0)) * eb * c->cells_adv;
+    h->stats.adv_bytes += (na == 4 ? 9.0 : (na == 3 ? 8.0 : 4.0)) * eb * c->cells_adv * (h->strang ? 2 : 1);
   }
   for (int i = 0; i < nw; ++i) {
     if (!(dt[i] > 0.0)) continue;
@@ -1123,8 +1149,11 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
   SFT_CUDA(h, cudaSetDevice(h->device));
   for (int r = 0; r < h->n_real; ++r) {
     const sft_flow_params& p = params[r];
-    if (p.adv_time != params[0].adv_time || p.diffusion != params[0].diffusion)
-      return fail(h, SFT_ERR_ARG, "adv_time and diffusion must be the same for all realizations");
+    if (p.adv_time != params[0].adv_time || p.diffusion != params[0].diffusion ||
+        p.splitting != params[0].splitting)
+      return fail(h, SFT_ERR_ARG, "adv_time, diffusion and splitting must be the same for all realizations");
+    if (p.splitting != SFT_SPLIT_LIE && p.splitting != SFT_SPLIT_STRANG)
+      return fail(h, SFT_ERR_ARG, "bad splitting");
     if (p.adv_space != SFT_ADV_WENO3_CSH && p.adv_space != SFT_ADV_UPWIND)
       return fail(h, SFT_ERR_ARG, "bad adv_space");
     if (p.adv_time < SFT_TIME_SSPRK43 || p.adv_time > SFT_TIME_FE)
@@ -1143,7 +1172,10 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
     w.configs.clear();
   }
   sft_status st = h->prec == SFT_FP32 ? set_flows_t<float>(h, params) : set_flows_t<double>(h, params);
-  if (st == SFT_OK) h->flows_set = true;
+  if (st == SFT_OK) {
+    h->flows_set = true;
+    h->strang = params[0].splitting == SFT_SPLIT_STRANG;
+  }
   return st;
 }
 

@@ -73,6 +73,7 @@ struct ShapeConst {
 // Per-realization parameters of one time step.
 struct StepParam {
   double dt;        // hours; 0 = idle this step
+  double dt_adv;    // hours of one advection advance: dt (Lie) or dt/2 (Strang)
   double nudt;      // nu * dt (R_sun^2)
   double eps_t;     // WENO eps in the theta sweep
   double eps_p;     // WENO eps in the phi sweep

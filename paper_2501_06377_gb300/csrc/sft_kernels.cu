@@ -382,7 +382,7 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
   const T* fn = s.fn ? s.fn + (s.fn_work ? d.woff : d.off) : nullptr;
   T* out = s.out + (s.out_work ? d.woff : d.off);
   const int pitch = d.pitch, np = d.np, nt = d.nt;
-  const T cdt = s.c * T(p.dt);
+  const T cdt = s.c * T(p.dt_adv);
   const T auw = T(p.alpha_uw);
 
   if (kind != 0) {
@@ -404,7 +404,7 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
     }
     const double fnp = fn ? double(fn[po]) : 0.0;  // read before the barrier
     const double div = (north ? 1.0 : -1.0) * shc[d.shape].pole_adv * block_sum(acc, sm);
-    const T o = T(double(s.a) * fnp + double(s.b) * double(bp) - double(s.c) * p.dt * div);
+    const T o = T(double(s.a) * fnp + double(s.b) * double(bp) - double(s.c) * p.dt_adv * div);
     for (int k = threadIdx.x; k < np; k += blockDim.x) out[po + k] = o;
     return;
   }

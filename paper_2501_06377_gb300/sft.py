@@ -27,6 +27,7 @@ SFT_FP32, SFT_FP64 = 0, 1
 ADV_SPACE = {"weno3": 0, "upwind": 1}
 ADV_TIME = {"ssprk43": 0, "ssprk33": 1, "fe": 2}
 DIFFUSION = {"rkl2": 0, "off": 1}
+SPLITTING = {"lie": 0, "strang": 1}
 
 
 class SFTError(RuntimeError):
@@ -44,7 +45,8 @@ class sft_flow_params(C.Structure):
                 ("m1", C.c_double), ("m3", C.c_double), ("m5", C.c_double),
                 ("nu", C.c_double), ("alpha_uw", C.c_double), ("cfl_safety", C.c_double),
                 ("eps_w", C.c_double), ("adv_space", C.c_int32), ("adv_time", C.c_int32),
-                ("diffusion", C.c_int32), ("advection", C.c_int32), ("atten_b0", C.c_double)]
+                ("diffusion", C.c_int32), ("advection", C.c_int32), ("atten_b0", C.c_double),
+                ("splitting", C.c_int32), ("reserved", C.c_int32)]
 
 
 class sft_assim_params(C.Structure):
@@ -161,12 +163,14 @@ class FlowParams:
     diffusion: str = "rkl2"
     advection: bool = True
     atten_b0: float = 0.0   # Eq. (flow_attenuation) saturation field in G; 0 = off
+    splitting: str = "lie"  # "lie" | "strang" (Sec. 3.5), the same for all realizations
 
     def to_c(self):
         return sft_flow_params(self.d0, self.d2, self.d4, self.m1, self.m3, self.m5, self.nu,
                                self.alpha_uw, self.cfl_safety, self.eps_w,
                                ADV_SPACE[self.adv_space], ADV_TIME[self.adv_time],
-                               DIFFUSION[self.diffusion], 1 if self.advection else 0, self.atten_b0)
+                               DIFFUSION[self.diffusion], 1 if self.advection else 0, self.atten_b0,
+                               SPLITTING[self.splitting], 0)
 
 
 @dataclass
