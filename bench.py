@@ -129,11 +129,11 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def make_inputs(nreal, rank, atten_b0=0.0):
+def make_inputs(nreal, rank, atten_b0=0.0, splitting="lie"):
     import sft_inputs as I
     from paper_2501_06377_gb300.sft import FlowParams
     draws = I.draw_realization_params(nreal, seed=3 + 1000 * rank)
-    params = [FlowParams(*d, atten_b0=atten_b0) for d in draws]
+    params = [FlowParams(*d, atten_b0=atten_b0, splitting=splitting) for d in draws]
     maps = [I.initial_map(NT, NP, seed=1 + i + 100 * rank).astype(np.float32) for i in range(8)]
     return params, maps
 
@@ -256,7 +256,7 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     stream = torch.cuda.Stream()
     nreal = args.nreal
-    params, maps = make_inputs(nreal, rank, args.atten_b0)
+    params, maps = make_inputs(nreal, rank, args.atten_b0, args.splitting)
     g = Grid([(NT, NP)] * nreal, "fp32", stream=stream)
     for r in range(nreal):
         g.set_state(r, maps[r % len(maps)])
@@ -287,6 +287,7 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local_rank) as clk:
+        t_before = sum(g.get_time())
         e0.record(stream)
         steps_done = 0
         for _ in range(args.steps):
@@ -294,6 +295,7 @@ def run_gpu(args, rank, world, local_rank):
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
+    sim_hours = sum(g.get_time()) - t_before  # simulated hours advanced, summed over realizations
     st = g.stats()
     ms = max_over_ranks(ms)
     updates = st["cell_updates"] * world
@@ -344,7 +346,8 @@ def run_gpu(args, rank, world, local_rank):
                        * world / (ms * 1e-3),
                        "rkl2_stages_per_step": st["diff_cell_stages"] / max(st["cell_updates"], 1),
                        "graph": True, "rkl2_stages_per_launch": g.get_fusion(),
-                       "flow_attenuation_b0": args.atten_b0,
+                       "flow_attenuation_b0": args.atten_b0, "splitting": args.splitting,
+                       "realization_hours_per_s": sim_hours * world / (ms * 1e-3),
                        "ms_per_step_split": {"rkl2": st["diff_ms"] / args.steps,
                                              "advection": st["adv_ms"] / args.steps,
                                              "rest": (ms - st["diff_ms"] - st["adv_ms"]) / args.steps}},
@@ -470,6 +473,8 @@ def main():
     ap.add_argument("--nreal", type=int, default=NREAL,
                     help="realizations per GPU (smaller only for profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--splitting", default="lie", choices=["lie", "strang"],
+                    help="operator splitting of a step (Sec. 3.5)")
     ap.add_argument("--atten-b0", type=float, default=0.0,
                     help="flow attenuation saturation field in G (Eq. flow_attenuation); 0 = off")
     ap.add_argument("--surrogate", action="store_true",
