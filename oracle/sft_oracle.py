@@ -284,6 +284,15 @@ def constant_nu(g: Grid, nu_rs2_hr: float):
     return np.full((g.nt - 1, g.np), float(nu_rs2_hr))
 
 
+def grid_nu(g: Grid, alpha_nu: float):
+    """Eq. (diffgrid): nu_g = alpha_nu [(dtheta)^2 + (dphi sin theta)^2], on
+    the half-half grid of the operator, shape (nt-1, np).  Reading: nu lives
+    where the operator takes it, at theta_{f+1/2} (uniform in phi); alpha_nu
+    is in 1/hour (the time unit), so nu_g is in R_sun^2/hour."""
+    nu = alpha_nu * (g.dth ** 2 + (g.dph * g.sin_th) ** 2)   # sin_th[f] = sin(theta_{f+1/2})
+    return np.repeat(nu[:, None], g.np, axis=1)
+
+
 def diffusion_operator(g: Grid, B, nu_hh):
     """Eq. (diffusion_op) on interior rows, App. A on the poles.
     nu_hh[f, k] = nu_{f+1/2, k+1/2}."""
@@ -574,6 +583,7 @@ class Params:
     eps_w: object = "h"
     atten_b0: float = 0.0        # Eq. (flow_attenuation) saturation field (G); 0 = off
     splitting: str = "lie"       # "lie" (Eq. num_opsplit_nostrang) | "strang" (Eq. num_opsplit_strang)
+    nu_grid_alpha: float = 0.0   # > 0: grid-based nu of Eq. (diffgrid) (1/hour) instead of nu
 
 
 @dataclass
@@ -592,7 +602,8 @@ class Realization:
     def __post_init__(self):
         p, g = self.p, self.g
         self.vt, self.vp = flow_profiles(g, p.d0, p.d2, p.d4, p.m1, p.m3, p.m5)
-        self.nu_hh = constant_nu(g, p.nu * KM2_S_TO_RS2_HR)
+        self.nu_hh = (grid_nu(g, p.nu_grid_alpha) if p.nu_grid_alpha > 0.0
+                      else constant_nu(g, p.nu * KM2_S_TO_RS2_HR))
         self.dt_adv = (advection_dt_limit(g, self.vt, self.vp, p.adv_time, p.safety)
                        if p.advection else math.inf)
         self.dt_euler = euler_dt_limit(g, self.nu_hh) if p.diffusion != "off" else math.inf

@@ -133,3 +133,44 @@ def test_soccer_ball_one_rkl2_step_matches_paper(paper_values):
     u = O.rkl2_advance(u0, v["t_hours"], lambda y: M @ y, s)
     ex = O.unique_unknowns(I.soccer_ball(g.nt, g.np, nu, v["t_hours"]))
     assert O.hh_metric(u, ex) == pytest.approx(v["value"], rel=v["rel_tol"])
+
+
+# --------------------------------------------------------------------------
+# Eq. (diffgrid): grid-based diffusivity (the flux-preserving smoother)
+# --------------------------------------------------------------------------
+def test_grid_nu_closed_form_and_conservation():
+    g = O.Grid(65, 128)
+    nu = O.grid_nu(g, 0.5)
+    th0 = 0.5 * g.dth   # theta_{1/2}
+    assert nu[0, 0] == pytest.approx(0.5 * (g.dth ** 2 + (g.dph * math.sin(th0)) ** 2), rel=1e-15)
+    assert np.all(nu[:, 1:] == nu[:, :1])             # uniform in phi
+    assert nu[(g.nt - 1) // 2 - 1].max() <= 0.5 * (g.dth ** 2 + g.dph ** 2)
+    B = I.initial_map(65, 128, seed=11)
+    L = O.diffusion_operator(g, B, nu)
+    assert abs((g.area * L).sum()) <= 1e-13 * (g.area * np.abs(L)).sum()
+    # the operator equals the entry-by-entry Eq. (diffusion_matrix) assembly
+    M = O.diffusion_matrix(g, nu)
+    u = O.unique_unknowns(B)
+    assert np.abs(M @ u - O.unique_unknowns(L)).max() <= 1e-12 * np.abs(L).max()
+
+
+def test_grid_nu_smoother_flattens_a_blob_and_keeps_flux():
+    """One smoothing hour with alpha = 0.5 on a narrow Gaussian (sigma = 2
+    cells): the peak drops, the blob widens, the total flux is unchanged.
+    (A single-cell spike rings under one large RKL2 step: the paper's PTL
+    limit, which it only cites, is what keeps such runs oscillation-free.)"""
+    g = O.Grid(65, 128)
+    th, ph = np.meshgrid(g.theta, g.phi, indexing="ij")
+    d2 = ((th - g.theta[20]) / g.dth) ** 2 + ((ph - g.phi[40]) * np.sin(g.theta[20]) / g.dth) ** 2
+    B = 1000.0 * np.exp(-d2 / 8.0)
+    r = O.Realization(g, O.Params(advection=False, nu_grid_alpha=0.5), B)
+    r.advance(1.0)
+    assert r.B.max() < 0.95 * B.max()
+    assert r.B[26, 40] > B[26, 40] and r.B.min() > -1e-3 * B.max()   # the tail (3 sigma) grows
+    assert O.total_flux(g, r.B) == pytest.approx(O.total_flux(g, B), rel=1e-13)
+
+
+def test_grid_nu_euler_limit_scales_inversely_with_alpha():
+    g = O.Grid(65, 128)
+    assert O.euler_dt_limit(g, O.grid_nu(g, 0.5)) == pytest.approx(
+        2.0 * O.euler_dt_limit(g, O.grid_nu(g, 1.0)), rel=1e-14)
