@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define SFT_ABI_VERSION 3
+#define SFT_ABI_VERSION 4
 
 typedef struct sft_grid* sft_handle;
 
@@ -89,7 +89,8 @@ typedef struct {
 typedef struct {
   double d0, d2, d4;  /* Eq. (dr): v_phi = (d0 + d2 cos^2 + d4 cos^4) sin(theta), m/s */
   double m1, m3, m5;  /* Eq. (mf): v_theta = -(m1 cos + m3 cos^3 + m5 cos^5) sin(theta), m/s */
-  double nu;          /* diffusivity, km^2/s (constant per realization), >= 0 */
+  double nu;          /* diffusivity, km^2/s (constant per realization), >= 0; unused when
+                         nu_grid_alpha > 0 */
   double alpha_uw;    /* upwind factor of the UW/CD flux (Sec. 3.6.1); 1 = upwind */
   double cfl_safety;  /* safety factor on the flow CFL limit (Sec. 3.6.2), e.g. 0.9 */
   double eps_w;       /* WENO epsilon: <= 0 selects eps_w = h (WENO3-CS(h)), > 0 a constant */
@@ -103,6 +104,10 @@ typedef struct {
                          otherwise > 0 (the paper's default is 500 G) */
   int32_t splitting;  /* SFT_SPLIT_* (must be the same for all realizations) */
   int32_t reserved;   /* 0 */
+  double nu_grid_alpha; /* > 0: the grid-based diffusivity of Eq. (diffgrid),
+                           nu_g = nu_grid_alpha [(dtheta)^2 + (dphi sin theta)^2] at the theta
+                           faces of the operator (1/hour; the map smoother of Sec. 2.2), in
+                           place of nu; 0 = the constant nu */
 } sft_flow_params;
 
 /* Assimilation weight and balance options (Sec. 2.3). */

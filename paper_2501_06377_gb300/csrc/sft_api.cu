@@ -58,6 +58,7 @@ struct RealInfo {
   double nu = 0.0;        // R_sun^2/hr
   double dt_cfl = 0.0;    // hours (inf when advection is off)
   double dt_euler = 0.0;  // hours (inf when nu == 0)
+  double cap_nu = 1.0;    // nu at the cap faces relative to nudt (grid-based nu: nu_g(theta_1/2))
 };
 
 constexpr int kMaxChains = 2;   // concurrent launch chains of the fused RKL2 passes
@@ -123,6 +124,8 @@ struct sft_grid {
   void* polar = nullptr;       // cap-block scratch of the fused path
   int64_t polar_elems = 0;
   RealDesc* d_desc = nullptr;
+  std::vector<RealDesc> desc;  // host copy (geometry offsets change with grid-based nu)
+  bool geo_custom = false;     // some realization has its own geometry block
   ShapeConst* d_shc = nullptr;
   void* d_geo = nullptr;       // RowGeo<T>
   RowGeoD* d_geod = nullptr;
@@ -219,6 +222,27 @@ void geo_rows(const ShapeInfo& s, std::vector<RowGeo<T>>& g, std::vector<RowGeoD
   }
 }
 
+// Eq. (diffgrid): nu_g at theta face f (f + 1/2), R_sun^2 / hour.
+double grid_nu_face(const ShapeInfo& s, double alpha, int f) {
+  const double a = s.dph * s.sin_h[f];
+  return alpha * (s.dth * s.dth + a * a);
+}
+
+// A realization's own geometry block with the grid-based diffusivity folded
+// into cN, cS, cE (computed in FP64 from the faces' nu, then rounded).
+template <typename T>
+void geo_rows_grid_nu(const ShapeInfo& s, double alpha, std::vector<RowGeo<T>>& g, std::vector<RowGeoD>& gd) {
+  const size_t base = g.size();
+  geo_rows<T>(s, g, gd);
+  for (int j = 1; j < s.nt - 1; ++j) {
+    const double st = s.sin_t[j], ndn = grid_nu_face(s, alpha, j - 1), nup = grid_nu_face(s, alpha, j);
+    RowGeo<T>& r = g[base + j];
+    r.cN = T(ndn * s.sin_h[j - 1] / (s.dth * s.dth * st));
+    r.cS = T(nup * s.sin_h[j] / (s.dth * s.dth * st));
+    r.cE = T(0.5 * (ndn + nup) / (s.dph * s.dph * st * st));
+  }
+}
+
 // ---- Sec. 2.1.1 flows and Sec. 3.6.2 / 3.7.2 limits -----------------------
 struct FlowRows {
   std::vector<double> vt;  // faces f = 0..nt-2
@@ -269,6 +293,20 @@ double euler_limit(const ShapeInfo& s, double nu) {
   const double pole = nu * std::sin(0.5 * s.dth) * s.dph * s.np / (s.dth * s.cap);
   amax = std::max(amax, pole);
   return 1.0 / amax;
+}
+
+// The same limit with the grid-based diffusivity of Eq. (diffgrid).
+double euler_limit_grid(const ShapeInfo& s, double alpha) {
+  double amax = 0.0;
+  for (int j = 1; j < s.nt - 1; ++j) {
+    const double st = s.sin_t[j], ndn = grid_nu_face(s, alpha, j - 1), nup = grid_nu_face(s, alpha, j);
+    const double a = (ndn * s.sin_h[j - 1] + nup * s.sin_h[j]) / (s.dth * s.dth * st) +
+                     (ndn + nup) / (s.dph * s.dph * st * st);
+    amax = std::max(amax, a);
+  }
+  const double line = std::sin(0.5 * s.dth) * s.dph * s.np / (s.dth * s.cap);
+  amax = std::max(amax, std::max(grid_nu_face(s, alpha, 0), grid_nu_face(s, alpha, s.nt - 2)) * line);
+  return amax > 0.0 ? 1.0 / amax : INFINITY;
 }
 
 // RKL2 stage count: smallest s >= 2 with dt <= dt_E (s^2 + s - 2) / 4.
@@ -431,6 +469,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     p.weno = ri.fp.adv_space == SFT_ADV_WENO3_CSH ? 1 : 0;
     p.adv = ri.fp.advection ? 1 : 0;
     p.inv_b0 = ri.fp.atten_b0 > 0.0 ? 1.0 / ri.fp.atten_b0 : 0.0;
+    p.cap_nu = ri.cap_nu;
     p.coef = (int)coefs.size();
     if (s[i] > 0) rkl2_coefs<T>(s[i], coefs);
     else coefs.push_back(Coef<T>{});
@@ -888,13 +927,50 @@ sft_status set_flows_t(sft_handle h, const sft_flow_params* params) {
       rows[ri.flow_row + j] = rf;
     }
     ri.fp = p;
-    ri.nu = p.nu * kKm2sToRs2Hr;
+    const bool grid_nu = p.nu_grid_alpha > 0.0;
+    ri.nu = grid_nu ? 1.0 : p.nu * kKm2sToRs2Hr;  // grid-based nu lives in the geometry block
+    ri.cap_nu = grid_nu ? grid_nu_face(s, p.nu_grid_alpha, 0) : 1.0;
     ri.dt_cfl = p.advection ? cfl_limit(s, f, p) : INFINITY;
-    ri.dt_euler = p.diffusion == SFT_DIFF_RKL2 ? euler_limit(s, ri.nu) : INFINITY;
+    ri.dt_euler = p.diffusion != SFT_DIFF_RKL2 ? INFINITY
+                  : (grid_nu ? euler_limit_grid(s, p.nu_grid_alpha) : euler_limit(s, ri.nu));
     ri.has_flows = true;
   }
   SFT_CUDA(h, cudaMemcpyAsync(h->d_flow, rows.data(), rows.size() * sizeof(RowFlow<T>),
                               cudaMemcpyHostToDevice, h->stream));
+  // geometry: the shapes' blocks, then one block per grid-based-nu realization
+  bool any_grid = false;
+  for (int r = 0; r < h->n_real; ++r) any_grid = any_grid || params[r].nu_grid_alpha > 0.0;
+  if (any_grid || h->geo_custom) {
+    std::vector<RowGeo<T>> g;
+    std::vector<RowGeoD> gd;
+    for (auto& sh : h->shapes) {
+      sh.geo = (int)g.size();
+      geo_rows<T>(sh, g, gd);
+    }
+    for (int r = 0; r < h->n_real; ++r) {
+      const ShapeInfo& sh = h->shapes[h->reals[r].shape];
+      if (params[r].nu_grid_alpha > 0.0) {
+        h->desc[r].geo = (int)g.size();
+        geo_rows_grid_nu<T>(sh, params[r].nu_grid_alpha, g, gd);
+      } else {
+        h->desc[r].geo = sh.geo;
+      }
+    }
+    SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+    if ((int)g.size() != h->geo_rows) {
+      cudaFree(h->d_geo);
+      cudaFree(h->d_geod);
+      h->d_geo = nullptr;
+      h->d_geod = nullptr;
+      SFT_CUDA(h, cudaMalloc(&h->d_geo, g.size() * sizeof(RowGeo<T>)));
+      SFT_CUDA(h, cudaMalloc(&h->d_geod, gd.size() * sizeof(RowGeoD)));
+      h->geo_rows = (int)g.size();
+    }
+    SFT_CUDA(h, cudaMemcpy(h->d_geo, g.data(), g.size() * sizeof(RowGeo<T>), cudaMemcpyHostToDevice));
+    SFT_CUDA(h, cudaMemcpy(h->d_geod, gd.data(), gd.size() * sizeof(RowGeoD), cudaMemcpyHostToDevice));
+    SFT_CUDA(h, cudaMemcpy(h->d_desc, h->desc.data(), h->desc.size() * sizeof(RealDesc), cudaMemcpyHostToDevice));
+    h->geo_custom = any_grid;
+  }
   SFT_CUDA(h, cudaStreamSynchronize(h->stream));
   return SFT_OK;
 }
@@ -1050,6 +1126,7 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   }
   CREATE_CUDA(cudaMalloc(&h->d_desc, desc.size() * sizeof(RealDesc)));
   CREATE_CUDA(cudaMemcpy(h->d_desc, desc.data(), desc.size() * sizeof(RealDesc), cudaMemcpyHostToDevice));
+  h->desc = desc;
   CREATE_CUDA(cudaMalloc(&h->d_status, sizeof(int)));
   CREATE_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
   // reduction tiles: bands of about 32k cells
@@ -1164,6 +1241,8 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
       return fail(h, SFT_ERR_ARG, "bad flow parameters (nu >= 0, cfl_safety > 0, finite)");
     if (!(p.atten_b0 >= 0.0) || !std::isfinite(p.atten_b0))
       return fail(h, SFT_ERR_ARG, "atten_b0 must be 0 (off) or a finite positive field");
+    if (!(p.nu_grid_alpha >= 0.0) || !std::isfinite(p.nu_grid_alpha))
+      return fail(h, SFT_ERR_ARG, "nu_grid_alpha must be 0 (constant nu) or finite positive");
   }
   // stale configurations refer to the old parameters
   SFT_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -30,7 +30,8 @@ struct RealDesc {
   int64_t off;     // element offset of row 0 in the state pool
   int64_t woff;    // element offset of row 0 in each work array
   int32_t nt, np, pitch, shape;
-  int32_t geo;     // first row of the shape's geometry table
+  int32_t geo;     // first row of the geometry table (the shape's, or the realization's own
+                   // with a grid-based diffusivity folded into cN, cS, cE)
   int32_t flow;    // first row of this realization's flow table
   int32_t col;     // first entry of the shape's cos/sin(phi_k) tables
   int32_t poff;    // element offset of this realization's polar-band scratch (fused RKL2)
@@ -79,6 +80,7 @@ struct StepParam {
   double eps_p;     // WENO eps in the phi sweep
   double alpha_uw;  // UW/CD factor
   double inv_b0;    // 1 / B_0 of Eq. (flow_attenuation); 0 = no attenuation
+  double cap_nu;    // nu at the cap faces relative to nudt: 1 (constant nu), nu_g(theta_1/2) (Eq. diffgrid)
   int32_t s;        // RKL2 stages (0 = no diffusion)
   int32_t coef;     // index of this realization's stage-0 coefficients
   int32_t weno;     // 1 = WENO3-CS(h), 0 = UW

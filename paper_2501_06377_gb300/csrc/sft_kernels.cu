@@ -199,7 +199,7 @@ rkl2_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
       if (stage > 2) d2 = double(Dout[po]);
       if (last) b0 = double(Bs[po]);
     }
-    const double Lp = shc[d.shape].pole_diff * block_sum(acc, sm);
+    const double Lp = shc[d.shape].pole_diff * p.cap_nu * block_sum(acc, sm);
     if (first) {
       const T g = T(double(nudt) * Lp);
       const T o = cf.mut * g;
@@ -784,7 +784,7 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
       const double gp = double(gG[(int64_t)(base + ip) * pitch]);
       double acc = 0.0;
       for (int k = threadIdx.x; k < np; k += blockDim.x) acc += double(cur[(int64_t)ia * pitch + k]) - yp;
-      const double Lp = shc[d.shape].pole_diff * block_sum(acc, sm);
+      const double Lp = shc[d.shape].pole_diff * p.cap_nu * block_sum(acc, sm);
       for (int i = i_lo; i <= i_hi; ++i) {
         const float* cr = cur + (int64_t)i * pitch;
         float* pr = prv + (int64_t)i * pitch;

@@ -46,7 +46,7 @@ class sft_flow_params(C.Structure):
                 ("nu", C.c_double), ("alpha_uw", C.c_double), ("cfl_safety", C.c_double),
                 ("eps_w", C.c_double), ("adv_space", C.c_int32), ("adv_time", C.c_int32),
                 ("diffusion", C.c_int32), ("advection", C.c_int32), ("atten_b0", C.c_double),
-                ("splitting", C.c_int32), ("reserved", C.c_int32)]
+                ("splitting", C.c_int32), ("reserved", C.c_int32), ("nu_grid_alpha", C.c_double)]
 
 
 class sft_assim_params(C.Structure):
@@ -164,13 +164,14 @@ class FlowParams:
     advection: bool = True
     atten_b0: float = 0.0   # Eq. (flow_attenuation) saturation field in G; 0 = off
     splitting: str = "lie"  # "lie" | "strang" (Sec. 3.5), the same for all realizations
+    nu_grid_alpha: float = 0.0  # > 0: grid-based nu of Eq. (diffgrid) (1/hour) instead of nu
 
     def to_c(self):
         return sft_flow_params(self.d0, self.d2, self.d4, self.m1, self.m3, self.m5, self.nu,
                                self.alpha_uw, self.cfl_safety, self.eps_w,
                                ADV_SPACE[self.adv_space], ADV_TIME[self.adv_time],
                                DIFFUSION[self.diffusion], 1 if self.advection else 0, self.atten_b0,
-                               SPLITTING[self.splitting], 0)
+                               SPLITTING[self.splitting], 0, self.nu_grid_alpha)
 
 
 @dataclass

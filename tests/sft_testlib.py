@@ -11,7 +11,7 @@ def oracle_params(fp: FlowParams) -> O.Params:
                     diffusion="rkl2" if fp.diffusion == "rkl2" else "off",
                     advection=fp.advection, alpha_uw=fp.alpha_uw, safety=fp.cfl_safety,
                     eps_w="h" if fp.eps_w <= 0 else fp.eps_w, atten_b0=fp.atten_b0,
-                    splitting=fp.splitting)
+                    splitting=fp.splitting, nu_grid_alpha=fp.nu_grid_alpha)
 
 
 def oracle_run(shape, fp, B0, t_target, max_steps=None):

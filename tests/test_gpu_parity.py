@@ -387,3 +387,31 @@ def test_strang_soccer_ball_rotation_matches_the_paper():
         g.step(672.0)
         hh = O.hh_metric(g.get_state(0), B0 * decay)
         assert hh == pytest.approx(4.8e-5, rel=0.1), (split, hh)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_grid_nu_smoother_matches_oracle(prec):
+    """Eq. (diffgrid) grid-based diffusivity (the map smoother, advection off)
+    beside constant-nu realizations in the same launches, incl. one with both
+    advection and grid-based nu."""
+    shapes = [(65, 128), (65, 128), (41, 96)]
+    draws = I.draw_realization_params(len(shapes), seed=14)
+    params = [params_from_draw(draws[0], advection=False, nu_grid_alpha=0.5),
+              params_from_draw(draws[1]),
+              params_from_draw(draws[2], nu_grid_alpha=2.0)]
+    g = Grid(shapes, prec)
+    maps = [I.initial_map(*s, seed=60 + r) for r, s in enumerate(shapes)]
+    for r, m in enumerate(maps):
+        g.set_state(r, m)
+    g.set_flows(params)
+    g.step(2.0)
+    for r, s in enumerate(shapes):
+        ref = oracle_run(s, params[r], maps[r], 2.0)
+        assert g.step_plan(r, 1.0)[1] == pytest.approx(ref.dt_euler, rel=1e-12)
+        assert rel_linf(g.get_state(r), ref.B) <= TOL[prec], (r, rel_linf(g.get_state(r), ref.B))
+    d = g.diagnostics()
+    assert abs(d[0]["flux_signed"] - O.total_flux(O.Grid(*shapes[0]), maps[0]) * O.R_SUN_CM ** 2) \
+        <= 1e-5 * d[0]["flux_pos"]
+    # back to constant nu for every realization: the shape geometry again
+    g.set_flows([params_from_draw(dd) for dd in draws])
+    g.step(3.0)
