@@ -561,6 +561,84 @@ def hh_metric(X, Y):
 
 
 # --------------------------------------------------------------------------
+# Sec. 2.4: random flux emergence (RFE)
+# --------------------------------------------------------------------------
+SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+
+
+def splitmix64_output(z):
+    """The SplitMix64 output function (Steele, Lea & Flood 2014) on uint64
+    array z (arithmetic mod 2^64)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def rfe_normals(g: Grid, seed, k):
+    """Standard normal draws Y of RFE map k (the N(0, 1) samples of Sec. 2.4),
+    one per unique cell (each pole cap is one cell; its row repeats it).
+    Counter-based: cell c of map k takes the SplitMix64 outputs of the states
+    seed + (2n+1) gamma and seed + (2n+2) gamma with n = k N_cells + c, as
+    uniforms u = (top 53 bits + 1/2) / 2^53, and Box-Muller
+    Y = sqrt(-2 ln u1) cos(2 pi u2)."""
+    nt, np_ = g.nt, g.np
+    ncell = (nt - 2) * np_ + 2
+    cid = np.empty((nt, np_), dtype=np.uint64)
+    cid[0, :] = 0
+    cid[1:-1, :] = 1 + np.arange((nt - 2) * np_, dtype=np.uint64).reshape(nt - 2, np_)
+    cid[-1, :] = ncell - 1
+    n = np.uint64(k) * np.uint64(ncell) + cid
+    gam = np.uint64(SPLITMIX_GAMMA)
+    with np.errstate(over="ignore"):
+        z1 = splitmix64_output(np.uint64(seed) + (np.uint64(2) * n + np.uint64(1)) * gam)
+        z2 = splitmix64_output(np.uint64(seed) + (np.uint64(2) * n + np.uint64(2)) * gam)
+    u1 = ((z1 >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    u2 = ((z2 >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def rfe_map(g: Grid, method, rate_mx_hr, seed, k):
+    """RFE source map k in G/hour: Eq. (rfe_m1) (method 1: uniform unsigned
+    flux per cell, divided by the cell's area) or Eq. (rfe_m2) (method 2:
+    uniform unsigned flux per unit area), flux balanced as Eq. (fluxbal)."""
+    Y = rfe_normals(g, seed, k)
+    r2 = R_SUN_CM ** 2
+    if method == 1:
+        ncell = (g.nt - 2) * g.np + 2
+        cell_area = g.area * r2                      # interior cells
+        cell_area[0, :] = g.cap_area * r2            # each cap is one cell
+        cell_area[-1, :] = g.cap_area * r2
+        S = rate_mx_hr / (cell_area * ncell) * math.sqrt(0.5 * math.pi) * Y
+    else:
+        S = rate_mx_hr / (4.0 * math.pi * r2) * math.sqrt(0.5 * math.pi) * Y
+    _, _, fp, fm = flux_balance_factors(g, S)
+    return np.where(S > 0.0, S * fp, S * fm)
+
+
+def rfe_weights(t0, tau, a, b):
+    """Maps and weights of the exact integral over [a, b] of Eq. (rfe_s),
+    S(t) = (1 - alpha) S_k + alpha S_{k+1}, alpha = (t - t_k) / tau on
+    t_k = t0 + k tau <= t <= t_{k+1} (tau = inf: S = S_0).  Returns
+    {k: weight (hours)}; the integral is sum_k weight_k S_k (linear in t:
+    each piece integrates exactly at its midpoint)."""
+    w = {}
+    if not math.isfinite(tau):
+        w[0] = b - a
+        return w
+    t = a
+    while t < b:
+        k = math.floor((t - t0) / tau + 1e-12)
+        end = min(b, t0 + (k + 1) * tau)
+        al = (0.5 * (t + end) - (t0 + k * tau)) / tau
+        w[k] = w.get(k, 0.0) + (end - t) * (1.0 - al)
+        w[k + 1] = w.get(k + 1, 0.0) + (end - t) * al
+        t = end
+    return w
+
+
+# --------------------------------------------------------------------------
 # Sec. 3.4 / 3.5: one realization's run (dt controller + Lie splitting)
 # --------------------------------------------------------------------------
 @dataclass
@@ -584,6 +662,11 @@ class Params:
     atten_b0: float = 0.0        # Eq. (flow_attenuation) saturation field (G); 0 = off
     splitting: str = "lie"       # "lie" (Eq. num_opsplit_nostrang) | "strang" (Eq. num_opsplit_strang)
     nu_grid_alpha: float = 0.0   # > 0: grid-based nu of Eq. (diffgrid) (1/hour) instead of nu
+    rfe_method: int = 0          # random flux emergence (Sec. 2.4): 0 off, 1 Eq. (rfe_m1), 2 Eq. (rfe_m2)
+    rfe_rate: float = 0.0        # total unsigned flux per hour, Mx/hour
+    rfe_lifetime: float = math.inf   # hours between source maps (tau of Eq. rfe_s)
+    rfe_seed: int = 0
+    rfe_t0: float = 0.0          # time of source map 0
 
 
 @dataclass
@@ -626,15 +709,30 @@ class Realization:
             return fe_diffusion_advance(B, dt, self.L, self.dt_euler)
         return B
 
+    def _S(self, B, a, b):
+        """The RFE source integrated over [a, b] (exactly, Eq. rfe_s)."""
+        p = self.p
+        if p.rfe_method == 0 or p.rfe_rate == 0.0:
+            return B
+        out = B.copy()
+        for k, w in sorted(rfe_weights(p.rfe_t0, p.rfe_lifetime, a, b).items()):
+            if w != 0.0:
+                out = out + w * rfe_map(self.g, p.rfe_method, p.rfe_rate, p.rfe_seed, k)
+        return out
+
     def lie_step(self, dt):
         """One time step (Sec. 3.5).  Eq. (num_opsplit_nostrang):
-        B* = A(B^n, dt), B** = D(B*, dt).  Eq. (num_opsplit_strang) with the
-        source S the identity (assimilation follows the advance):
-        B* = A(B^n, dt/2), B** = D(B*, dt), B^{n+1} = A(B**, dt/2)."""
+        B* = A(B^n, dt), B** = D(B*, dt), B^{n+1} = S(B**) with S the random
+        flux emergence source integrated over the step.  Eq.
+        (num_opsplit_strang): S over the first half step, A(dt/2), D(dt),
+        A(dt/2), S over the second half.  (Assimilation follows the advance.)"""
+        t = self.t
         if self.p.splitting == "strang":
-            self.B = self._A(self._D(self._A(self.B, 0.5 * dt), dt), 0.5 * dt)
+            B = self._S(self.B, t, t + 0.5 * dt)
+            B = self._A(self._D(self._A(B, 0.5 * dt), dt), 0.5 * dt)
+            self.B = self._S(B, t + 0.5 * dt, t + dt)
         else:
-            self.B = self._D(self._A(self.B, dt), dt)
+            self.B = self._S(self._D(self._A(self.B, dt), dt), t, t + dt)
 
     def flow_dt_limit(self):
         """The step the flow allows: its CFL limit, twice that with Strang
@@ -643,9 +741,13 @@ class Realization:
 
     def next_dt(self, t_target):
         """Sec. 3.4: start from the time remaining to the target (the next
-        output / assimilation time) and reduce it to the stable flow step."""
+        output / assimilation time) and reduce it to the stable flow step
+        (and, with RFE, to the source lifetime, so that a step spans at most
+        two source segments)."""
         remaining = t_target - self.t
         lim = self.flow_dt_limit()
+        if self.p.rfe_method != 0 and self.p.rfe_rate != 0.0:
+            lim = min(lim, self.p.rfe_lifetime)
         return remaining if remaining <= lim else lim
 
     def advance(self, t_target, max_steps=None):
