@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define SFT_ABI_VERSION 4
+#define SFT_ABI_VERSION 5
 
 typedef struct sft_grid* sft_handle;
 
@@ -109,6 +109,17 @@ typedef struct {
                            faces of the operator (1/hour; the map smoother of Sec. 2.2), in
                            place of nu; 0 = the constant nu */
 } sft_flow_params;
+
+/* Random flux emergence of a realization (Sec. 2.4). */
+typedef struct {
+  int32_t method;          /* 0 off, 1 Eq. (rfe_m1): uniform unsigned flux per cell, 2 Eq. (rfe_m2):
+                              uniform unsigned flux per unit area (the paper's default) */
+  int32_t reserved;        /* 0 */
+  double rate_mx_per_hour; /* total unsigned flux per hour of the source maps, Mx/hour, >= 0 */
+  double lifetime_hours;   /* tau of Eq. (rfe_s), the time between source maps; <= 0 or inf: one
+                              map for ever */
+  uint64_t seed;           /* of the counter-based normal draws */
+} sft_rfe_params;
 
 /* Assimilation weight and balance options (Sec. 2.3). */
 typedef struct {
@@ -302,6 +313,21 @@ sft_status sft_flux_diagnostics_noalloc(const void* br_device, int32_t ntheta, i
  * sft_create_grid or handle-free call when h is NULL).  Valid until the next
  * call on h. */
 const char* sft_last_error(sft_handle h);
+
+/*
+ * Random flux emergence (Sec. 2.4), params[r] per realization (NULL: off for
+ * all).  Source map k of a realization is Eq. (rfe_m1) or Eq. (rfe_m2) from
+ * standard normal draws (counter-based in seed, map and cell: the SplitMix64
+ * output function of two states per cell and Box-Muller; each polar cap is
+ * one cell), flux balanced as Eq. (fluxbal); map k belongs to time
+ * t0 + k tau with t0 the realization's time at this call, and Eq. (rfe_s)
+ * interpolates linearly between maps.  Every step adds the exact time
+ * integral of that source over the step: after the diffusion advance (Lie),
+ * or half before the first and half after the second advection advance
+ * (Strang).  A finite lifetime caps the time step at tau.  Nothing is stored
+ * per map: each step regenerates the (at most four) maps it needs.
+ */
+sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params);
 
 /* SFT_ABI_VERSION of the loaded library. */
 int32_t sft_abi_version(void);

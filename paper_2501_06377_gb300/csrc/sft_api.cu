@@ -59,6 +59,8 @@ struct RealInfo {
   double dt_cfl = 0.0;    // hours (inf when advection is off)
   double dt_euler = 0.0;  // hours (inf when nu == 0)
   double cap_nu = 1.0;    // nu at the cap faces relative to nudt (grid-based nu: nu_g(theta_1/2))
+  sft_rfe_params rfe{};   // random flux emergence (method 0: off)
+  double rfe_t0 = 0.0;    // time of source map 0
 };
 
 constexpr int kMaxChains = 2;   // concurrent launch chains of the fused RKL2 passes
@@ -126,6 +128,9 @@ struct sft_grid {
   RealDesc* d_desc = nullptr;
   std::vector<RealDesc> desc;  // host copy (geometry offsets change with grid-based nu)
   bool geo_custom = false;     // some realization has its own geometry block
+  bool any_rfe = false;        // random flux emergence on for some realization
+  RfeStep* d_rfe = nullptr;    // this step's maps and weights per realization
+  double* d_rfe_fac = nullptr; // Eq. (fluxbal) factors of the step's maps (8 per realization)
   ShapeConst* d_shc = nullptr;
   void* d_geo = nullptr;       // RowGeo<T>
   RowGeoD* d_geod = nullptr;
@@ -309,6 +314,33 @@ double euler_limit_grid(const ShapeInfo& s, double alpha) {
   return amax > 0.0 ? 1.0 / amax : INFINITY;
 }
 
+// Eq. (rfe_s) integrated over [a, b]: maps k (from t0, tau apart) and
+// weights (hours) such that the integral is sum_k w_k S_k (each piece of the
+// piecewise-linear source integrates exactly at its midpoint).  Returns the
+// first map index; w[0..3] for maps m0..m0+3 (a step spans at most two
+// segments because it is capped at tau).
+int64_t rfe_weights(double t0, double tau, double a, double b, double (&w)[4]) {
+  for (double& x : w) x = 0.0;
+  if (!std::isfinite(tau) || tau <= 0.0) {
+    w[0] = b - a;
+    return 0;
+  }
+  const int64_t m0 = (int64_t)std::floor((a - t0) / tau + 1e-12);
+  double t = a;
+  while (t < b) {
+    const int64_t k = (int64_t)std::floor((t - t0) / tau + 1e-12);
+    const double end = std::min(b, t0 + (double)(k + 1) * tau);
+    const double al = (0.5 * (t + end) - (t0 + (double)k * tau)) / tau;
+    const int64_t i = k - m0;
+    if (i >= 0 && i + 1 < 4) {
+      w[i] += (end - t) * (1.0 - al);
+      w[i + 1] += (end - t) * al;
+    }
+    t = end;
+  }
+  return m0;
+}
+
 // RKL2 stage count: smallest s >= 2 with dt <= dt_E (s^2 + s - 2) / 4.
 int rkl2_stages(double dt, double dte) {
   if (!(dt > 0.0)) return 0;
@@ -375,6 +407,8 @@ void free_handle(sft_handle h) {
   cudaFree(h->d_rtiles);
   cudaFree(h->d_rstart);
   cudaFree(h->d_partials);
+  cudaFree(h->d_rfe);
+  cudaFree(h->d_rfe_fac);
   cudaFree(h->d_red);
   if (h->h_red) cudaFreeHost(h->h_red);
   cudaFree(h->d_wpar);
@@ -609,6 +643,13 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
   T* W1 = ptr<T>(h->work[1]);
   T* W2 = ptr<T>(h->work[2]);
   const auto* geo = ptr<const RowGeo<T>>(h->d_geo);
+  if (h->any_rfe) {  // the step's source maps: Eq. (fluxbal) factors, then the first application
+    SFT_CUDA(h, launch_rfe_sums<T>(h->n_rtiles, st, h->d_rtiles, h->d_desc, h->d_geod, h->d_rfe, h->d_partials));
+    SFT_CUDA(h, launch_rfe_fold(h->n_real, st, h->d_rstart, h->d_partials, h->d_rfe_fac));
+    if (h->strang)
+      SFT_CUDA(h, launch_rfe_apply<T>(h->n_rtiles, st, h->d_rtiles, h->d_desc, h->d_geod, h->d_rfe, h->d_rfe_fac, 0,
+                                      B));
+  }
   if (record_events) SFT_CUDA(h, record(h->ev[0], st, capturing));
   {
     sft_status sa = enqueue_adv<T>(h, c, st);
@@ -661,6 +702,9 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
     if (sa != SFT_OK) return sa;
     if (record_events) SFT_CUDA(h, record(h->ev[5], st, capturing));
   }
+  if (h->any_rfe)  // Lie: the source after D; Strang: its second half
+    SFT_CUDA(h, launch_rfe_apply<T>(h->n_rtiles, st, h->d_rtiles, h->d_desc, h->d_geod, h->d_rfe, h->d_rfe_fac,
+                                    h->strang ? 1 : 0, B));
   return SFT_OK;
 }
 
@@ -687,7 +731,10 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     const double rem = t_target - ri.t;
     if (!(rem > 0.0)) continue;
     // Sec. 3.4: the remaining time, cut to the flow limit
-    const double lim = h->strang ? 2.0 * ri.dt_cfl : ri.dt_cfl;  // Strang: two dt/2 advances
+    double lim = h->strang ? 2.0 * ri.dt_cfl : ri.dt_cfl;  // Strang: two dt/2 advances
+    if (ri.rfe.method != 0 && ri.rfe.rate_mx_per_hour > 0.0 && std::isfinite(ri.rfe.lifetime_hours) &&
+        ri.rfe.lifetime_hours > 0.0)
+      lim = std::min(lim, ri.rfe.lifetime_hours);  // a step spans at most two source segments
     dt[i] = rem <= lim ? rem : lim;
     s[i] = ri.fp.diffusion == SFT_DIFF_RKL2 ? rkl2_stages(dt[i], ri.dt_euler) : 0;
     *any = true;
@@ -713,6 +760,37 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     if (st != SFT_OK) return st;
   }
   c->last_use = ++h->use_counter;
+  if (h->any_rfe) {  // this step's source maps and weights (read by the step's kernels)
+    std::vector<RfeStep> rs(h->n_real);
+    std::memset(rs.data(), 0, rs.size() * sizeof(RfeStep));
+    for (int i = 0; i < nw; ++i) {
+      const int r = w.reals[i];
+      const RealInfo& ri = h->reals[r];
+      if (!(dt[i] > 0.0) || ri.rfe.method == 0 || !(ri.rfe.rate_mx_per_hour > 0.0)) continue;
+      RfeStep& q = rs[r];
+      const ShapeInfo& sh = h->shapes[ri.shape];
+      const double ncell = (double)(sh.nt - 2) * sh.np + 2.0, r2 = kRsunCm * kRsunCm;
+      q.method = ri.rfe.method;
+      q.seed = ri.rfe.seed;
+      q.c = ri.rfe.rate_mx_per_hour * std::sqrt(0.5 * kPi) / (ri.rfe.method == 1 ? r2 * ncell : 4.0 * kPi * r2);
+      const double tau = ri.rfe.lifetime_hours, t = ri.t;
+      double wa[4], wb[4];
+      if (h->strang) {
+        const int64_t ma = rfe_weights(ri.rfe_t0, tau, t, t + 0.5 * dt[i], wa);
+        const int64_t mb = rfe_weights(ri.rfe_t0, tau, t + 0.5 * dt[i], t + dt[i], wb);
+        q.m0 = std::min(ma, mb);
+        for (int k = 0; k < 4; ++k) {
+          if (k + ma - q.m0 < 4) q.wa[k + ma - q.m0] = wa[k];
+          if (k + mb - q.m0 < 4) q.wb[k + mb - q.m0] = wb[k];
+        }
+      } else {
+        q.m0 = rfe_weights(ri.rfe_t0, tau, t, t + dt[i], wa);
+        for (int k = 0; k < 4; ++k) q.wa[k] = wa[k];
+      }
+    }
+    SFT_CUDA(h, cudaMemcpyAsync(h->d_rfe, rs.data(), rs.size() * sizeof(RfeStep), cudaMemcpyHostToDevice,
+                                h->stream));
+  }
   c->uses += 1;
   const bool ev = h->profiling;
   // A configuration used once (a shortened last step, a one-off member
@@ -1367,6 +1445,39 @@ sft_status sft_assimilate(sft_handle h, const void* br_obs, const void* mu, int3
                                      ptr<double>(h->state), aa, h->d_red));
   }
   if (!on_device) SFT_CUDA(h, cudaStreamSynchronize(h->stream));  // staging reused next call
+  return SFT_OK;
+}
+
+sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  SFT_CUDA(h, cudaSetDevice(h->device));
+  if (params) {
+    for (int r = 0; r < h->n_real; ++r) {
+      const sft_rfe_params& p = params[r];
+      if (p.method < 0 || p.method > 2) return fail(h, SFT_ERR_ARG, "rfe method must be 0, 1 or 2");
+      if (!(p.rate_mx_per_hour >= 0.0) || !std::isfinite(p.rate_mx_per_hour))
+        return fail(h, SFT_ERR_ARG, "rfe rate must be finite and >= 0");
+      if (std::isnan(p.lifetime_hours)) return fail(h, SFT_ERR_ARG, "rfe lifetime is NaN");
+    }
+  }
+  // the step graphs change shape: drop the cached configurations
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (auto& w : h->waves) {
+    for (auto& c : w.configs) free_config(*c, h->stream);
+    w.configs.clear();
+  }
+  bool any = false;
+  for (int r = 0; r < h->n_real; ++r) {
+    RealInfo& ri = h->reals[r];
+    ri.rfe = params ? params[r] : sft_rfe_params{};
+    ri.rfe_t0 = ri.t;
+    any = any || (ri.rfe.method != 0 && ri.rfe.rate_mx_per_hour > 0.0);
+  }
+  if (any && !h->d_rfe) {
+    SFT_CUDA(h, cudaMalloc(&h->d_rfe, (size_t)h->n_real * sizeof(RfeStep)));
+    SFT_CUDA(h, cudaMalloc(&h->d_rfe_fac, (size_t)h->n_real * 8 * sizeof(double)));
+  }
+  h->any_rfe = any;
   return SFT_OK;
 }
 

@@ -160,6 +160,21 @@ cudaError_t launch_fix_poles(int n_real, cudaStream_t st, const RealDesc* rd, T*
 // Reductions: one block per (realization, band of rows); partial results
 // per block; a second kernel folds them per realization in a fixed order.
 enum RedMode { RED_DIAG = 0, RED_ASSIM = 1, RED_BALANCE = 2 };
+
+// Random flux emergence of one step (Sec. 2.4), per realization: source maps
+// m0 .. m0+3 (the map indices of Eq. rfe_s) and their weights in hours, wa
+// for the step's first source application, wb for the second (Lie: one
+// application after D; Strang: one before the first and one after the second
+// advection).  c: Eq. (rfe_m2)'s G/hour per unit normal draw, or for Eq.
+// (rfe_m1) the same times the cell area (divided by it per cell).
+struct RfeStep {
+  int32_t method;   // 0 off (or idle this step), 1 Eq. rfe_m1, 2 Eq. rfe_m2
+  int32_t pad;
+  int64_t m0;
+  uint64_t seed;
+  double c;
+  double wa[4], wb[4];
+};
 constexpr int kDiagFields = 14;
 
 struct RedTile {
@@ -180,6 +195,14 @@ cudaError_t launch_reduce(int mode, int n_tiles, cudaStream_t st, const RedTile*
                           const RealDesc* rd, const RowGeoD* geod, const double* cosp,
                           const double* sinp, const T* state, double lat_cut, AssimArgs aa,
                           double* partials);
+template <typename T>
+cudaError_t launch_rfe_sums(int n_tiles, cudaStream_t st, const RedTile* tiles, const RealDesc* rd,
+                            const RowGeoD* geod, const RfeStep* rs, double* partials);
+cudaError_t launch_rfe_fold(int n_real, cudaStream_t st, const int* tile_start, const double* partials,
+                            double* fac);
+template <typename T>
+cudaError_t launch_rfe_apply(int n_tiles, cudaStream_t st, const RedTile* tiles, const RealDesc* rd,
+                             const RowGeoD* geod, const RfeStep* rs, const double* fac, int phase, T* state);
 cudaError_t launch_fold(int mode, int n_real, cudaStream_t st, const int* tile_start,
                         const double* partials, const double* wpar, double* out);
 template <typename T>

@@ -1140,6 +1140,137 @@ apply_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __rest
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Random flux emergence (Sec. 2.4).  Map m's normal draw of cell c is
+// counter-based (no stored maps): the SplitMix64 output function (Steele, Lea
+// & Flood 2014) of the states seed + (2n+1) gamma and seed + (2n+2) gamma,
+// n = m N_cells + c, as two uniforms, and Box-Muller.  FP64 grids draw in
+// FP64 (53-bit uniforms), FP32 grids in FP32 (24-bit uniforms).  Cell ids:
+// north cap 0, interior 1 + (j-1) np + k, south cap N_cells - 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix_output(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T> __device__ __forceinline__ T rfe_normal(uint64_t seed, uint64_t n);
+template <> __device__ __forceinline__ double rfe_normal<double>(uint64_t seed, uint64_t n) {
+  const uint64_t g = 0x9E3779B97F4A7C15ull;
+  const uint64_t z1 = splitmix_output(seed + (2 * n + 1) * g), z2 = splitmix_output(seed + (2 * n + 2) * g);
+  const double u1 = ((double)(z1 >> 11) + 0.5) * 0x1p-53, u2 = ((double)(z2 >> 11) + 0.5) * 0x1p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+template <> __device__ __forceinline__ float rfe_normal<float>(uint64_t seed, uint64_t n) {
+  const uint64_t g = 0x9E3779B97F4A7C15ull;
+  const uint64_t z1 = splitmix_output(seed + (2 * n + 1) * g), z2 = splitmix_output(seed + (2 * n + 2) * g);
+  const float u1 = ((float)(z1 >> 40) + 0.5f) * 0x1p-24f, u2 = ((float)(z2 >> 40) + 0.5f) * 0x1p-24f;
+  return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
+// FP64 positive / negative fluxes of the (unbalanced) maps m0..m0+3 that the
+// step uses: partials[tile][2m], [2m+1] (Eq. fluxbal needs them per map).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+rfe_sums_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+                const RowGeoD* __restrict__ geod, const RfeStep* __restrict__ rs, double* __restrict__ partials) {
+  __shared__ double sm[kThreads / 32];
+  const RedTile tl = tiles[blockIdx.x];
+  const RealDesc d = rd[tl.r];
+  const RfeStep R = rs[tl.r];
+  double acc[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) acc[f] = 0.0;
+  if (R.method != 0) {
+    const int64_t ncell = (int64_t)(d.nt - 2) * d.np + 2;
+    for (int j = tl.j0; j < tl.j1; ++j) {
+      const RowGeoD gd = geod[d.geo + j];
+      const bool pole = j == 0 || j == d.nt - 1;
+      const double cell_area = pole ? gd.area * d.np : gd.area;  // a cap is one cell
+      const double sc = R.method == 1 ? R.c / cell_area : R.c;
+      for (int k = threadIdx.x; k < (pole ? 1 : d.np); k += blockDim.x) {
+        const int64_t cell = pole ? (j == 0 ? 0 : ncell - 1) : 1 + (int64_t)(j - 1) * d.np + k;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          if (R.wa[m] == 0.0 && R.wb[m] == 0.0) continue;
+          const double S = sc * double(rfe_normal<T>(R.seed, (uint64_t)(R.m0 + m) * (uint64_t)ncell + cell));
+          if (S > 0.0) acc[2 * m] += cell_area * S;
+          else if (S < 0.0) acc[2 * m + 1] += cell_area * S;
+        }
+      }
+    }
+  }
+  double* out = partials + (int64_t)blockIdx.x * kDiagFields;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    const double t = block_sum(acc[f], sm);
+    if (threadIdx.x == 0) out[f] = t;
+  }
+}
+
+// One block per realization: fold the tiles' partials in a fixed order and
+// form Eq. (fluxbal)'s factors per map: fac[r][2m] for S > 0, [2m+1] for S <= 0.
+__global__ void rfe_fold_kernel(const int* __restrict__ tile_start, const double* __restrict__ partials,
+                                double* __restrict__ fac) {
+  __shared__ double sm[kThreads / 32];
+  const int r = blockIdx.x;
+  const int t0 = tile_start[r], t1 = tile_start[r + 1];
+  double v[8];
+  for (int f = 0; f < 8; ++f) {
+    double a = 0.0;
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) a += partials[(int64_t)t * kDiagFields + f];
+    v[f] = block_sum(a, sm);
+  }
+  if (threadIdx.x != 0) return;
+  for (int m = 0; m < 4; ++m) {
+    const double pp = v[2 * m], pm = v[2 * m + 1];
+    double fp = 1.0, fm = 1.0;
+    if (pp != 0.0 && pm != 0.0) {
+      const double ratio = fabs(pp / pm);
+      fp = 1.0 / sqrt(ratio);
+      fm = sqrt(ratio);
+    }
+    fac[8 * r + 2 * m] = fp;
+    fac[8 * r + 2 * m + 1] = fm;
+  }
+}
+
+// B += sum_m w_m S_m (balanced), phase 0 with wa, phase 1 with wb; the sum in
+// FP64, rounded once into the state.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+rfe_apply_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+                 const RowGeoD* __restrict__ geod, const RfeStep* __restrict__ rs, const double* __restrict__ fac,
+                 int phase, T* __restrict__ state) {
+  const RedTile tl = tiles[blockIdx.x];
+  const RfeStep R = rs[tl.r];
+  if (R.method == 0) return;
+  const RealDesc d = rd[tl.r];
+  const double* w = phase == 0 ? R.wa : R.wb;
+  const double* fr = fac + 8 * tl.r;
+  const int64_t ncell = (int64_t)(d.nt - 2) * d.np + 2;
+  T* b = state + d.off;
+  for (int j = tl.j0; j < tl.j1; ++j) {
+    const RowGeoD gd = geod[d.geo + j];
+    const bool pole = j == 0 || j == d.nt - 1;
+    const double cell_area = pole ? gd.area * d.np : gd.area;
+    const double sc = R.method == 1 ? R.c / cell_area : R.c;
+    T* row = b + (int64_t)j * d.pitch;
+    for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+      const int64_t cell = pole ? (j == 0 ? 0 : ncell - 1) : 1 + (int64_t)(j - 1) * d.np + k;
+      double add = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (w[m] == 0.0) continue;
+        const double S = sc * double(rfe_normal<T>(R.seed, (uint64_t)(R.m0 + m) * (uint64_t)ncell + cell));
+        add += w[m] * S * (S > 0.0 ? fr[2 * m] : fr[2 * m + 1]);
+      }
+      row[k] = T(double(row[k]) + add);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
@@ -1182,6 +1313,29 @@ cudaError_t launch_reduce(int mode, int n_tiles, cudaStream_t st, const RedTile*
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_rfe_sums(int n_tiles, cudaStream_t st, const RedTile* tiles, const RealDesc* rd,
+                            const RowGeoD* geod, const RfeStep* rs, double* partials) {
+  if (n_tiles <= 0) return cudaSuccess;
+  rfe_sums_kernel<T><<<n_tiles, kThreads, 0, st>>>(tiles, rd, geod, rs, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rfe_fold(int n_real, cudaStream_t st, const int* tile_start, const double* partials,
+                            double* fac) {
+  if (n_real <= 0) return cudaSuccess;
+  rfe_fold_kernel<<<n_real, kThreads, 0, st>>>(tile_start, partials, fac);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rfe_apply(int n_tiles, cudaStream_t st, const RedTile* tiles, const RealDesc* rd,
+                             const RowGeoD* geod, const RfeStep* rs, const double* fac, int phase, T* state) {
+  if (n_tiles <= 0) return cudaSuccess;
+  rfe_apply_kernel<T><<<n_tiles, kThreads, 0, st>>>(tiles, rd, geod, rs, fac, phase, state);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fold(int mode, int n_real, cudaStream_t st, const int* tile_start,
                         const double* partials, const double* wpar, double* out) {
   if (n_real <= 0) return cudaSuccess;
@@ -1210,7 +1364,11 @@ cudaError_t launch_apply(int mode, int n_tiles, cudaStream_t st, const RedTile* 
                                         const RowGeoD*, const double*, const double*, const T*,   \
                                         double, AssimArgs, double*);                              \
   template cudaError_t launch_apply<T>(int, int, cudaStream_t, const RedTile*, const RealDesc*,   \
-                                       const RowGeoD*, T*, AssimArgs, const double*);
+                                       const RowGeoD*, T*, AssimArgs, const double*);             \
+  template cudaError_t launch_rfe_sums<T>(int, cudaStream_t, const RedTile*, const RealDesc*,     \
+                                          const RowGeoD*, const RfeStep*, double*);              \
+  template cudaError_t launch_rfe_apply<T>(int, cudaStream_t, const RedTile*, const RealDesc*,    \
+                                           const RowGeoD*, const RfeStep*, const double*, int, T*);
 
 SFT_INSTANTIATE(float)
 SFT_INSTANTIATE(double)

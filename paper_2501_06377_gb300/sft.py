@@ -10,6 +10,7 @@ Maps may be numpy arrays (host) or torch tensors (host or CUDA), row-major
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import re
 from dataclasses import dataclass, fields
@@ -49,6 +50,11 @@ class sft_flow_params(C.Structure):
                 ("splitting", C.c_int32), ("reserved", C.c_int32), ("nu_grid_alpha", C.c_double)]
 
 
+class sft_rfe_params(C.Structure):
+    _fields_ = [("method", C.c_int32), ("reserved", C.c_int32), ("rate_mx_per_hour", C.c_double),
+                ("lifetime_hours", C.c_double), ("seed", C.c_uint64)]
+
+
 class sft_assim_params(C.Structure):
     _fields_ = [("alpha_mu", C.c_double), ("mu_lim", C.c_double), ("lat_lim_deg", C.c_double),
                 ("flux_balance", C.c_int32), ("reserved", C.c_int32)]
@@ -85,6 +91,7 @@ _SIGS = {
     "sft_assimilate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                  C.POINTER(sft_assim_params)]),
     "sft_balance_flux": (C.c_int, [C.c_void_p]),
+    "sft_set_rfe": (C.c_int, [C.c_void_p, C.POINTER(sft_rfe_params)]),
     "sft_flux_diagnostics": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(sft_diag)]),
     "sft_get_stats": (C.c_int, [C.c_void_p, C.POINTER(sft_stats)]),
     "sft_reset_stats": (C.c_int, [C.c_void_p]),
@@ -172,6 +179,18 @@ class FlowParams:
                                ADV_SPACE[self.adv_space], ADV_TIME[self.adv_time],
                                DIFFUSION[self.diffusion], 1 if self.advection else 0, self.atten_b0,
                                SPLITTING[self.splitting], 0, self.nu_grid_alpha)
+
+
+@dataclass
+class RfeParams:
+    """Python view of sft_rfe_params (Sec. 2.4 random flux emergence)."""
+    method: int = 2                 # 1: Eq. (rfe_m1), 2: Eq. (rfe_m2)
+    rate_mx_per_hour: float = 1e23  # total unsigned flux per hour
+    lifetime_hours: float = math.inf
+    seed: int = 0
+
+    def to_c(self):
+        return sft_rfe_params(self.method, 0, self.rate_mx_per_hour, self.lifetime_hours, self.seed)
 
 
 @dataclass
@@ -272,6 +291,18 @@ class Grid:
             params = [params] * self.n_real
         arr = (sft_flow_params * self.n_real)(*[p.to_c() for p in params])
         self._check(self.lib.sft_set_flows(self.h, arr))
+
+    def set_rfe(self, params):
+        """Random flux emergence per realization (a RfeParams, a list of
+        them with None for off, or None for off everywhere)."""
+        if params is None:
+            self._check(self.lib.sft_set_rfe(self.h, None))
+            return
+        if isinstance(params, RfeParams):
+            params = [params] * self.n_real
+        arr = (sft_rfe_params * self.n_real)(*[(p or RfeParams(method=0, rate_mx_per_hour=0.0)).to_c()
+                                               for p in params])
+        self._check(self.lib.sft_set_rfe(self.h, arr))
 
     def step(self, t_target, max_steps=0):
         n = C.c_int32(0)

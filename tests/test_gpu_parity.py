@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 import sft_inputs as I
 from paper_2501_06377_gb300 import build as B
-from paper_2501_06377_gb300.sft import AssimParams, FlowParams, Grid, SFTError
+from paper_2501_06377_gb300.sft import AssimParams, FlowParams, Grid, RfeParams, SFTError
 from tests.sft_testlib import oracle_params, oracle_run, params_from_draw, rel_linf
 
 pytestmark = pytest.mark.gpu
@@ -415,3 +415,56 @@ def test_grid_nu_smoother_matches_oracle(prec):
     # back to constant nu for every realization: the shape geometry again
     g.set_flows([params_from_draw(dd) for dd in draws])
     g.step(3.0)
+
+
+def _oracle_rfe(shape, fp, B0, rp, t_end):
+    p = oracle_params(fp)
+    if rp is not None:
+        p.rfe_method, p.rfe_rate, p.rfe_seed = rp.method, rp.rate_mx_per_hour, rp.seed
+        p.rfe_lifetime = rp.lifetime_hours if rp.lifetime_hours > 0 else math.inf
+    r = O.Realization(O.Grid(*shape), p, np.asarray(B0, dtype=np.float64))
+    r.advance(t_end)
+    return r
+
+
+@pytest.mark.parametrize("prec,split", [("fp64", "lie"), ("fp64", "strang"), ("fp32", "lie"), ("fp32", "strang")])
+def test_random_flux_emergence_matches_oracle(prec, split):
+    """Sec. 2.4 with flows and diffusion: method 2 with a 0.3 h lifetime (the
+    step is capped, maps change inside steps), method 1 with one map for ever,
+    and a realization without RFE, in the same launches."""
+    shapes = [(33, 64), (41, 96), (33, 64)]
+    draws = I.draw_realization_params(len(shapes), seed=16)
+    params = [params_from_draw(d, splitting=split) for d in draws]
+    rfes = [RfeParams(method=2, rate_mx_per_hour=1e23, lifetime_hours=0.3, seed=5),
+            RfeParams(method=1, rate_mx_per_hour=5e22, lifetime_hours=math.inf, seed=9), None]
+    g = Grid(shapes, prec)
+    maps = [I.initial_map(*s, seed=80 + r) for r, s in enumerate(shapes)]
+    for r, m in enumerate(maps):
+        g.set_state(r, m)
+    g.set_flows(params)
+    g.set_rfe(rfes)
+    g.step(1.0)
+    for r, s in enumerate(shapes):
+        ref = _oracle_rfe(s, params[r], maps[r], rfes[r], 1.0)
+        assert g.diagnostics()[r]["steps"] == ref.steps
+        assert rel_linf(g.get_state(r), ref.B) <= TOL[prec], (r, rel_linf(g.get_state(r), ref.B))
+
+
+def test_random_flux_emergence_realizes_the_rate():
+    """The paper's RFE check on the GPU: source only, from a zero map, one map
+    for ever: the unsigned flux grows at the requested rate, the net flux
+    stays zero; a 0.3 h lifetime grows far more slowly."""
+    shape = (129, 256)
+    out = {}
+    for life in (math.inf, 0.3):
+        g = Grid([shape], "fp64")
+        g.set_state(0, np.zeros(shape))
+        g.set_flows([FlowParams(advection=False, diffusion="off")])
+        g.set_rfe([RfeParams(method=2, rate_mx_per_hour=1e23, lifetime_hours=life, seed=3)])
+        g.step(10.0)
+        d = g.diagnostics()[0]
+        out[life] = d
+        assert abs(d["flux_signed"]) <= 1e-10 * d["flux_pos"]
+    unsigned = out[math.inf]["flux_pos"] - out[math.inf]["flux_neg"]
+    assert unsigned == pytest.approx(10.0 * 1e23, rel=0.02)
+    assert out[0.3]["flux_pos"] - out[0.3]["flux_neg"] < 0.3 * unsigned
