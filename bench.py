@@ -262,6 +262,10 @@ def run_gpu(args, rank, world, local_rank):
         g.set_state(r, maps[r % len(maps)])
     g.balance_flux()
     g.set_flows(params)
+    if args.rfe_rate > 0.0:
+        from paper_2501_06377_gb300.sft import RfeParams
+        g.set_rfe([RfeParams(method=2, rate_mx_per_hour=args.rfe_rate, lifetime_hours=args.rfe_lifetime,
+                             seed=7 + r) for r in range(nreal)])
     cells_per_step = float(nreal * NT * NP)
 
     def one_step():
@@ -347,6 +351,8 @@ def run_gpu(args, rank, world, local_rank):
                        "rkl2_stages_per_step": st["diff_cell_stages"] / max(st["cell_updates"], 1),
                        "graph": True, "rkl2_stages_per_launch": g.get_fusion(),
                        "flow_attenuation_b0": args.atten_b0, "splitting": args.splitting,
+                       "rfe": ({"method": 2, "rate_mx_per_hour": args.rfe_rate, "lifetime_hours": args.rfe_lifetime}
+                               if args.rfe_rate > 0.0 else None),
                        "realization_hours_per_s": sim_hours * world / (ms * 1e-3),
                        "ms_per_step_split": {"rkl2": st["diff_ms"] / args.steps,
                                              "advection": st["adv_ms"] / args.steps,
@@ -532,6 +538,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--splitting", default="lie", choices=["lie", "strang"],
                     help="operator splitting of a step (Sec. 3.5)")
+    ap.add_argument("--rfe-rate", type=float, default=0.0,
+                    help="random flux emergence (Sec. 2.4, method 2): unsigned Mx per hour; 0 = off")
+    ap.add_argument("--rfe-lifetime", type=float, default=24.0, help="hours between RFE source maps")
     ap.add_argument("--atten-b0", type=float, default=0.0,
                     help="flow attenuation saturation field in G (Eq. flow_attenuation); 0 = off")
     ap.add_argument("--surrogate", action="store_true",

@@ -61,6 +61,7 @@ struct RealInfo {
   double cap_nu = 1.0;    // nu at the cap faces relative to nudt (grid-based nu: nu_g(theta_1/2))
   sft_rfe_params rfe{};   // random flux emergence (method 0: off)
   double rfe_t0 = 0.0;    // time of source map 0
+  int64_t rfe_m0 = -1;    // map window whose balance factors are on the device (-1: none)
 };
 
 constexpr int kMaxChains = 2;   // concurrent launch chains of the fused RKL2 passes
@@ -645,7 +646,7 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
   const auto* geo = ptr<const RowGeo<T>>(h->d_geo);
   if (h->any_rfe) {  // the step's source maps: Eq. (fluxbal) factors, then the first application
     SFT_CUDA(h, launch_rfe_sums<T>(h->n_rtiles, st, h->d_rtiles, h->d_desc, h->d_geod, h->d_rfe, h->d_partials));
-    SFT_CUDA(h, launch_rfe_fold(h->n_real, st, h->d_rstart, h->d_partials, h->d_rfe_fac));
+    SFT_CUDA(h, launch_rfe_fold(h->n_real, st, h->d_rstart, h->d_rfe, h->d_partials, h->d_rfe_fac));
     if (h->strang)
       SFT_CUDA(h, launch_rfe_apply<T>(h->n_rtiles, st, h->d_rtiles, h->d_desc, h->d_geod, h->d_rfe, h->d_rfe_fac, 0,
                                       B));
@@ -787,6 +788,8 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
         q.m0 = rfe_weights(ri.rfe_t0, tau, t, t + dt[i], wa);
         for (int k = 0; k < 4; ++k) q.wa[k] = wa[k];
       }
+      q.fresh = ri.rfe_m0 != q.m0 ? 1 : 0;  // the factors of a kept window stay valid
+      h->reals[r].rfe_m0 = q.m0;
     }
     SFT_CUDA(h, cudaMemcpyAsync(h->d_rfe, rs.data(), rs.size() * sizeof(RfeStep), cudaMemcpyHostToDevice,
                                 h->stream));
@@ -1471,6 +1474,7 @@ sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params) {
     RealInfo& ri = h->reals[r];
     ri.rfe = params ? params[r] : sft_rfe_params{};
     ri.rfe_t0 = ri.t;
+    ri.rfe_m0 = -1;
     any = any || (ri.rfe.method != 0 && ri.rfe.rate_mx_per_hour > 0.0);
   }
   if (any && !h->d_rfe) {

@@ -169,7 +169,7 @@ enum RedMode { RED_DIAG = 0, RED_ASSIM = 1, RED_BALANCE = 2 };
 // (rfe_m1) the same times the cell area (divided by it per cell).
 struct RfeStep {
   int32_t method;   // 0 off (or idle this step), 1 Eq. rfe_m1, 2 Eq. rfe_m2
-  int32_t pad;
+  int32_t fresh;    // 1: (re)compute the Eq. (fluxbal) factors of maps m0..m0+3 this step
   int64_t m0;
   uint64_t seed;
   double c;
@@ -198,8 +198,8 @@ cudaError_t launch_reduce(int mode, int n_tiles, cudaStream_t st, const RedTile*
 template <typename T>
 cudaError_t launch_rfe_sums(int n_tiles, cudaStream_t st, const RedTile* tiles, const RealDesc* rd,
                             const RowGeoD* geod, const RfeStep* rs, double* partials);
-cudaError_t launch_rfe_fold(int n_real, cudaStream_t st, const int* tile_start, const double* partials,
-                            double* fac);
+cudaError_t launch_rfe_fold(int n_real, cudaStream_t st, const int* tile_start, const RfeStep* rs,
+                            const double* partials, double* fac);
 template <typename T>
 cudaError_t launch_rfe_apply(int n_tiles, cudaStream_t st, const RedTile* tiles, const RealDesc* rd,
                              const RowGeoD* geod, const RfeStep* rs, const double* fac, int phase, T* state);

@@ -1169,8 +1169,9 @@ template <> __device__ __forceinline__ float rfe_normal<float>(uint64_t seed, ui
   return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
 }
 
-// FP64 positive / negative fluxes of the (unbalanced) maps m0..m0+3 that the
-// step uses: partials[tile][2m], [2m+1] (Eq. fluxbal needs them per map).
+// FP64 positive / negative fluxes of the (unbalanced) maps m0..m0+3 of a
+// realization whose window is new this step: partials[tile][2m], [2m+1]
+// (Eq. fluxbal needs them per map; the factors are kept while the window is).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 rfe_sums_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__ rd,
@@ -1182,7 +1183,7 @@ rfe_sums_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__ 
   double acc[8];
 #pragma unroll
   for (int f = 0; f < 8; ++f) acc[f] = 0.0;
-  if (R.method != 0) {
+  if (R.method != 0 && R.fresh) {
     const int64_t ncell = (int64_t)(d.nt - 2) * d.np + 2;
     for (int j = tl.j0; j < tl.j1; ++j) {
       const RowGeoD gd = geod[d.geo + j];
@@ -1193,7 +1194,6 @@ rfe_sums_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__ 
         const int64_t cell = pole ? (j == 0 ? 0 : ncell - 1) : 1 + (int64_t)(j - 1) * d.np + k;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          if (R.wa[m] == 0.0 && R.wb[m] == 0.0) continue;
           const double S = sc * double(rfe_normal<T>(R.seed, (uint64_t)(R.m0 + m) * (uint64_t)ncell + cell));
           if (S > 0.0) acc[2 * m] += cell_area * S;
           else if (S < 0.0) acc[2 * m + 1] += cell_area * S;
@@ -1211,10 +1211,11 @@ rfe_sums_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__ 
 
 // One block per realization: fold the tiles' partials in a fixed order and
 // form Eq. (fluxbal)'s factors per map: fac[r][2m] for S > 0, [2m+1] for S <= 0.
-__global__ void rfe_fold_kernel(const int* __restrict__ tile_start, const double* __restrict__ partials,
-                                double* __restrict__ fac) {
+__global__ void rfe_fold_kernel(const int* __restrict__ tile_start, const RfeStep* __restrict__ rs,
+                                const double* __restrict__ partials, double* __restrict__ fac) {
   __shared__ double sm[kThreads / 32];
   const int r = blockIdx.x;
+  if (rs[r].method == 0 || !rs[r].fresh) return;  // uniform over the block
   const int t0 = tile_start[r], t1 = tile_start[r + 1];
   double v[8];
   for (int f = 0; f < 8; ++f) {
@@ -1236,8 +1237,9 @@ __global__ void rfe_fold_kernel(const int* __restrict__ tile_start, const double
   }
 }
 
-// B += sum_m w_m S_m (balanced), phase 0 with wa, phase 1 with wb; the sum in
-// FP64, rounded once into the state.
+// B += sum_m w_m S_m (balanced), phase 0 with wa, phase 1 with wb, in the
+// state's precision: per map the weight times the Eq. (fluxbal) factor of
+// each sign (S has the sign of its draw), per row the map scale.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 rfe_apply_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__ rd,
@@ -1249,24 +1251,30 @@ rfe_apply_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__
   const RealDesc d = rd[tl.r];
   const double* w = phase == 0 ? R.wa : R.wb;
   const double* fr = fac + 8 * tl.r;
+  T wp[4], wn[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    wp[m] = T(w[m] * fr[2 * m]);
+    wn[m] = T(w[m] * fr[2 * m + 1]);
+  }
   const int64_t ncell = (int64_t)(d.nt - 2) * d.np + 2;
   T* b = state + d.off;
   for (int j = tl.j0; j < tl.j1; ++j) {
     const RowGeoD gd = geod[d.geo + j];
     const bool pole = j == 0 || j == d.nt - 1;
     const double cell_area = pole ? gd.area * d.np : gd.area;
-    const double sc = R.method == 1 ? R.c / cell_area : R.c;
+    const T sc = T(R.method == 1 ? R.c / cell_area : R.c);
     T* row = b + (int64_t)j * d.pitch;
     for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
       const int64_t cell = pole ? (j == 0 ? 0 : ncell - 1) : 1 + (int64_t)(j - 1) * d.np + k;
-      double add = 0.0;
+      T add = T(0);
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         if (w[m] == 0.0) continue;
-        const double S = sc * double(rfe_normal<T>(R.seed, (uint64_t)(R.m0 + m) * (uint64_t)ncell + cell));
-        add += w[m] * S * (S > 0.0 ? fr[2 * m] : fr[2 * m + 1]);
+        const T y = rfe_normal<T>(R.seed, (uint64_t)(R.m0 + m) * (uint64_t)ncell + cell);
+        add += sc * y * (y > T(0) ? wp[m] : wn[m]);
       }
-      row[k] = T(double(row[k]) + add);
+      row[k] += add;
     }
   }
 }
@@ -1321,10 +1329,10 @@ cudaError_t launch_rfe_sums(int n_tiles, cudaStream_t st, const RedTile* tiles, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rfe_fold(int n_real, cudaStream_t st, const int* tile_start, const double* partials,
-                            double* fac) {
+cudaError_t launch_rfe_fold(int n_real, cudaStream_t st, const int* tile_start, const RfeStep* rs,
+                            const double* partials, double* fac) {
   if (n_real <= 0) return cudaSuccess;
-  rfe_fold_kernel<<<n_real, kThreads, 0, st>>>(tile_start, partials, fac);
+  rfe_fold_kernel<<<n_real, kThreads, 0, st>>>(tile_start, rs, partials, fac);
   return cudaGetLastError();
 }
 
