@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define SFT_ABI_VERSION 5
+#define SFT_ABI_VERSION 6
 
 typedef struct sft_grid* sft_handle;
 
@@ -114,11 +114,13 @@ typedef struct {
 typedef struct {
   int32_t method;          /* 0 off, 1 Eq. (rfe_m1): uniform unsigned flux per cell, 2 Eq. (rfe_m2):
                               uniform unsigned flux per unit area (the paper's default) */
-  int32_t reserved;        /* 0 */
+  int32_t origin_given;    /* 0: source map 0 belongs to the realization's time at sft_set_rfe;
+                              1: to origin_hours (resuming a run from a checkpoint) */
   double rate_mx_per_hour; /* total unsigned flux per hour of the source maps, Mx/hour, >= 0 */
   double lifetime_hours;   /* tau of Eq. (rfe_s), the time between source maps; <= 0 or inf: one
                               map for ever */
   uint64_t seed;           /* of the counter-based normal draws */
+  double origin_hours;     /* t0 when origin_given = 1 */
 } sft_rfe_params;
 
 /* Assimilation weight and balance options (Sec. 2.3). */
@@ -320,12 +322,15 @@ const char* sft_last_error(sft_handle h);
  * standard normal draws (counter-based in seed, map and cell: the SplitMix64
  * output function of two states per cell and Box-Muller; each polar cap is
  * one cell), flux balanced as Eq. (fluxbal); map k belongs to time
- * t0 + k tau with t0 the realization's time at this call, and Eq. (rfe_s)
+ * t0 + k tau with t0 the realization's time at this call (or origin_hours),
+ * and Eq. (rfe_s)
  * interpolates linearly between maps.  Every step adds the exact time
  * integral of that source over the step: after the diffusion advance (Lie),
  * or half before the first and half after the second advection advance
  * (Strang).  A finite lifetime caps the time step at tau.  Nothing is stored
- * per map: each step regenerates the (at most four) maps it needs.
+ * per map: each step regenerates the (at most four) maps it needs, so a run
+ * resumed from a checkpoint (state, time, and these parameters with the
+ * original origin) continues bit for bit.
  */
 sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params);
 

@@ -20,6 +20,7 @@
 
 #include "sfs.h"
 #include "sfs_fused.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 namespace sft {
 void set_global_error(const std::string& msg);
@@ -1080,6 +1081,10 @@ sft_status sfs_get_params(sfs_handle h, float* host_params) {
 }
 
 sft_status sfs_forward(sfs_handle h, const float* x, const float* p, int32_t n, float* y) {
+  nvtxRangePushA("sfs_forward");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   sft_status st = check_batch(h, x, p, n);
   if (st != SFT_OK) return st;
   if (!y) return fail("NULL output", SFT_ERR_ARG);
@@ -1107,6 +1112,10 @@ sft_status sfs_loss_grad(sfs_handle h, const float* x, const float* p, const flo
 
 sft_status sfs_train_step(sfs_handle h, const float* x, const float* p, const float* y, int32_t n, double lr,
                           double wd, float* loss) {
+  nvtxRangePushA("sfs_train_step");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   sft_status st = check_batch(h, x, p, n);
   if (st != SFT_OK) return st;
   if (!y) return fail("NULL argument", SFT_ERR_ARG);

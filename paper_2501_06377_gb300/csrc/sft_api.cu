@@ -23,6 +23,7 @@
 
 #include "sft.h"
 #include "sft_device.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace sft;
 
@@ -167,6 +168,13 @@ struct sft_grid {
 };
 
 namespace {
+
+// An NVTX range for the duration of a public call (a timeline marker for
+// profilers; no cost without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 sft_status fail(sft_handle h, sft_status code, const std::string& msg) {
   if (h) h->err = msg;
@@ -1340,6 +1348,7 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
 }
 
 sft_status sft_step(sft_handle h, double t_target_hours, int32_t max_steps, int32_t* steps_taken) {
+  NvtxRange nvtx("sft_step");
   if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
   if (steps_taken) *steps_taken = 0;
   if (!h->flows_set) return fail(h, SFT_ERR_STATE, "sft_set_flows must come before sft_step");
@@ -1369,6 +1378,7 @@ sft_status sft_step(sft_handle h, double t_target_hours, int32_t max_steps, int3
 
 sft_status sft_assimilate(sft_handle h, const void* br_obs, const void* mu, int32_t obs_per_realization,
                           int32_t on_device, const sft_assim_params* params) {
+  NvtxRange nvtx("sft_assimilate");
   if (!h || !br_obs || !mu || !params) return fail(h, SFT_ERR_ARG, "NULL argument");
   SFT_CUDA(h, cudaSetDevice(h->device));
   std::vector<int64_t> off(h->n_real, 0);
@@ -1461,6 +1471,7 @@ sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params) {
       if (!(p.rate_mx_per_hour >= 0.0) || !std::isfinite(p.rate_mx_per_hour))
         return fail(h, SFT_ERR_ARG, "rfe rate must be finite and >= 0");
       if (std::isnan(p.lifetime_hours)) return fail(h, SFT_ERR_ARG, "rfe lifetime is NaN");
+      if (p.origin_given && !std::isfinite(p.origin_hours)) return fail(h, SFT_ERR_ARG, "rfe origin must be finite");
     }
   }
   // the step graphs change shape: drop the cached configurations
@@ -1473,7 +1484,7 @@ sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params) {
   for (int r = 0; r < h->n_real; ++r) {
     RealInfo& ri = h->reals[r];
     ri.rfe = params ? params[r] : sft_rfe_params{};
-    ri.rfe_t0 = ri.t;
+    ri.rfe_t0 = ri.rfe.origin_given ? ri.rfe.origin_hours : ri.t;
     ri.rfe_m0 = -1;
     any = any || (ri.rfe.method != 0 && ri.rfe.rate_mx_per_hour > 0.0);
   }
@@ -1505,6 +1516,7 @@ sft_status sft_balance_flux(sft_handle h) {
 }
 
 sft_status sft_flux_diagnostics(sft_handle h, double lat_cut_deg, sft_diag* out) {
+  NvtxRange nvtx("sft_flux_diagnostics");
   if (!h || !out) return fail(h, SFT_ERR_ARG, "NULL argument");
   SFT_CUDA(h, cudaSetDevice(h->device));
   AssimArgs aa{nullptr, nullptr, nullptr, nullptr};

@@ -51,8 +51,8 @@ class sft_flow_params(C.Structure):
 
 
 class sft_rfe_params(C.Structure):
-    _fields_ = [("method", C.c_int32), ("reserved", C.c_int32), ("rate_mx_per_hour", C.c_double),
-                ("lifetime_hours", C.c_double), ("seed", C.c_uint64)]
+    _fields_ = [("method", C.c_int32), ("origin_given", C.c_int32), ("rate_mx_per_hour", C.c_double),
+                ("lifetime_hours", C.c_double), ("seed", C.c_uint64), ("origin_hours", C.c_double)]
 
 
 class sft_assim_params(C.Structure):
@@ -188,9 +188,12 @@ class RfeParams:
     rate_mx_per_hour: float = 1e23  # total unsigned flux per hour
     lifetime_hours: float = math.inf
     seed: int = 0
+    origin_hours: float = None      # None: the realization's time at set_rfe
 
     def to_c(self):
-        return sft_rfe_params(self.method, 0, self.rate_mx_per_hour, self.lifetime_hours, self.seed)
+        given = self.origin_hours is not None
+        return sft_rfe_params(self.method, 1 if given else 0, self.rate_mx_per_hour, self.lifetime_hours,
+                              self.seed, float(self.origin_hours) if given else 0.0)
 
 
 @dataclass

@@ -27,7 +27,7 @@ def test_binding_covers_the_header(lib):
 
 
 def test_abi_version(lib):
-    assert lib.sft_abi_version() == 5
+    assert lib.sft_abi_version() == 6
 
 
 def test_create_rejects_bad_arguments_before_any_cuda_call(lib):

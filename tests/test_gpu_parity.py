@@ -468,3 +468,38 @@ def test_random_flux_emergence_realizes_the_rate():
     unsigned = out[math.inf]["flux_pos"] - out[math.inf]["flux_neg"]
     assert unsigned == pytest.approx(10.0 * 1e23, rel=0.02)
     assert out[0.3]["flux_pos"] - out[0.3]["flux_neg"] < 0.3 * unsigned
+
+
+def test_checkpoint_resume_with_rfe_is_bitwise():
+    """Random flux emergence is counter-based: a run resumed from a checkpoint
+    (state, time, and the RFE parameters with the original origin) continues
+    bit for bit, map changes inside steps included."""
+    shapes = [(33, 64), (33, 64)]
+    rfe = [RfeParams(method=2, rate_mx_per_hour=1e23, lifetime_hours=0.7, seed=4, origin_hours=0.0),
+           RfeParams(method=1, rate_mx_per_hour=3e22, lifetime_hours=2.5, seed=8, origin_hours=0.0)]
+    g, params, maps = _batch(shapes, "fp32", seed=23)
+    g.set_rfe(rfe)
+    assert g.step(500.0, max_steps=6) == 6
+    full = [g.get_state(r) for r in range(2)]
+    g2, _, _ = _batch(shapes, "fp32", seed=23)
+    g2.set_rfe(rfe)
+    assert g2.step(500.0, max_steps=2) == 2
+    saved = [g2.get_state(r) for r in range(2)]
+    t = g2.get_time()
+    g3 = Grid(shapes, "fp32")
+    for r in range(2):
+        g3.set_state(r, saved[r])
+    g3.set_flows(params)
+    g3.set_time(t)
+    g3.set_rfe(rfe)   # origin 0, not the resume time
+    assert g3.step(500.0, max_steps=4) == 4
+    for r in range(2):
+        np.testing.assert_array_equal(g3.get_state(r), full[r])
+
+
+def test_state_larger_than_the_hbm_budget_is_refused():
+    """Admission by HBM footprint: a budget below the resident state fails at
+    creation with SFT_ERR_OOM (no kernel runs)."""
+    with pytest.raises(SFTError) as e:
+        Grid([(257, 512)] * 4, "fp32", hbm_budget=1 << 20)
+    assert "OOM" in str(e.value) or "budget" in str(e.value).lower()
