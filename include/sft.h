@@ -13,8 +13,11 @@
  *   - diffusion with the 5-point operator of Eq. (diffusion_op) advanced by
  *     RKL2 super time stepping (Sec. 3.7.2);
  *   - finite-volume polar caps (App. A) and a periodic phi boundary;
- *   - Lie operator splitting A then D (Eq. num_opsplit_nostrang) with the
- *     time-step controller of Sec. 3.4;
+ *   - Lie operator splitting A then D (Eq. num_opsplit_nostrang) or Strang
+ *     splitting (Eq. num_opsplit_strang) with the time-step controller of
+ *     Sec. 3.4;
+ *   - optional flow attenuation (Eq. flow_attenuation), grid-based
+ *     diffusivity (Eq. diffgrid) and random flux emergence (Sec. 2.4);
  *   - the weighted, optionally flux-balanced assimilation blend of Sec. 2.3
  *     (Eq. data_assim, data_assim_f, data_assim_deltab, fluxbal);
  *   - the analysis quantities of Sec. 2.6.
@@ -31,9 +34,15 @@
  *   - Pointers flagged on_device = 1 are CUDA device pointers of the current
  *     device; on_device = 0 means host memory.  The library copies caller
  *     arrays and never retains a caller pointer.
- *   - The handle owns all device memory it uses (cudaMalloc at
- *     sft_create_grid, cudaFree at sft_destroy); no call allocates after
- *     sft_create_grid except the graph/coefficient caches of sft_step.
+ *   - The handle owns all device memory it uses (allocated by
+ *     sft_create_grid, freed by sft_destroy).  After sft_create_grid only
+ *     these allocate: sft_step (its cached step configurations and graphs),
+ *     sft_set_flows (a larger geometry table for grid-based diffusivity),
+ *     sft_set_rfe (its per-realization buffers, once) and sft_assimilate
+ *     (its observation buffer, when it grows).  A failed allocation returns
+ *     SFT_ERR_OOM and frees what the call had allocated; the call can be
+ *     repeated (after a failed sft_set_flows, sft_step waits for one that
+ *     succeeds).
  *   - Work is queued on the handle's CUDA stream.  sft_get_state (host
  *     destination), sft_flux_diagnostics, sft_get_stats and sft_step with
  *     profiling on synchronise that stream; the other calls are asynchronous.
@@ -53,7 +62,7 @@
 extern "C" {
 #endif
 
-#define SFT_ABI_VERSION 6
+#define SFT_ABI_VERSION 7
 
 typedef struct sft_grid* sft_handle;
 
@@ -333,6 +342,37 @@ const char* sft_last_error(sft_handle h);
  * original origin) continues bit for bit.
  */
 sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params);
+
+/* ---- Debug build and host fault injection ------------------------------
+ * The library built with -DSFT_DEBUG (libsft_debug.so) checks, inside the
+ * stepping and reduction kernels, every index a kernel derives from its
+ * tile and realization descriptor (row, first column, first and last row
+ * of a fused band, rows of a reduction tile) against the range that keeps
+ * all its accesses inside the realization.  A failed check records the
+ * check site and the offending value on the device and clamps or skips the
+ * access; nothing traps.  The release build compiles the checks away, and
+ * both builds check the host-built descriptor and tile tables whenever
+ * they are built (SFT_ERR_STATE on an inconsistency, before any launch).
+ */
+
+/* Reads the device record: *first_failure = (site << 48) | (value mod 2^48)
+ * of the first failed check, 0 when none; *failures = number of failed
+ * checks (either pointer may be NULL).  reset != 0 clears the record.
+ * Synchronises the device.  SFT_ERR_STATE in a release build. */
+sft_status sft_debug_checks(uint64_t* first_failure, uint32_t* failures, int32_t reset);
+
+/* Runs one check on the device, value against [lo, hi], with no memory
+ * access: a self-test of the record path (site 1..65535, lo <= hi).
+ * Synchronises the device.  SFT_ERR_STATE in a release build. */
+sft_status sft_debug_probe(int32_t site, int64_t value, int64_t lo, int64_t hi);
+
+/* Host fault injection, in every build: the nth device or pinned allocation
+ * made by an sft_* call from now on (1 = the next) reports an allocation
+ * failure without allocating; the call that makes it returns SFT_ERR_OOM
+ * and frees what it had allocated, and the same call made again succeeds
+ * (sft_step after a failed sft_set_flows waits for a successful one).
+ * 0 disarms.  Process-wide. */
+sft_status sft_debug_fail_alloc(int32_t nth);
 
 /* SFT_ABI_VERSION of the loaded library. */
 int32_t sft_abi_version(void);

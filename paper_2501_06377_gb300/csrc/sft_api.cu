@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -180,6 +181,33 @@ sft_status fail(sft_handle h, sft_status code, const std::string& msg) {
   if (h) h->err = msg;
   else g_create_error = msg;
   return code;
+}
+
+// Host fault injection (sft_debug_fail_alloc): armed with n, the n-th device
+// or pinned allocation made by an sft_* call from then on reports
+// cudaErrorMemoryAllocation without allocating, then the injector disarms.
+std::atomic<int> g_fail_alloc{0};
+
+bool injected_alloc_failure() {
+  int n = g_fail_alloc.load();
+  while (n > 0)
+    if (g_fail_alloc.compare_exchange_weak(n, n - 1)) return n == 1;
+  return false;
+}
+
+template <typename P> cudaError_t dev_malloc(P** p, size_t bytes) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+template <typename P> cudaError_t dev_malloc_async(P** p, size_t bytes, cudaStream_t st) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st);
+}
+
+template <typename P> cudaError_t host_malloc(P** p, size_t bytes) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
 }
 
 #define SFT_CUDA(h, call)                                                              \
@@ -454,6 +482,58 @@ sft_status sync(sft_handle h) {
 // ---------------------------------------------------------------------------
 int vec_width(const sft_grid* h) { return h->prec == SFT_FP32 ? 4 : 2; }
 
+// Consistency of the host-built tables the kernels index by.  Every
+// realization's rows lie inside the state pool, the work arrays, the cap
+// scratch and the geometry, flow and longitude tables, and the state extents
+// are disjoint; every tile names a realization and starts inside it.  Run
+// whenever the tables are (re)built; a failure is an internal error reported
+// as SFT_ERR_STATE before anything is launched.  Returns "" when consistent.
+std::string check_desc(const sft_grid* h) {
+  if ((int)h->desc.size() != h->n_real) return "descriptor count";
+  std::vector<std::pair<int64_t, int64_t>> ext;
+  for (int r = 0; r < h->n_real; ++r) {
+    const RealDesc& d = h->desc[r];
+    const std::string at = " (realization " + std::to_string(r) + ")";
+    if (d.nt < 5 || d.np < 8 || d.pitch < (int)round_up(d.np, 4) || d.pitch % 4 != 0) return "shape" + at;
+    const int64_t cells = (int64_t)d.nt * d.pitch;
+    if (d.off < 0 || d.off + cells > h->state_elems) return "state extent" + at;
+    if (d.woff < 0 || d.woff + cells > h->work_elems) return "work extent" + at;
+    if (h->fused_ok && (d.poff < 0 || d.poff + 4ll * fused::NB * d.pitch > h->polar_elems))
+      return "cap scratch extent" + at;
+    if (d.geo < 0 || d.geo + d.nt > h->geo_rows) return "geometry rows" + at;
+    if (d.flow < 0 || d.flow + d.nt > h->flow_rows) return "flow rows" + at;
+    if (d.col < 0 || d.col + d.np > h->col_entries) return "longitude table" + at;
+    if (d.shape < 0 || d.shape >= (int)h->shapes.size()) return "shape id" + at;
+    ext.emplace_back(d.off, d.off + cells);
+  }
+  std::sort(ext.begin(), ext.end());
+  for (size_t i = 1; i < ext.size(); ++i)
+    if (ext[i].first < ext[i - 1].second) return "overlapping state extents";
+  return "";
+}
+
+std::string check_tiles(const sft_grid* h, const std::vector<Tile>& tiles, bool fused_tiles) {
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    const Tile& t = tiles[i];
+    const std::string at = " (tile " + std::to_string(i) + ")";
+    if (t.r < 0 || t.r >= h->n_real) return "realization index" + at;
+    const RealDesc& d = h->desc[t.r];
+    const int kind = t.kind & 3;
+    if (kind == 3) return "tile kind" + at;
+    if (kind != 0) continue;
+    if (fused_tiles) {
+      const int n_strips = (d.np + fused::STRIP - 1) / fused::STRIP;
+      const int n_bands = (d.nt - 2 - 2 * fused::PB + fused::BAND - 1) / fused::BAND;
+      if (t.j0 < 0 || t.j0 >= n_bands * n_strips) return "fused work item" + at;
+    } else {
+      const int lx = t.kind >> 8;
+      if (lx < 0 || (1 << lx) > kThreads) return "tile width" + at;
+      if (t.j0 < 1 || t.j0 > d.nt - 2 || t.k0 < 0 || t.k0 >= d.np) return "tile origin" + at;
+    }
+  }
+  return "";
+}
+
 void append_tiles(const sft_grid* h, int r, int tr, std::vector<Tile>& tiles) {
   const RealInfo& ri = h->reals[r];
   const ShapeInfo& s = h->shapes[ri.shape];
@@ -481,6 +561,14 @@ template <typename T>
 sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
                         const std::vector<int>& s, Config** out) {
   auto c = std::make_unique<Config>();
+  // a failed allocation or copy below releases what was allocated before it
+  struct Release {
+    cudaStream_t st;
+    Config* c;
+    ~Release() {
+      if (c) free_config(*c, st);
+    }
+  } release{h->stream, c.get()};
   c->dt = dt;
   c->s = s;
   for (auto& sh : h->shapes) c->tr.push_back(sh.tile_rows);
@@ -559,8 +647,10 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
       const ShapeInfo& sh = h->shapes[h->reals[w.reals[i]].shape];
       if (s[i] > 0) c->diff_words += (double)sh.nt * sh.np * (3.0 + 5.0 * ((s[i] - 1 + fused::K - 1) / fused::K));
     }
+    const std::string bad = check_tiles(h, ft, true);
+    if (!bad.empty()) return fail(h, SFT_ERR_STATE, "internal table check: " + bad);
     if (!ft.empty()) {
-      SFT_CUDA(h, cudaMallocAsync(reinterpret_cast<void**>(&c->d_ftiles), ft.size() * sizeof(Tile), h->stream));
+      SFT_CUDA(h, dev_malloc_async(&c->d_ftiles, ft.size() * sizeof(Tile), h->stream));
       SFT_CUDA(h, cudaMemcpyAsync(c->d_ftiles, ft.data(), ft.size() * sizeof(Tile),
                                   cudaMemcpyHostToDevice, h->stream));
     }
@@ -572,16 +662,20 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     while (n < (int)order.size() && s[order[n]] >= j) ++n;
     c->stage_tiles[j] = n == 0 ? 0 : tile_end[n - 1];
   }
+  {
+    const std::string bad = check_tiles(h, tiles, false);
+    if (!bad.empty()) return fail(h, SFT_ERR_STATE, "internal table check: " + bad);
+  }
   if (!tiles.empty()) {
-    SFT_CUDA(h, cudaMallocAsync(reinterpret_cast<void**>(&c->d_tiles), tiles.size() * sizeof(Tile), h->stream));
+    SFT_CUDA(h, dev_malloc_async(&c->d_tiles, tiles.size() * sizeof(Tile), h->stream));
     SFT_CUDA(h, cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(Tile),
                                 cudaMemcpyHostToDevice, h->stream));
   }
-  SFT_CUDA(h, cudaMallocAsync(reinterpret_cast<void**>(&c->d_sp), sp.size() * sizeof(StepParam), h->stream));
+  SFT_CUDA(h, dev_malloc_async(&c->d_sp, sp.size() * sizeof(StepParam), h->stream));
   SFT_CUDA(h, cudaMemcpyAsync(c->d_sp, sp.data(), sp.size() * sizeof(StepParam),
                               cudaMemcpyHostToDevice, h->stream));
   if (coefs.empty()) coefs.push_back(Coef<T>{});
-  SFT_CUDA(h, cudaMallocAsync(&c->d_coef, coefs.size() * sizeof(Coef<T>), h->stream));
+  SFT_CUDA(h, dev_malloc_async(&c->d_coef, coefs.size() * sizeof(Coef<T>), h->stream));
   SFT_CUDA(h, cudaMemcpyAsync(c->d_coef, coefs.data(), coefs.size() * sizeof(Coef<T>),
                               cudaMemcpyHostToDevice, h->stream));
   // (pageable-source async copies are staged before they return: the host
@@ -595,6 +689,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     free_config(**it, h->stream);
     w.configs.erase(it);
   }
+  release.c = nullptr;
   *out = c.get();
   w.configs.push_back(std::move(c));
   return SFT_OK;
@@ -769,6 +864,9 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     if (st != SFT_OK) return st;
   }
   c->last_use = ++h->use_counter;
+  // map windows whose balance factors this step computes (recorded once the
+  // step's launches are enqueued: a step that fails leaves them unclaimed)
+  std::vector<std::pair<int, int64_t>> rfe_fresh;
   if (h->any_rfe) {  // this step's source maps and weights (read by the step's kernels)
     std::vector<RfeStep> rs(h->n_real);
     std::memset(rs.data(), 0, rs.size() * sizeof(RfeStep));
@@ -797,7 +895,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
         for (int k = 0; k < 4; ++k) q.wa[k] = wa[k];
       }
       q.fresh = ri.rfe_m0 != q.m0 ? 1 : 0;  // the factors of a kept window stay valid
-      h->reals[r].rfe_m0 = q.m0;
+      rfe_fresh.emplace_back(r, q.m0);
     }
     SFT_CUDA(h, cudaMemcpyAsync(h->d_rfe, rs.data(), rs.size() * sizeof(RfeStep), cudaMemcpyHostToDevice,
                                 h->stream));
@@ -828,6 +926,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     sft_status st = enqueue_step<T>(h, *c, ev, false);
     if (st != SFT_OK) return st;
   }
+  for (auto& f : rfe_fresh) h->reals[f.first].rfe_m0 = f.second;
   const int n_adv = (c->n_adv_tiles > 0 ? adv_stage_count(h) : 0) * (h->strang ? 2 : 1);
   // RKL2 passes (one fused pass = K stages, over both chains) and launches
   const int n_diff = c->fused ? (c->smax >= 1 ? 1 + (c->smax - 1 + fused::K - 1) / fused::K : 0) : c->smax;
@@ -901,8 +1000,8 @@ sft_status autotune(sft_handle h, Wave& w) {
     int best = 1;
     float best_ms = 1e30f;
     cudaError_t err = cudaSuccess;
-    err = cudaMalloc(&d_sp, sp.size() * sizeof(StepParam));
-    if (err == cudaSuccess) err = cudaMalloc(&d_coef, coefs.size() * sizeof(Coef<T>));
+    err = dev_malloc(&d_sp, sp.size() * sizeof(StepParam));
+    if (err == cudaSuccess) err = dev_malloc(&d_coef, coefs.size() * sizeof(Coef<T>));
     if (err == cudaSuccess) err = cudaMemcpy(d_sp, sp.data(), sp.size() * sizeof(StepParam), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(d_coef, coefs.data(), coefs.size() * sizeof(Coef<T>), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaEventCreate(&e0);
@@ -914,7 +1013,11 @@ sft_status autotune(sft_handle h, Wave& w) {
       for (int r : members) append_tiles(h, r, tr, tiles);
       cudaFree(d_tiles);
       d_tiles = nullptr;
-      err = cudaMalloc(&d_tiles, tiles.size() * sizeof(Tile));
+      if (!check_tiles(h, tiles, false).empty()) {
+        err = cudaErrorInvalidValue;
+        break;
+      }
+      err = dev_malloc(&d_tiles, tiles.size() * sizeof(Tile));
       if (err != cudaSuccess) break;
       err = cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
       if (err != cudaSuccess) break;
@@ -948,7 +1051,9 @@ sft_status autotune(sft_handle h, Wave& w) {
     cudaFree(d_coef);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (err != cudaSuccess) return fail(h, SFT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));
+    if (err != cudaSuccess)
+      return fail(h, err == cudaErrorMemoryAllocation ? SFT_ERR_OOM : SFT_ERR_CUDA,
+                  std::string("autotune: ") + cudaGetErrorString(err));
     sh.tile_rows = best;
   }
   return SFT_OK;
@@ -972,15 +1077,16 @@ sft_status upload_tables(sft_handle h) {
     sc.push_back(ShapeConst{line / (s.dth * s.cap), line / s.cap, s.dth, s.dph});
   }
   h->geo_rows = (int)g.size();
-  SFT_CUDA(h, cudaMalloc(&h->d_geo, g.size() * sizeof(RowGeo<T>)));
+  h->col_entries = (int)cp.size();
+  SFT_CUDA(h, dev_malloc(&h->d_geo, g.size() * sizeof(RowGeo<T>)));
   SFT_CUDA(h, cudaMemcpy(h->d_geo, g.data(), g.size() * sizeof(RowGeo<T>), cudaMemcpyHostToDevice));
-  SFT_CUDA(h, cudaMalloc(&h->d_geod, gd.size() * sizeof(RowGeoD)));
+  SFT_CUDA(h, dev_malloc(&h->d_geod, gd.size() * sizeof(RowGeoD)));
   SFT_CUDA(h, cudaMemcpy(h->d_geod, gd.data(), gd.size() * sizeof(RowGeoD), cudaMemcpyHostToDevice));
-  SFT_CUDA(h, cudaMalloc(&h->d_cosp, cp.size() * sizeof(double)));
+  SFT_CUDA(h, dev_malloc(&h->d_cosp, cp.size() * sizeof(double)));
   SFT_CUDA(h, cudaMemcpy(h->d_cosp, cp.data(), cp.size() * sizeof(double), cudaMemcpyHostToDevice));
-  SFT_CUDA(h, cudaMalloc(&h->d_sinp, sp.size() * sizeof(double)));
+  SFT_CUDA(h, dev_malloc(&h->d_sinp, sp.size() * sizeof(double)));
   SFT_CUDA(h, cudaMemcpy(h->d_sinp, sp.data(), sp.size() * sizeof(double), cudaMemcpyHostToDevice));
-  SFT_CUDA(h, cudaMalloc(&h->d_shc, sc.size() * sizeof(ShapeConst)));
+  SFT_CUDA(h, dev_malloc(&h->d_shc, sc.size() * sizeof(ShapeConst)));
   SFT_CUDA(h, cudaMemcpy(h->d_shc, sc.data(), sc.size() * sizeof(ShapeConst), cudaMemcpyHostToDevice));
   // flow tables: one block of nt rows per realization (filled by sft_set_flows)
   int rows = 0;
@@ -989,7 +1095,7 @@ sft_status upload_tables(sft_handle h) {
     rows += h->shapes[r.shape].nt;
   }
   h->flow_rows = rows;
-  SFT_CUDA(h, cudaMalloc(&h->d_flow, (size_t)rows * sizeof(RowFlow<T>)));
+  SFT_CUDA(h, dev_malloc(&h->d_flow, (size_t)rows * sizeof(RowFlow<T>)));
   SFT_CUDA(h, cudaMemset(h->d_flow, 0, (size_t)rows * sizeof(RowFlow<T>)));
   return SFT_OK;
 }
@@ -1036,24 +1142,39 @@ sft_status set_flows_t(sft_handle h, const sft_flow_params* params) {
       sh.geo = (int)g.size();
       geo_rows<T>(sh, g, gd);
     }
+    std::vector<RealDesc> nd = h->desc;
     for (int r = 0; r < h->n_real; ++r) {
       const ShapeInfo& sh = h->shapes[h->reals[r].shape];
       if (params[r].nu_grid_alpha > 0.0) {
-        h->desc[r].geo = (int)g.size();
+        nd[r].geo = (int)g.size();
         geo_rows_grid_nu<T>(sh, params[r].nu_grid_alpha, g, gd);
       } else {
-        h->desc[r].geo = sh.geo;
+        nd[r].geo = sh.geo;
       }
     }
     SFT_CUDA(h, cudaStreamSynchronize(h->stream));
     if ((int)g.size() != h->geo_rows) {
+      // new tables first: a failed allocation leaves the old ones (and the
+      // descriptors that index them) in place
+      void* ng = nullptr;
+      RowGeoD* ngd = nullptr;
+      cudaError_t e = dev_malloc(&ng, g.size() * sizeof(RowGeo<T>));
+      if (e == cudaSuccess) e = dev_malloc(&ngd, gd.size() * sizeof(RowGeoD));
+      if (e != cudaSuccess) {
+        cudaFree(ng);
+        return fail(h, e == cudaErrorMemoryAllocation ? SFT_ERR_OOM : SFT_ERR_CUDA,
+                    std::string("geometry tables: ") + cudaGetErrorString(e));
+      }
       cudaFree(h->d_geo);
       cudaFree(h->d_geod);
-      h->d_geo = nullptr;
-      h->d_geod = nullptr;
-      SFT_CUDA(h, cudaMalloc(&h->d_geo, g.size() * sizeof(RowGeo<T>)));
-      SFT_CUDA(h, cudaMalloc(&h->d_geod, gd.size() * sizeof(RowGeoD)));
+      h->d_geo = ng;
+      h->d_geod = ngd;
       h->geo_rows = (int)g.size();
+    }
+    h->desc = nd;
+    {
+      const std::string bad = check_desc(h);
+      if (!bad.empty()) return fail(h, SFT_ERR_STATE, "internal table check: " + bad);
     }
     SFT_CUDA(h, cudaMemcpy(h->d_geo, g.data(), g.size() * sizeof(RowGeo<T>), cudaMemcpyHostToDevice));
     SFT_CUDA(h, cudaMemcpy(h->d_geod, gd.data(), gd.size() * sizeof(RowGeoD), cudaMemcpyHostToDevice));
@@ -1184,10 +1305,10 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
     h->wave_size = 0;
     for (auto& w : h->waves) h->wave_size = std::max<int>(h->wave_size, (int)w.reals.size());
   }
-  CREATE_CUDA(cudaMalloc(&h->state, state_bytes));
+  CREATE_CUDA(dev_malloc(&h->state, state_bytes));
   CREATE_CUDA(cudaMemsetAsync(h->state, 0, state_bytes, h->stream));
   for (int i = 0; i < h->n_work; ++i) {
-    CREATE_CUDA(cudaMalloc(&h->work[i], std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem));
+    CREATE_CUDA(dev_malloc(&h->work[i], std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem));
     CREATE_CUDA(cudaMemsetAsync(h->work[i], 0, std::max<int64_t>(h->work_elems, 32) * (int64_t)h->elem,
                                 h->stream));
   }
@@ -1202,7 +1323,7 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
       }
       h->polar_elems = std::max(h->polar_elems, used);
     }
-    CREATE_CUDA(cudaMalloc(&h->polar, std::max<int64_t>(h->polar_elems, 32) * sizeof(float)));
+    CREATE_CUDA(dev_malloc(&h->polar, std::max<int64_t>(h->polar_elems, 32) * sizeof(float)));
     CREATE_CUDA(prepare_rkl2_fused());
   }
   sft_status st = prec == SFT_FP32 ? upload_tables<float>(h) : upload_tables<double>(h);
@@ -1213,10 +1334,17 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
     const ShapeInfo& s = h->shapes[ri.shape];
     desc[r] = RealDesc{ri.off, ri.woff, s.nt, s.np, s.pitch, ri.shape, s.geo, ri.flow_row, s.col, poff[r]};
   }
-  CREATE_CUDA(cudaMalloc(&h->d_desc, desc.size() * sizeof(RealDesc)));
+  CREATE_CUDA(dev_malloc(&h->d_desc, desc.size() * sizeof(RealDesc)));
   CREATE_CUDA(cudaMemcpy(h->d_desc, desc.data(), desc.size() * sizeof(RealDesc), cudaMemcpyHostToDevice));
   h->desc = desc;
-  CREATE_CUDA(cudaMalloc(&h->d_status, sizeof(int)));
+  {
+    const std::string bad = check_desc(h);
+    if (!bad.empty()) {
+      h->err = "internal table check: " + bad;
+      return bail(SFT_ERR_STATE);
+    }
+  }
+  CREATE_CUDA(dev_malloc(&h->d_status, sizeof(int)));
   CREATE_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
   // reduction tiles: bands of about 32k cells
   std::vector<RedTile> rt;
@@ -1229,15 +1357,15 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   }
   rstart.push_back((int)rt.size());
   h->n_rtiles = (int)rt.size();
-  CREATE_CUDA(cudaMalloc(&h->d_rtiles, rt.size() * sizeof(RedTile)));
+  CREATE_CUDA(dev_malloc(&h->d_rtiles, rt.size() * sizeof(RedTile)));
   CREATE_CUDA(cudaMemcpy(h->d_rtiles, rt.data(), rt.size() * sizeof(RedTile), cudaMemcpyHostToDevice));
-  CREATE_CUDA(cudaMalloc(&h->d_rstart, rstart.size() * sizeof(int)));
+  CREATE_CUDA(dev_malloc(&h->d_rstart, rstart.size() * sizeof(int)));
   CREATE_CUDA(cudaMemcpy(h->d_rstart, rstart.data(), rstart.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CREATE_CUDA(cudaMalloc(&h->d_partials, (size_t)h->n_rtiles * kDiagFields * sizeof(double)));
-  CREATE_CUDA(cudaMalloc(&h->d_red, (size_t)n_real * kDiagFields * sizeof(double)));
-  CREATE_CUDA(cudaMallocHost(&h->h_red, (size_t)n_real * kDiagFields * sizeof(double)));
-  CREATE_CUDA(cudaMalloc(&h->d_wpar, (size_t)n_real * 4 * sizeof(double)));
-  CREATE_CUDA(cudaMalloc(&h->d_obs_off, (size_t)n_real * sizeof(int64_t)));
+  CREATE_CUDA(dev_malloc(&h->d_partials, (size_t)h->n_rtiles * kDiagFields * sizeof(double)));
+  CREATE_CUDA(dev_malloc(&h->d_red, (size_t)n_real * kDiagFields * sizeof(double)));
+  CREATE_CUDA(host_malloc(&h->h_red, (size_t)n_real * kDiagFields * sizeof(double)));
+  CREATE_CUDA(dev_malloc(&h->d_wpar, (size_t)n_real * 4 * sizeof(double)));
+  CREATE_CUDA(dev_malloc(&h->d_obs_off, (size_t)n_real * sizeof(int64_t)));
   for (auto& e : h->ev) CREATE_CUDA(cudaEventCreate(&e));
   CREATE_CUDA(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device));
   CREATE_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
@@ -1339,6 +1467,8 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
     for (auto& c : w.configs) free_config(*c, h->stream);
     w.configs.clear();
   }
+  // tables are rewritten in place: until they are complete no step may run
+  h->flows_set = false;
   sft_status st = h->prec == SFT_FP32 ? set_flows_t<float>(h, params) : set_flows_t<double>(h, params);
   if (st == SFT_OK) {
     h->flows_set = true;
@@ -1435,7 +1565,7 @@ sft_status sft_assimilate(sft_handle h, const void* br_obs, const void* mu, int3
       cudaFree(h->d_obs);
       h->d_obs = nullptr;
       h->obs_bytes = 0;
-      SFT_CUDA(h, cudaMalloc(&h->d_obs, 2 * bytes));
+      SFT_CUDA(h, dev_malloc(&h->d_obs, 2 * bytes));
       h->obs_bytes = 2 * bytes;
     }
     char* base = static_cast<char*>(h->d_obs);
@@ -1481,16 +1611,16 @@ sft_status sft_set_rfe(sft_handle h, const sft_rfe_params* params) {
     w.configs.clear();
   }
   bool any = false;
+  for (int r = 0; r < h->n_real && params; ++r)
+    any = any || (params[r].method != 0 && params[r].rate_mx_per_hour > 0.0);
+  // buffers first: a failed allocation leaves the previous settings in force
+  if (any && !h->d_rfe) SFT_CUDA(h, dev_malloc(&h->d_rfe, (size_t)h->n_real * sizeof(RfeStep)));
+  if (any && !h->d_rfe_fac) SFT_CUDA(h, dev_malloc(&h->d_rfe_fac, (size_t)h->n_real * 8 * sizeof(double)));
   for (int r = 0; r < h->n_real; ++r) {
     RealInfo& ri = h->reals[r];
     ri.rfe = params ? params[r] : sft_rfe_params{};
     ri.rfe_t0 = ri.rfe.origin_given ? ri.rfe.origin_hours : ri.t;
     ri.rfe_m0 = -1;
-    any = any || (ri.rfe.method != 0 && ri.rfe.rate_mx_per_hour > 0.0);
-  }
-  if (any && !h->d_rfe) {
-    SFT_CUDA(h, cudaMalloc(&h->d_rfe, (size_t)h->n_real * sizeof(RfeStep)));
-    SFT_CUDA(h, cudaMalloc(&h->d_rfe_fac, (size_t)h->n_real * 8 * sizeof(double)));
   }
   h->any_rfe = any;
   return SFT_OK;
@@ -1616,6 +1746,28 @@ sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cf
   if (dt_cfl) *dt_cfl = ri.dt_cfl;
   if (dt_euler) *dt_euler = ri.dt_euler;
   if (stages) *stages = ri.fp.diffusion == SFT_DIFF_RKL2 ? rkl2_stages(dt_hours, ri.dt_euler) : 0;
+  return SFT_OK;
+}
+
+sft_status sft_debug_checks(uint64_t* first_failure, uint32_t* failures, int32_t reset) {
+  if (!sft::kDebugBuild) return fail(nullptr, SFT_ERR_STATE, "library built without SFT_DEBUG");
+  const cudaError_t e = sft::debug_read(first_failure, failures, reset != 0);
+  if (e != cudaSuccess) return fail(nullptr, SFT_ERR_CUDA, std::string("sft_debug_checks: ") + cudaGetErrorString(e));
+  return SFT_OK;
+}
+
+sft_status sft_debug_probe(int32_t site, int64_t value, int64_t lo, int64_t hi) {
+  if (!sft::kDebugBuild) return fail(nullptr, SFT_ERR_STATE, "library built without SFT_DEBUG");
+  if (site <= 0 || site > 0xffff || lo > hi) return fail(nullptr, SFT_ERR_ARG, "site in 1..65535 and lo <= hi");
+  cudaError_t e = sft::launch_debug_probe(site, value, lo, hi, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(nullptr, SFT_ERR_CUDA, std::string("sft_debug_probe: ") + cudaGetErrorString(e));
+  return SFT_OK;
+}
+
+sft_status sft_debug_fail_alloc(int32_t nth) {
+  if (nth < 0) return fail(nullptr, SFT_ERR_ARG, "nth must be >= 0");
+  g_fail_alloc.store(nth);
   return SFT_OK;
 }
 

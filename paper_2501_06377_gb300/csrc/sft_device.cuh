@@ -22,6 +22,56 @@ namespace sft {
 
 constexpr int kThreads = 256;
 
+// ---- Index checks of the debug build (compiled with -DSFT_DEBUG) ----------
+// A kernel checks each index it derives from its tile and descriptor (a row,
+// a column, the first and last row of a band) against the closed range
+// [lo, hi] inside which every access it makes with that index stays within
+// the realization's rows.  A failed check records (site, value) on the device
+// (the first failure wins; a counter counts them all) and clamps the index
+// into its range, so the accesses that follow stay in bounds and nothing
+// traps.  The release build compiles the checks away.  The host-built tables
+// the kernels start from (descriptors, tiles) are checked on the host when
+// they are built, in every build.
+#ifdef SFT_DEBUG
+constexpr bool kDebugBuild = true;
+#define SFT_DCHECK(site, v, lo, hi) ((v) = ::sft::dbg_check((site), (v), (lo), (hi)))
+#else
+constexpr bool kDebugBuild = false;
+#define SFT_DCHECK(site, v, lo, hi) ((void)0)
+#endif
+
+// Check sites (the high 16 bits of the recorded word).
+enum DebugSite : int {
+  DBG_PROBE = 1,          // sft_debug_probe
+  DBG_STAGE_ROW = 2,      // rkl2_stage_kernel interior row j in [1, nt-2]
+  DBG_STAGE_COL = 3,      // its first column kc in [0, pitch-V]
+  DBG_ADV_ROW = 4,        // adv_stage_kernel interior row
+  DBG_ADV_COL = 5,        // its first column
+  DBG_FUSED_FIRST = 6,    // rkl2_fused_kernel band: first loaded row in [0, nt-1]
+  DBG_FUSED_LAST = 7,     // last loaded row in [first, nt-1]
+  DBG_FUSED_COL = 8,      // a lane's first column in [0, np-1] (np-4 when vectorised)
+  DBG_FUSED_CAP = 9,      // first row of a cap block in [0, nt-NB]
+  DBG_RED_ROWS = 10,      // reduction / RFE tile rows within [0, nt]
+};
+
+// Records (site, value) and counts the failure (defined in the debug build).
+__device__ void dbg_record(int site, int64_t v);
+
+template <typename I>
+__device__ __forceinline__ I dbg_check(int site, I v, I lo, I hi) {
+  if (v < lo || v > hi) {
+    dbg_record(site, (int64_t)v);
+    return v < lo ? lo : hi;
+  }
+  return v;
+}
+
+// Host side of the checks: read (and optionally clear) the record, run one
+// check on the device with no memory access (a self-test of the record path).
+// Both return cudaErrorNotSupported in the release build.
+cudaError_t debug_read(uint64_t* first, uint32_t* count, bool reset);
+cudaError_t launch_debug_probe(int site, int64_t v, int64_t lo, int64_t hi, cudaStream_t st);
+
 template <typename T> struct VecT;
 template <> struct VecT<float> { using type = float4; static constexpr int N = 4; };
 template <> struct VecT<double> { using type = double2; static constexpr int N = 2; };

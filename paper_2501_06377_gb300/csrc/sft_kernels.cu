@@ -20,6 +20,50 @@
 
 namespace sft {
 
+#ifdef SFT_DEBUG
+namespace {
+__device__ unsigned long long g_dbg_first;  // (site << 48) | (value mod 2^48) of the first failed check
+__device__ unsigned int g_dbg_count;        // failed checks
+
+__global__ void debug_probe_kernel(int site, int64_t v, int64_t lo, int64_t hi) {
+  (void)dbg_check(site, v, lo, hi);
+}
+}  // namespace
+
+__device__ void dbg_record(int site, int64_t v) {
+  const unsigned long long w =
+      ((unsigned long long)(site & 0xffff) << 48) | ((unsigned long long)v & ((1ull << 48) - 1));
+  atomicCAS(&g_dbg_first, 0ull, w);
+  atomicAdd(&g_dbg_count, 1u);
+}
+
+cudaError_t debug_read(uint64_t* first, uint32_t* count, bool reset) {
+  cudaError_t e = cudaDeviceSynchronize();  // side streams included
+  unsigned long long f = 0;
+  unsigned int c = 0;
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&f, g_dbg_first, sizeof(f));
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&c, g_dbg_count, sizeof(c));
+  if (e != cudaSuccess) return e;
+  if (first) *first = f;
+  if (count) *count = c;
+  if (reset) {
+    f = 0;
+    c = 0;
+    e = cudaMemcpyToSymbol(g_dbg_first, &f, sizeof(f));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dbg_count, &c, sizeof(c));
+  }
+  return e;
+}
+
+cudaError_t launch_debug_probe(int site, int64_t v, int64_t lo, int64_t hi, cudaStream_t st) {
+  debug_probe_kernel<<<1, 1, 0, st>>>(site, v, lo, hi);
+  return cudaGetLastError();
+}
+#else
+cudaError_t debug_read(uint64_t*, uint32_t*, bool) { return cudaErrorNotSupported; }
+cudaError_t launch_debug_probe(int, int64_t, int64_t, int64_t, cudaStream_t) { return cudaErrorNotSupported; }
+#endif
+
 namespace {
 
 template <typename T> struct Vec;
@@ -223,9 +267,11 @@ rkl2_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   }
 
   const int ty = threadIdx.x >> lx, tx = threadIdx.x & ((1 << lx) - 1), lane = threadIdx.x & 31;
-  const int j = tl.j0 + ty;
+  int j = tl.j0 + ty;
   if (j > d.nt - 2) return;  // a warp lies within one row: uniform exit
-  const int kc = tl.k0 + tx * N;
+  SFT_DCHECK(DBG_STAGE_ROW, j, 1, d.nt - 2);
+  int kc = tl.k0 + tx * N;
+  if (kc < np) SFT_DCHECK(DBG_STAGE_COL, kc, 0, min(np - 1, pitch - N));
   const int64_t ro = (int64_t)j * pitch;
   T c[N], up[N], dn[N];
   if (kc < np) {
@@ -410,9 +456,11 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
   }
 
   const int ty = threadIdx.x >> lx, tx = threadIdx.x & ((1 << lx) - 1), lane = threadIdx.x & 31;
-  const int j = tl.j0 + ty;
+  int j = tl.j0 + ty;
   if (j > nt - 2) return;
-  const int kc = tl.k0 + tx * N;
+  SFT_DCHECK(DBG_ADV_ROW, j, 1, nt - 2);
+  int kc = tl.k0 + tx * N;
+  if (kc < np) SFT_DCHECK(DBG_ADV_COL, kc, 0, min(np - 1, pitch - N));
   const int64_t ro = (int64_t)j * pitch;
   T R[5][N];
   if (kc < np) {
@@ -748,7 +796,8 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
     // round trips are in flight per thread instead of one.
     constexpr int CU = 8;
     const bool north = kind == 1;
-    const int base = north ? 0 : nt - NB;  // global row of local row 0
+    int base = north ? 0 : nt - NB;  // global row of local row 0
+    SFT_DCHECK(DBG_FUSED_CAP, base, 0, nt - NB);
     float* prv = polar + d.poff + (north ? 0 : 2 * NB * pitch);  // level m-2, updated to m
     float* cur = prv + NB * pitch;                                // level m-1
     for (int i = 0; i < NB; ++i) {
@@ -869,6 +918,15 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   extern __shared__ __align__(16) float4 rings[];
   const int tmin = J0 - K;        // first row loaded
   const int t_end = J1 - 1 + kk;  // last row loaded
+#ifdef SFT_DEBUG
+  // every row the band loads or writes lies in [tmin, t_end]; a band or a
+  // column outside the realization skips the work item (whole warp: the
+  // march shuffles across lanes) after its check is recorded
+  const bool dbg_bad = dbg_check(DBG_FUSED_FIRST, tmin, 0, nt - 1) != tmin ||
+                       dbg_check(DBG_FUSED_LAST, t_end, tmin, nt - 1) != t_end ||
+                       dbg_check(DBG_FUSED_COL, col, 0, vec ? np - 4 : np - 1) != col;
+  if (__any_sync(0xffffffffu, dbg_bad)) return;
+#endif
   March S;
   S.rc = rings + warp * RING_F4;
   S.ra = S.rc + D * LANES;
@@ -985,6 +1043,9 @@ reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __res
   const RedTile tl = tiles[blockIdx.x];
   const RealDesc d = rd[tl.r];
   const T* b = state + d.off;
+  int j0 = tl.j0, j1 = tl.j1;
+  SFT_DCHECK(DBG_RED_ROWS, j0, 0, d.nt);
+  SFT_DCHECK(DBG_RED_ROWS, j1, j0, d.nt);
   double acc[11];
 #pragma unroll
   for (int f = 0; f < 11; ++f) acc[f] = 0.0;
@@ -992,7 +1053,7 @@ reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __res
   const double* w = aa.wpar ? aa.wpar + 4 * tl.r : nullptr;
   const int64_t obase = aa.obs_off ? aa.obs_off[tl.r] : 0;
   T tmn = T(INFINITY), tmx = T(-INFINITY), tamn = T(INFINITY);
-  for (int j = tl.j0; j < tl.j1; ++j) {
+  for (int j = j0; j < j1; ++j) {
     const RowGeoD gd = geod[d.geo + j];
     const bool pole = (j == 0) || (j == d.nt - 1);
     const T* row = b + (int64_t)j * d.pitch;
@@ -1259,7 +1320,10 @@ rfe_apply_kernel(const RedTile* __restrict__ tiles, const RealDesc* __restrict__
   }
   const int64_t ncell = (int64_t)(d.nt - 2) * d.np + 2;
   T* b = state + d.off;
-  for (int j = tl.j0; j < tl.j1; ++j) {
+  int j0 = tl.j0, j1 = tl.j1;
+  SFT_DCHECK(DBG_RED_ROWS, j0, 0, d.nt);
+  SFT_DCHECK(DBG_RED_ROWS, j1, j0, d.nt);
+  for (int j = j0; j < j1; ++j) {
     const RowGeoD gd = geod[d.geo + j];
     const bool pole = j == 0 || j == d.nt - 1;
     const double cell_area = pole ? gd.area * d.np : gd.area;

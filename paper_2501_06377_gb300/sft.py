@@ -106,6 +106,9 @@ _SIGS = {
                                 C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "sft_flux_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int,
                                                C.c_double, C.c_void_p, C.POINTER(sft_diag)]),
+    "sft_debug_checks": (C.c_int, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint32), C.c_int32]),
+    "sft_debug_probe": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64]),
+    "sft_debug_fail_alloc": (C.c_int, [C.c_int32]),
     "sft_last_error": (C.c_char_p, [C.c_void_p]),
     "sft_abi_version": (C.c_int32, []),
 }

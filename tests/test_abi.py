@@ -27,7 +27,7 @@ def test_binding_covers_the_header(lib):
 
 
 def test_abi_version(lib):
-    assert lib.sft_abi_version() == 6
+    assert lib.sft_abi_version() == 7
 
 
 def test_create_rejects_bad_arguments_before_any_cuda_call(lib):
@@ -60,3 +60,20 @@ def test_surrogate_header_exported_and_bound(lib):
     raw = C.CDLL(sft.LIB_PATH)
     assert all(hasattr(raw, n) for n in names)
     assert set(names) == set(surrogate._SIGS)
+
+
+def test_debug_entry_points_without_a_gpu(lib):
+    """The release library reports that it has no device checks, and the
+    allocation-failure injector validates its argument (no CUDA call)."""
+    assert lib.sft_debug_checks(None, None, 0) == sft.SFT_ERR_STATE
+    assert b"SFT_DEBUG" in lib.sft_last_error(None)
+    assert lib.sft_debug_probe(1, 5, 0, 10) == sft.SFT_ERR_STATE
+    assert lib.sft_debug_fail_alloc(-1) == sft.SFT_ERR_ARG
+    assert lib.sft_debug_fail_alloc(0) == sft.SFT_OK
+
+
+def test_debug_library_builds_and_exports_the_header():
+    path = B.build(debug=True)
+    raw = C.CDLL(path)
+    missing = [n for n in sft.header_functions() if not hasattr(raw, n)]
+    assert not missing, missing
