@@ -13,9 +13,10 @@ value: realization-cell-updates/s (sum over realizations of ntheta*nphi per
 step / device time), inputs resident in HBM.  e2e: the same step driven
 through the C-ABI with pinned host buffers (set_state from host, step,
 get_state to host) inside the timed region.  roofline: the RKL2 stages
-(the fused four-stage kernel dominates), algorithmic bytes per pass (20 B
-per cell per four stages: read delta_{j-2}, delta_{j-1}, G, write two
-increments; stage 1 3 words) over the CUDA-event time of the RKL2 region.  cpu_baseline: the FP64 oracle on a bounded sample, one
+(the fused eight-stage kernel dominates), algorithmic bytes per pass (20 B
+per cell per pass of eight stages: read delta_{j-2}, delta_{j-1}, G, write
+two increments; stage 1 3 words) over the CUDA-event time of the RKL2
+region.  cpu_baseline: the FP64 oracle on a bounded sample, one
 realization per host core (spawned processes).
 
 Multi-GPU (torchrun): realizations are independent, so each rank runs its
@@ -42,13 +43,13 @@ import numpy as np  # noqa: E402
 NT, NP, NREAL = 1024, 2048, 64
 
 # DRAM traffic of rkl2_fused_kernel from one ncu capture (16 x 1024x2048
-# ensemble, one launch of the chain holding 8 realizations, all four stages):
-# dram__bytes_read + dram__bytes_write = 0.9845 x the launch's algorithmic
-# bytes (reads +14.6 %: band-overlap rows; writes -25 %: dirty lines still in
-# L2 when the launch ends).  Reported per pass as ratio x algorithmic bytes,
-# and only while the kernel sources hash to the profiled ones.
-FUSED_TRAFFIC = {"ratio": 0.9845, "profile": "profiles/rkl2_fused_kernel_ncu_16x1024x2048.md",
-                 "sha256": "3d82c579ff7f4269e0978838dc152b36a360c544be6eb38e3b6a1e53606b8730"}
+# ensemble, one pass over all 16 realizations, eight stages):
+# dram__bytes_read + dram__bytes_write = 1.0826 x the launch's algorithmic
+# bytes (reads +16.9 %: band-overlap rows; writes -4.7 %: dirty lines still
+# in L2 when the launch ends).  Reported per pass as ratio x algorithmic
+# bytes, and only while the kernel sources hash to the profiled ones.
+FUSED_TRAFFIC = {"ratio": 1.0826, "profile": "profiles/rkl2_fused_kernel_ncu_16x1024x2048.md",
+                 "sha256": "a94f0c30d0a1f6c59877f73d9c3f1430a7b8d6e6fe272e53cacb7b885a185c21"}
 KERNEL_SOURCES = ("paper_2501_06377_gb300/csrc/sft_kernels.cu", "paper_2501_06377_gb300/csrc/sft_device.cuh")
 
 
@@ -305,7 +306,7 @@ def run_gpu(args, rank, world, local_rank):
     updates = st["cell_updates"] * world
     value = updates / (ms * 1e-3)
     peak, peak_kind = _peaks()
-    # per RKL2 pass (a fused pass = 4 stages; its launches on the two chains overlap)
+    # per RKL2 pass (a fused pass = 8 stages; its launches on the two chains overlap)
     diff_pass_ms = st["diff_ms"] / max(st["diff_launches"], 1)
     diff_pass_bytes = st["diff_bytes"] / max(st["diff_launches"], 1)
     achieved = diff_pass_bytes / (diff_pass_ms * 1e-3) / 1e9
@@ -358,14 +359,14 @@ def run_gpu(args, rank, world, local_rank):
                                              "advection": st["adv_ms"] / args.steps,
                                              "rest": (ms - st["diff_ms"] - st["adv_ms"]) / args.steps}},
             "roofline": {"bound": "hbm",
-                         "kernel": ("rkl2_fused_kernel (4 RKL2 stages per launch, two launch chains)"
-                                    if g.get_fusion() == 4 else "rkl2_stage_kernel<float>"),
+                         "kernel": ("rkl2_fused_kernel (8 RKL2 stages per launch, two launch chains)"
+                                    if g.get_fusion() > 1 else "rkl2_stage_kernel<float>"),
                          "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind + " hbm_gbs",
                          "bytes_per_pass": diff_pass_bytes, "ms_per_pass": diff_pass_ms,
                          "traffic": (FUSED_TRAFFIC["ratio"] * diff_pass_bytes
-                                     if g.get_fusion() == 4
+                                     if g.get_fusion() > 1
                                      and FUSED_TRAFFIC["sha256"] == kernel_sources_sha256() else None),
                          "traffic_source": FUSED_TRAFFIC["profile"]},
             "e2e": {"value": cells_per_step * world / (e2e_ms * 1e-3), "unit": "cell-updates/s",

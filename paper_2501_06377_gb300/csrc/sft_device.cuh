@@ -175,8 +175,8 @@ cudaError_t launch_adv_stage(int n_tiles, cudaStream_t st, const Tile* tiles, co
 // Fused RKL2: K stages per launch (see rkl2_fused_kernel in sft_kernels.cu).
 namespace fused {
 constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
-constexpr int K = 4;             // RKL2 stages per pass
-constexpr int BAND = 64;         // rows of one interior band (a warp marches through it)
+constexpr int K = 8;             // RKL2 stages per pass
+constexpr int BAND = 128;        // rows of one interior band (a warp marches through it)
 constexpr int LANES = 32;
 constexpr int HL = (K + 3) / 4;  // phi-halo lanes on each side of a strip (4 columns each, >= K)
 constexpr int STRIP = 4 * (LANES - 2 * HL);  // output columns of one warp strip (lanes HL..31-HL)

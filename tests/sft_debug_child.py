@@ -83,7 +83,7 @@ def main():
     lib = sft.load()
     out = {"errors": {}}
     ragged = [(33, 64), (20, 100), (41, 70)]        # phi tails off the vector width
-    fused = [(20, 100), (57, 520), (41, 70)]        # the fused path, float4 and scalar rows
+    fused = [(36, 100), (57, 520), (41, 70)]        # the fused path, float4 and scalar rows
     out["errors"]["fp64_lie"], _ = case_steps("fp64", ragged, 3, 6.0)
     out["errors"]["fp32_fused"], out["fusion"] = case_steps("fp32", fused, 4, 6.0)
     out["errors"]["fp32_strang_atten_rfe"], _ = case_steps("fp32", fused, 5, 1.0, rfe=True,
