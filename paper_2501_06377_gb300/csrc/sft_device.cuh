@@ -180,14 +180,16 @@ constexpr int BAND = 128;        // rows of one interior band (a warp marches th
 constexpr int LANES = 32;
 constexpr int HL = (K + 3) / 4;  // phi-halo lanes on each side of a strip (4 columns each, >= K)
 constexpr int STRIP = 4 * (LANES - 2 * HL);  // output columns of one warp strip (lanes HL..31-HL)
-constexpr int WARPS = 8;         // strips per block
+constexpr int WARPS = 4;         // strips per block (two 128-thread blocks share an SM)
+constexpr int THREADS = WARPS * LANES;
 constexpr int PB = K;            // rows next to each pole owned by the cap blocks
 constexpr int NB = PB + K + 1;   // rows a cap block holds (pole row + PB + K halo rows)
 constexpr int D = 4;             // rows of asynchronous-copy lookahead per warp (a power of 2)
 constexpr int DG = pow2_at_least(D + K);  // G ring depth: level m reads G m rows back
 constexpr int RING_F4 = (2 * D + DG) * LANES;   // float4 slots of one warp's rings
 constexpr int GROWS = BAND + 3 * K;             // geometry rows of one work item (rows tmin-K ..)
-constexpr size_t kSmemBytes = sizeof(float) * 4 * (RING_F4 + 2 * GROWS) * WARPS;
+// per warp: rings, geometry (one float4 per row), coefficient table (DG rows x K levels x 2 float4)
+constexpr size_t kSmemBytes = sizeof(float) * 4 * (RING_F4 + GROWS + 2 * K * DG) * WARPS;
 static_assert((D & (D - 1)) == 0 && (DG & (DG - 1)) == 0 && DG >= D + K, "ring sizes");
 // A grid shape can use the fused path when the interior band is non-empty.
 inline bool shape_ok(int nt, int np) { return nt >= 2 * NB + 2 && np >= 16; }

@@ -565,23 +565,20 @@ __device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group
 //   o = a0 c + a1 up + a2 dn + a3 (l + r) + nu d2 + gsum G,
 //   a1..a3 = mu~ nu dt (cN, cS, cE),  a0 = mu + mu~ nu dt cC,
 //   cC = -(cN + cS + 2 cE)
-// (the same stage as rkl2_point, other rounding), evaluated on (x, y) and
+// (the same stage as rkl2_point, other rounding and summation order), evaluated on (x, y) and
 // (z, w) pairs with the packed f32x2 FMA: the same IEEE operations per
-// element as the scalar forms.
-struct LevelK {  // per-level constants, each duplicated into a pair
-  float2 mu, md, nu, gs;
+// element as the scalar forms.  A row's coefficients for all K levels are
+// formed once per row by the warp, one per lane, and read back as pairs
+// ka = (a1, a1, a2, a2), kb = (a3, a3, a0, a0).
+struct LevelNG {  // per-level constants, each duplicated into a pair
+  float2 nu, gs;
 };
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
-__device__ __forceinline__ float4 level_update(const LevelK& q, float4 g0, float4 g1, float4 c, float4 up,
+__device__ __forceinline__ float4 level_update(const LevelNG& q, float4 ka, float4 kb, float4 c, float4 up,
                                                float4 dn, float4 d2, float4 gv) {
-  // g0 = (cN, cN, cS, cS), g1 = (cE, cE, cC, cC) of the row
-  const float2 a1 = __fmul2_rn(q.md, lo2(g0));
-  const float2 a2 = __fmul2_rn(q.md, hi2(g0));
-  const float2 a3 = __fmul2_rn(q.md, lo2(g1));
-  const float2 a0 = __ffma2_rn(q.md, hi2(g1), q.mu);
   const float l = __shfl_up_sync(0xffffffffu, c.w, 1);
   const float r = __shfl_down_sync(0xffffffffu, c.x, 1);
   const float2 h01 = make_float2(l + c.y, c.x + c.z);
@@ -590,14 +587,16 @@ __device__ __forceinline__ float4 level_update(const LevelK& q, float4 g0, float
   float2 o23 = __fmul2_rn(q.gs, hi2(gv));
   o01 = __ffma2_rn(q.nu, lo2(d2), o01);
   o23 = __ffma2_rn(q.nu, hi2(d2), o23);
-  o01 = __ffma2_rn(a3, h01, o01);
-  o23 = __ffma2_rn(a3, h23, o23);
-  o01 = __ffma2_rn(a2, lo2(dn), o01);
-  o23 = __ffma2_rn(a2, hi2(dn), o23);
-  o01 = __ffma2_rn(a1, lo2(up), o01);
-  o23 = __ffma2_rn(a1, hi2(up), o23);
-  o01 = __ffma2_rn(a0, lo2(c), o01);
-  o23 = __ffma2_rn(a0, hi2(c), o23);
+  o01 = __ffma2_rn(lo2(kb), h01, o01);
+  o23 = __ffma2_rn(lo2(kb), h23, o23);
+  o01 = __ffma2_rn(lo2(ka), lo2(up), o01);
+  o23 = __ffma2_rn(lo2(ka), hi2(up), o23);
+  o01 = __ffma2_rn(hi2(kb), lo2(c), o01);
+  o23 = __ffma2_rn(hi2(kb), hi2(c), o23);
+  // dn (level m-1's row computed in this same step) enters last: one FMA
+  // per level on the chain through the K levels of a row step
+  o01 = __ffma2_rn(hi2(ka), lo2(dn), o01);
+  o23 = __ffma2_rn(hi2(ka), hi2(dn), o23);
   return make_float4(o01.x, o01.y, o23.x, o23.y);
 }
 
@@ -607,16 +606,28 @@ __device__ __forceinline__ float4 level_update(const LevelK& q, float4 g0, float
 // only at its output step.  The inputs arrive through per-warp shared-memory
 // rings filled D rows ahead by cp.async (each lane copies its own float4, so
 // a lane only ever reads what it copied itself); G keeps K more rows because
-// level m reads it m rows behind the loads.  The band's row geometry sits in
-// shared memory as coefficient pairs, staged once per work item.
+// level m reads it m rows behind the loads.  The band's row geometry (cN,
+// cS, cE, cC per row) is staged once per work item in shared memory; at
+// each row step every lane forms one of the row's 4K level coefficients
+// (level lane/4, coefficient lane%4) into a table ring indexed like G's.
 struct March {
   float4 Win[fused::K][3];
   float4 d2m1;               // delta_{j-2} at row t-1
   float4 *rc, *ra, *rg;      // rings: C, A (D rows), G (DG rows)
-  const float4* geo;         // 2 float4 per row; row r at 2 (r - gbase)
+  const float4* geo;         // (cN, cS, cE, cC); row r at r - gbase
+  float4* tab;               // coefficient table: DG rows x K levels x (ka, kb)
   int gbase;
-  LevelK lv[fused::K];       // per-level constants (registers)
+  float kmul, kadd;          // this lane's coefficient: kmul * geometry + kadd
+  LevelNG lv[fused::K];      // per-level constants (registers)
 };
+
+// This lane's coefficient of row r (all K levels of a row: one per lane).
+__device__ __forceinline__ void table_row(March& S, int r, int lane) {
+  static_assert(4 * fused::K == fused::LANES, "one coefficient per lane");
+  const float gc = reinterpret_cast<const float*>(S.geo + (r - S.gbase))[lane & 3];
+  const float v = fmaf(S.kmul, gc, S.kadd);
+  reinterpret_cast<float2*>(S.tab)[(r & (fused::DG - 1)) * fused::LANES + lane] = make_float2(v, v);
+}
 
 // Issue the asynchronous copies of row r's inputs into the rings (one commit
 // group; empty past the band's last row t_end, which keeps the group count
@@ -653,18 +664,18 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, co
   S.Win[0][P] = S.rc[cs];
   const float4 a_t = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : S.ra[cs];
   float4 top = make_float4(0.f, 0.f, 0.f, 0.f);  // level K at row t-K
-  const float4* gp = S.geo + 2 * (t - S.gbase);   // geometry of row t; level m reads row t-m
-  const int tg = t & (DG - 1);                    // G ring slot of row t
+  const int tg = t & (DG - 1);                    // G and table ring slot of row t
 #pragma unroll
   for (int m = 1; m <= K; ++m) {
     if (FULL || m <= kk) {
       const int sc = ((P - m) % 3 + 3) % 3;       // slot of row t-m in level m-1's window
       const int su = ((P - m - 1) % 3 + 3) % 3;   // row t-m-1
       const int sd = ((P - m + 1) % 3 + 3) % 3;   // row t-m+1
-      const float4* gr = gp - 2 * m;
+      const int rm = (tg - m) & (DG - 1);         // ring slot of row t-m
       const float4 d2 = m == 1 ? S.d2m1 : S.Win[m - 2][sc];
-      const float4 gv = S.rg[((tg - m) & (DG - 1)) * LANES + lane];
-      const float4 o = level_update(S.lv[m - 1], gr[0], gr[1], S.Win[m - 1][sc], S.Win[m - 1][su],
+      const float4 gv = S.rg[rm * LANES + lane];
+      const float4* kr = S.tab + (rm * K + m - 1) * 2;
+      const float4 o = level_update(S.lv[m - 1], kr[0], kr[1], S.Win[m - 1][sc], S.Win[m - 1][su],
                                     S.Win[m - 1][sd], d2, gv);
       if (m < K) S.Win[m][sc] = o;
       else top = o;
@@ -672,6 +683,9 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, co
   }
   constexpr bool vec = VEC;
   S.d2m1 = a_t;
+  // row t's coefficients, first read at step t+1; they replace row t-DG's
+  table_row(S, t, lane);
+  __syncwarp();
   // leave the pipeline: level kk (and kk-1) at row t - kk (always < J1)
   const int orow = t - (FULL ? K : kk);
   if (orow >= J0 && lane_out) {
@@ -761,7 +775,7 @@ __device__ __forceinline__ void march_band(March& S, int tmin, int t_end, int kk
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(fused::THREADS)
 rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd,
                   const StepParam* __restrict__ sp, const RowGeo<float>* __restrict__ geo,
                   const ShapeConst* __restrict__ shc, const Coef<float>* __restrict__ coef,
@@ -769,7 +783,7 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
                   const float* __restrict__ Dm1, float* __restrict__ Om2, float* __restrict__ Om1,
                   float* __restrict__ polar, int j0, int* __restrict__ status) {
   using namespace fused;
-  __shared__ double sm[kThreads / 32];
+  __shared__ double sm[THREADS / 32];
   __shared__ Coef<float> s_cf[K];
   const Tile tl = tiles[blockIdx.x];
   const int kind = tl.kind & 3;
@@ -802,17 +816,17 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
     float* cur = prv + NB * pitch;                                // level m-1
     for (int i = 0; i < NB; ++i) {
       const int64_t go = (int64_t)(base + i) * pitch, lo = (int64_t)i * pitch;
-      for (int k0 = threadIdx.x; k0 < np; k0 += CU * kThreads) {
+      for (int k0 = threadIdx.x; k0 < np; k0 += CU * THREADS) {
         float vc[CU], va[CU];
 #pragma unroll
         for (int q = 0; q < CU; ++q) {
-          const int k = min(k0 + q * kThreads, np - 1);  // columns past np repeat np-1, not stored
+          const int k = min(k0 + q * THREADS, np - 1);  // columns past np repeat np-1, not stored
           vc[q] = gC[go + k];
           va[q] = zero_m2 ? 0.f : gA[go + k];
         }
 #pragma unroll
         for (int q = 0; q < CU; ++q) {
-          const int k = k0 + q * kThreads;
+          const int k = k0 + q * THREADS;
           if (k < np) {
             cur[lo + k] = vc[q];
             prv[lo + k] = va[q];
@@ -839,11 +853,11 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
         float* pr = prv + (int64_t)i * pitch;
         const float* gr = gG + (int64_t)(base + i) * pitch;
         const RowGeo<float> g = geo[d.geo + base + i];
-        for (int k0 = threadIdx.x; k0 < np; k0 += CU * kThreads) {
+        for (int k0 = threadIdx.x; k0 < np; k0 += CU * THREADS) {
           float vc[CU], vu[CU], vd[CU], vl[CU], vr[CU], vp[CU], vg[CU];
 #pragma unroll
           for (int q = 0; q < CU; ++q) {
-            const int k = min(k0 + q * kThreads, np - 1);
+            const int k = min(k0 + q * THREADS, np - 1);
             vc[q] = cr[k];
             vu[q] = cr[k - pitch];
             vd[q] = cr[k + pitch];
@@ -854,7 +868,7 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
           }
 #pragma unroll
           for (int q = 0; q < CU; ++q) {
-            const int k = k0 + q * kThreads;
+            const int k = k0 + q * THREADS;
             if (k < np) pr[k] = rkl2_point(g, cf, mutdt, vc[q], vu[q], vd[q], vl[q], vr[q], vp[q], vg[q]);
           }
         }
@@ -862,7 +876,7 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
       pole_last = double(cf.mu) * yp + double(cf.nu) * pp + double(cf.mut) * double(nudt) * Lp +
                   double(cf.gsum) * gp;
       const float vpole = float(pole_last);
-      for (int k = threadIdx.x; k < np; k += kThreads) prv[(int64_t)ip * pitch + k] = vpole;
+      for (int k = threadIdx.x; k < np; k += THREADS) prv[(int64_t)ip * pitch + k] = vpole;
       __syncthreads();
       float* t = cur;
       cur = prv;
@@ -872,17 +886,17 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
     bool bad = false;
     for (int i = o_lo; i <= o_hi; ++i) {
       const int64_t go = (int64_t)(base + i) * pitch, lo = (int64_t)i * pitch;
-      for (int k0 = threadIdx.x; k0 < np; k0 += CU * kThreads) {
+      for (int k0 = threadIdx.x; k0 < np; k0 += CU * THREADS) {
         float vc[CU], va[CU];
 #pragma unroll
         for (int q = 0; q < CU; ++q) {
-          const int k = min(k0 + q * kThreads, np - 1);
+          const int k = min(k0 + q * THREADS, np - 1);
           vc[q] = cur[lo + k];
           va[q] = fin ? Bs[go + k] : prv[lo + k];
         }
 #pragma unroll
         for (int q = 0; q < CU; ++q) {
-          const int k = k0 + q * kThreads;
+          const int k = k0 + q * THREADS;
           if (k >= np) continue;
           if (fin) {
             const float v = i == ip ? float(double(va[q]) + pole_last) : va[q] + vc[q];
@@ -931,26 +945,34 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   S.rc = rings + warp * RING_F4;
   S.ra = S.rc + D * LANES;
   S.rg = S.ra + D * LANES;
-  // band geometry as coefficient pairs, rows tmin-K .. tmin-K+GROWS-1 (clamped)
-  float4* sg = rings + WARPS * RING_F4 + warp * 2 * GROWS;
+  // band geometry, rows tmin-K .. tmin-K+GROWS-1 (clamped), then the
+  // coefficient table ring
+  float4* sg = rings + WARPS * RING_F4 + warp * (GROWS + 2 * K * DG);
   S.geo = sg;
+  S.tab = sg + GROWS;
   S.gbase = tmin - K;
   const RowGeo<float>* grow = geo + d.geo;
   for (int i = lane; i < GROWS; i += LANES) {
     const int row = min(max(S.gbase + i, 0), nt - 1);
     const float cN = grow[row].cN, cS = grow[row].cS, cE = grow[row].cE;
-    const float cC = -(cN + cS + 2.f * cE);
-    sg[2 * i] = make_float4(cN, cN, cS, cS);
-    sg[2 * i + 1] = make_float4(cE, cE, cC, cC);
+    sg[i] = make_float4(cN, cS, cE, -(cN + cS + 2.f * cE));
   }
-  __syncwarp();
+  {
+    // lane = 4 (level - 1) + coefficient: a1 = md cN, a2 = md cS, a3 = md cE, a0 = mu + md cC
+    const Coef<float> c = s_cf[lane >> 2];
+    S.kmul = c.mut * nudt;
+    S.kadd = (lane & 3) == 3 ? c.mu : 0.f;
+  }
 #pragma unroll
   for (int m = 0; m < K; ++m) {
     const Coef<float> c = s_cf[m];
-    const float md = c.mut * nudt;
-    S.lv[m] = LevelK{make_float2(c.mu, c.mu), make_float2(md, md), make_float2(c.nu, c.nu),
-                     make_float2(c.gsum, c.gsum)};
+    S.lv[m] = LevelNG{make_float2(c.nu, c.nu), make_float2(c.gsum, c.gsum)};
   }
+  __syncwarp();
+  // coefficients of the K rows above the first loaded one (read by the
+  // pipeline's first steps, whose results never reach an output)
+  for (int r = tmin - K; r < tmin; ++r) table_row(S, r, lane);
+  __syncwarp();
 #pragma unroll
   for (int l = 0; l < K; ++l)
 #pragma unroll
@@ -985,7 +1007,7 @@ cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, c
                               const float* Dm1, float* Om2, float* Om1, float* polar, int j0,
                               int* status) {
   if (n_tiles <= 0) return cudaSuccess;
-  rkl2_fused_kernel<<<n_tiles, kThreads, fused::kSmemBytes, st>>>(tiles, rd, sp, geo, shc, coef, B, G,
+  rkl2_fused_kernel<<<n_tiles, fused::THREADS, fused::kSmemBytes, st>>>(tiles, rd, sp, geo, shc, coef, B, G,
                                                                    Dm2, Dm1, Om2, Om1, polar, j0,
                                                                    status);
   return cudaGetLastError();
