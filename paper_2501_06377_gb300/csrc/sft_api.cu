@@ -82,9 +82,10 @@ struct Config {
   std::vector<double> dt;        // per wave member (wave order)
   std::vector<int> s;            // per wave member
   std::vector<int> tr;           // tile rows per shape at build time
-  int smax = 0, n_adv_tiles = 0;
+  int smax = 0, n_adv_tiles = 0;  // advection tiles (row groups of kAdvRun rows per thread)
   std::vector<int> stage_tiles;  // [j] = tiles launched at RKL2 stage j (1..smax)
-  Tile* d_tiles = nullptr;
+  Tile* d_tiles = nullptr;       // single-stage RKL2 tiles
+  Tile* d_atiles = nullptr;      // advection tiles
   StepParam* d_sp = nullptr;
   void* d_coef = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -416,6 +417,8 @@ void free_config(Config& c, cudaStream_t st) {
   if (c.d_ftiles) cudaFreeAsync(c.d_ftiles, st);
   c.d_ftiles = nullptr;
   if (c.d_tiles) cudaFreeAsync(c.d_tiles, st);
+  if (c.d_atiles) cudaFreeAsync(c.d_atiles, st);
+  c.d_atiles = nullptr;
   if (c.d_sp) cudaFreeAsync(c.d_sp, st);
   if (c.d_coef) cudaFreeAsync(c.d_coef, st);
   c.exec = nullptr;
@@ -534,14 +537,16 @@ std::string check_tiles(const sft_grid* h, const std::vector<Tile>& tiles, bool 
   return "";
 }
 
-void append_tiles(const sft_grid* h, int r, int tr, std::vector<Tile>& tiles) {
+// Interior tiles of TR thread rows x (kThreads/TR) threads; each thread row
+// covers `run` grid rows (1 for the RKL2 stages, kAdvRun for advection).
+void append_tiles(const sft_grid* h, int r, int tr, int run, std::vector<Tile>& tiles) {
   const RealInfo& ri = h->reals[r];
   const ShapeInfo& s = h->shapes[ri.shape];
   const int tx = kThreads / tr;
   int lx = 0;
   while ((1 << lx) < tx) ++lx;
   const int tc = tx * vec_width(h);
-  for (int j0 = 1; j0 <= s.nt - 2; j0 += tr)
+  for (int j0 = 1; j0 <= s.nt - 2; j0 += tr * run)
     for (int k0 = 0; k0 < s.np; k0 += tc) tiles.push_back(Tile{r, j0, k0, lx << 8});
   tiles.push_back(Tile{r, 0, 0, 1});
   tiles.push_back(Tile{r, 0, 0, 2});
@@ -578,7 +583,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
   for (int i = 0; i < nw; ++i)
     if (dt[i] > 0.0) order.push_back(i);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s[a] > s[b]; });
-  std::vector<Tile> tiles;
+  std::vector<Tile> tiles, atiles;
   std::vector<int> tile_end;
   std::vector<StepParam> sp(h->n_real);
   std::memset(sp.data(), 0, sp.size() * sizeof(StepParam));
@@ -587,7 +592,8 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     const int r = w.reals[i];
     const RealInfo& ri = h->reals[r];
     const ShapeInfo& sh = h->shapes[ri.shape];
-    append_tiles(h, r, std::max(1, sh.tile_rows), tiles);
+    append_tiles(h, r, std::max(1, sh.tile_rows), 1, tiles);
+    append_tiles(h, r, std::max(1, sh.tile_rows), kAdvRun, atiles);
     tile_end.push_back((int)tiles.size());
     StepParam& p = sp[r];
     p.dt = dt[i];
@@ -655,7 +661,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
                                   cudaMemcpyHostToDevice, h->stream));
     }
   }
-  c->n_adv_tiles = tile_end.empty() ? 0 : tile_end.back();
+  c->n_adv_tiles = (int)atiles.size();
   c->stage_tiles.assign(c->smax + 1, 0);
   for (int j = 1; j <= c->smax; ++j) {
     int n = 0;
@@ -663,8 +669,14 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     c->stage_tiles[j] = n == 0 ? 0 : tile_end[n - 1];
   }
   {
-    const std::string bad = check_tiles(h, tiles, false);
+    std::string bad = check_tiles(h, tiles, false);
+    if (bad.empty()) bad = check_tiles(h, atiles, false);
     if (!bad.empty()) return fail(h, SFT_ERR_STATE, "internal table check: " + bad);
+  }
+  if (!atiles.empty()) {
+    SFT_CUDA(h, dev_malloc_async(&c->d_atiles, atiles.size() * sizeof(Tile), h->stream));
+    SFT_CUDA(h, cudaMemcpyAsync(c->d_atiles, atiles.data(), atiles.size() * sizeof(Tile),
+                                cudaMemcpyHostToDevice, h->stream));
   }
   if (!tiles.empty()) {
     SFT_CUDA(h, dev_malloc_async(&c->d_tiles, tiles.size() * sizeof(Tile), h->stream));
@@ -731,7 +743,7 @@ sft_status enqueue_adv(sft_handle h, Config& c, cudaStream_t st) {
     S(W0, 1, nullptr, 0, B, 0, 0.0, 1.0, 0.0);  // copy back
   }
   for (auto& s : stages) {
-    SFT_CUDA(h, launch_adv_stage<T>(c.n_adv_tiles, st, c.d_tiles, h->d_desc, c.d_sp, geo, flow, h->d_shc, B, W0,
+    SFT_CUDA(h, launch_adv_stage<T>(c.n_adv_tiles, st, c.d_atiles, h->d_desc, c.d_sp, geo, flow, h->d_shc, B, W0,
                                     W1, s));
   }
   return SFT_OK;
@@ -1010,7 +1022,7 @@ sft_status autotune(sft_handle h, Wave& w) {
     for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci) {
       const int tr = cand[ci];
       std::vector<Tile> tiles;
-      for (int r : members) append_tiles(h, r, tr, tiles);
+      for (int r : members) append_tiles(h, r, tr, 1, tiles);
       cudaFree(d_tiles);
       d_tiles = nullptr;
       if (!check_tiles(h, tiles, false).empty()) {

@@ -21,6 +21,7 @@
 namespace sft {
 
 constexpr int kThreads = 256;
+constexpr int kAdvRun = 8;  // interior rows one advection thread marches through
 
 // ---- Index checks of the debug build (compiled with -DSFT_DEBUG) ----------
 // A kernel checks each index it derives from its tile and descriptor (a row,

@@ -329,22 +329,18 @@ rkl2_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   }
 }
 
-// The divergence part of one advection stage for a thread's N points of row
-// j: o = b R_j - c dt F_A.  ATT: Eq. (flow_attenuation) -- every flux term
-// v B_i carries the cell's factor a_i = 1 - tanh(|B_i| / B_0) (the upwind
-// flux and the advective part of the LLF split); the dissipative alpha B
-// term keeps the unattenuated bound.
+// Face fluxes of one advection stage.  ATT: Eq. (flow_attenuation) -- every
+// flux term v B_i carries the cell's factor a_i = 1 - tanh(|B_i| / B_0) (the
+// upwind flux and the advective part of the LLF split); the dissipative
+// alpha B term keeps the unattenuated bound.
+//
+// phi faces k-1/2 of a thread's N points, k = kc .. kc+N, from the row's
+// values e (columns kc-2 .. kc+N+1) and v_phi of the row.
 template <typename T, int N, bool ATT>
-__device__ __forceinline__ void adv_divergence(const StepParam& p, const RowGeo<T>& g, const RowFlow<T> (&fl)[5],
-                                               const T (&R)[5][N], const T (&e)[N + 4], int j, int nt, T sb,
-                                               T cdt, T auw, T (&o)[N]) {
+__device__ __forceinline__ void phi_faces(const StepParam& p, T v, const T (&e)[N + 4], T auw, T (&F)[N + 1]) {
   const T ib0 = T(p.inv_b0);
   auto att = [&](T x) -> T { return ATT ? T(1) - tanh(fabs(x) * ib0) : T(1); };
-  const bool weno = p.weno != 0;
-  // phi faces k-1/2, k = kc .. kc+N
-  T F[N + 1];
-  const T v = fl[2].vp;
-  if (weno) {
+  if (p.weno != 0) {
     const T eps = T(p.eps_p);
     const T av = fabs(v);
     if (ATT) {
@@ -369,36 +365,32 @@ __device__ __forceinline__ void adv_divergence(const StepParam& p, const RowGeo<
       F[i] = ATT ? uw_flux(v, att(e[i + 1]) * e[i + 1], att(e[i + 2]) * e[i + 2], auw)
                  : uw_flux(v, e[i + 1], e[i + 2], auw);
   }
-  // theta faces j-1/2 (f = j-1) and j+1/2 (f = j)
-  const bool wdn = weno && (j - 1 >= 2) && (j - 1 <= nt - 4);
-  const bool wup = weno && (j >= 2) && (j <= nt - 4);
-  const T eps = T(p.eps_t);
-  // LLF parts of cell m of the five-row window: LM uses v at its lower face, LP at its upper
+}
+
+// theta face f+1/2 of a thread's N columns from rows f-1 .. f+2 (values R,
+// flow rows fl, clamped to the interior): WENO3-CS(h) with the LLF split (LM
+// uses v at a cell's lower face, LP at its upper) when `weno`, else UW with
+// vface, v_theta at the face (taken from an unclamped row by the caller).
+template <typename T, int N, bool ATT>
+__device__ __forceinline__ void theta_face(const StepParam& p, const RowFlow<T> (&fl)[4], const T (&R)[4][N],
+                                           bool weno, T vface, T auw, T (&F)[N]) {
+  const T ib0 = T(p.inv_b0);
+  auto att = [&](T x) -> T { return ATT ? T(1) - tanh(fabs(x) * ib0) : T(1); };
   auto LM = [&](int m, T b) -> T {
     return ATT ? T(0.5) * (fl[m].vdn * att(b) * b + fl[m].alpha * b) : T(0.5) * b * (fl[m].vdn + fl[m].alpha);
   };
   auto LP = [&](int m, T b) -> T {
     return ATT ? T(0.5) * (fl[m].vup * att(b) * b - fl[m].alpha * b) : T(0.5) * b * (fl[m].vup - fl[m].alpha);
   };
+  const T eps = T(p.eps_t);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    T Fdn, Fup;
-    if (wdn) {
-      Fdn = weno_flux(LM(0, R[0][i]), LM(1, R[1][i]), LM(2, R[2][i]), LP(1, R[1][i]), LP(2, R[2][i]),
-                      LP(3, R[3][i]), eps);
-    } else {
-      Fdn = ATT ? uw_flux(fl[2].vdn, att(R[1][i]) * R[1][i], att(R[2][i]) * R[2][i], auw)
-                : uw_flux(fl[2].vdn, R[1][i], R[2][i], auw);
-    }
-    if (wup) {
-      Fup = weno_flux(LM(1, R[1][i]), LM(2, R[2][i]), LM(3, R[3][i]), LP(2, R[2][i]), LP(3, R[3][i]),
-                      LP(4, R[4][i]), eps);
-    } else {
-      Fup = ATT ? uw_flux(fl[2].vup, att(R[2][i]) * R[2][i], att(R[3][i]) * R[3][i], auw)
-                : uw_flux(fl[2].vup, R[2][i], R[3][i], auw);
-    }
-    const T div = (g.sup * Fup - g.sdn * Fdn) * g.inv_sdth + (F[i + 1] - F[i]) * g.inv_sdph;
-    o[i] = sb * R[2][i] - cdt * div;
+    if (weno)
+      F[i] = weno_flux(LM(0, R[0][i]), LM(1, R[1][i]), LM(2, R[2][i]), LP(1, R[1][i]), LP(2, R[2][i]),
+                       LP(3, R[3][i]), eps);
+    else
+      F[i] = ATT ? uw_flux(vface, att(R[1][i]) * R[1][i], att(R[2][i]) * R[2][i], auw)
+                 : uw_flux(vface, R[1][i], R[2][i], auw);
   }
 }
 
@@ -455,53 +447,97 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
     return;
   }
 
+  // interior: thread (ty, tx) marches rows jb .. jb+kAdvRun-1 (< nt-1) over
+  // its N columns; the theta face between two rows is computed once, as the
+  // upper face of the first and carried as the lower face of the second
   const int ty = threadIdx.x >> lx, tx = threadIdx.x & ((1 << lx) - 1), lane = threadIdx.x & 31;
-  int j = tl.j0 + ty;
-  if (j > nt - 2) return;
-  SFT_DCHECK(DBG_ADV_ROW, j, 1, nt - 2);
+  int jb = tl.j0 + ty * kAdvRun;
+  if (jb > nt - 2) return;  // a warp lies within one row group: uniform exit
+  SFT_DCHECK(DBG_ADV_ROW, jb, 1, nt - 2);
+  const int je = min(jb + kAdvRun, nt - 1);
   int kc = tl.k0 + tx * N;
   if (kc < np) SFT_DCHECK(DBG_ADV_COL, kc, 0, min(np - 1, pitch - N));
-  const int64_t ro = (int64_t)j * pitch;
+  const bool act = kc < np;
+  const bool weno = p.weno != 0;
+  // five-row windows: values of rows j-2 .. j+2 (clamped to the grid) and
+  // flow rows (clamped to the interior)
   T R[5][N];
-  if (kc < np) {
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      int jj = j - 2 + m;
-      jj = jj < 0 ? 0 : (jj > nt - 1 ? nt - 1 : jj);
-      Vec<T>::ldg(fin + (int64_t)jj * pitch + kc, R[m]);
-    }
-  } else {
-#pragma unroll
-    for (int m = 0; m < 5; ++m)
+  RowFlow<T> fl[5];
+  auto load_row = [&](int m, int jj) {
+    const int jr = jj < 0 ? 0 : (jj > nt - 1 ? nt - 1 : jj);
+    if (act) {
+      Vec<T>::ldg(fin + (int64_t)jr * pitch + kc, R[m]);
+    } else {
 #pragma unroll
       for (int i = 0; i < N; ++i) R[m][i] = T(0);
-  }
-  T e[N + 4];
-  row_ext<T, N, 2>(fin + ro, kc, np, lane, R[2], e);
-  if (kc >= np) return;
-  T o[N];
-  if (s.c == T(0)) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) o[i] = s.b * R[2][i];
-  } else {
-    const RowGeo<T> g = geo[d.geo + j];
-    RowFlow<T> fl[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      int jj = j - 2 + m;
-      jj = jj < 1 ? 1 : (jj > nt - 2 ? nt - 2 : jj);
-      fl[m] = flow[d.flow + jj];
     }
-    if (p.inv_b0 != 0.0) adv_divergence<T, N, true>(p, g, fl, R, e, j, nt, s.b, cdt, auw, o);
-    else adv_divergence<T, N, false>(p, g, fl, R, e, j, nt, s.b, cdt, auw, o);
-  }
-  if (fn != nullptr && s.a != T(0)) {
-    T f0[N];
-    Vec<T>::ld(fn + ro + kc, f0);
+    const int jf = jj < 1 ? 1 : (jj > nt - 2 ? nt - 2 : jj);
+    fl[m] = flow[d.flow + jf];
+  };
 #pragma unroll
-    for (int i = 0; i < N; ++i) o[i] += s.a * f0[i];
+  for (int m = 0; m < 4; ++m) load_row(m, jb - 2 + m);
+  T Fdn[N];
+  if (s.c != T(0) && act) {
+    const RowFlow<T> f4[4] = {fl[0], fl[1], fl[2], fl[3]};
+    T R4[4][N];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int i = 0; i < N; ++i) R4[m][i] = R[m][i];
+    const bool wdn = weno && (jb - 1 >= 2) && (jb - 1 <= nt - 4);
+    // the lower face of row jb: v from row jb's own table (row jb-1 may be a pole)
+    if (p.inv_b0 != 0.0) theta_face<T, N, true>(p, f4, R4, wdn, fl[2].vdn, auw, Fdn);
+    else theta_face<T, N, false>(p, f4, R4, wdn, fl[2].vdn, auw, Fdn);
   }
-  Vec<T>::st(out + ro + kc, o);
+  for (int j = jb; j < je; ++j) {
+    load_row(4, j + 2);
+    const int64_t ro = (int64_t)j * pitch;
+    T e[N + 4];
+    row_ext<T, N, 2>(fin + ro, kc, np, lane, R[2], e);
+    if (act) {
+      T o[N];
+      if (s.c == T(0)) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = s.b * R[2][i];
+      } else {
+        const RowGeo<T> g = geo[d.geo + j];
+        const RowFlow<T> f4[4] = {fl[1], fl[2], fl[3], fl[4]};
+        T R4[4][N];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+          for (int i = 0; i < N; ++i) R4[m][i] = R[m + 1][i];
+        const bool wup = weno && (j >= 2) && (j <= nt - 4);
+        T F[N + 1], Fup[N];
+        if (p.inv_b0 != 0.0) {
+          phi_faces<T, N, true>(p, fl[2].vp, e, auw, F);
+          theta_face<T, N, true>(p, f4, R4, wup, fl[2].vup, auw, Fup);
+        } else {
+          phi_faces<T, N, false>(p, fl[2].vp, e, auw, F);
+          theta_face<T, N, false>(p, f4, R4, wup, fl[2].vup, auw, Fup);
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const T div = (g.sup * Fup[i] - g.sdn * Fdn[i]) * g.inv_sdth + (F[i + 1] - F[i]) * g.inv_sdph;
+          o[i] = s.b * R[2][i] - cdt * div;
+          Fdn[i] = Fup[i];
+        }
+      }
+      if (fn != nullptr && s.a != T(0)) {
+        T f0[N];
+        Vec<T>::ld(fn + ro + kc, f0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] += s.a * f0[i];
+      }
+      Vec<T>::st(out + ro + kc, o);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      fl[m] = fl[m + 1];
+#pragma unroll
+      for (int i = 0; i < N; ++i) R[m][i] = R[m + 1][i];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
