@@ -140,6 +140,7 @@ struct sft_grid {
   RowGeoD* d_geod = nullptr;
   double* d_cosp = nullptr;
   double* d_sinp = nullptr;
+  float4* d_csf = nullptr;     // cos / sin phi as (hi, lo) float pairs
   void* d_flow = nullptr;      // RowFlow<T>
   int* d_status = nullptr;
   RedTile* d_rtiles = nullptr;
@@ -442,6 +443,7 @@ void free_handle(sft_handle h) {
   cudaFree(h->d_geod);
   cudaFree(h->d_cosp);
   cudaFree(h->d_sinp);
+  cudaFree(h->d_csf);
   cudaFree(h->d_flow);
   cudaFree(h->d_status);
   cudaFree(h->d_rtiles);
@@ -1098,6 +1100,15 @@ sft_status upload_tables(sft_handle h) {
   SFT_CUDA(h, cudaMemcpy(h->d_cosp, cp.data(), cp.size() * sizeof(double), cudaMemcpyHostToDevice));
   SFT_CUDA(h, dev_malloc(&h->d_sinp, sp.size() * sizeof(double)));
   SFT_CUDA(h, cudaMemcpy(h->d_sinp, sp.data(), sp.size() * sizeof(double), cudaMemcpyHostToDevice));
+  {
+    std::vector<float4> cf(cp.size());
+    for (size_t i = 0; i < cp.size(); ++i) {
+      const float ch = (float)cp[i], sh = (float)sp[i];
+      cf[i] = make_float4(ch, (float)(cp[i] - (double)ch), sh, (float)(sp[i] - (double)sh));
+    }
+    SFT_CUDA(h, dev_malloc(&h->d_csf, cf.size() * sizeof(float4)));
+    SFT_CUDA(h, cudaMemcpy(h->d_csf, cf.data(), cf.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  }
   SFT_CUDA(h, dev_malloc(&h->d_shc, sc.size() * sizeof(ShapeConst)));
   SFT_CUDA(h, cudaMemcpy(h->d_shc, sc.data(), sc.size() * sizeof(ShapeConst), cudaMemcpyHostToDevice));
   // flow tables: one block of nt rows per realization (filled by sft_set_flows)
@@ -1201,7 +1212,7 @@ sft_status set_flows_t(sft_handle h, const sft_flow_params* params) {
 template <typename T>
 sft_status reduce_fold(sft_handle h, int mode, double lat_cut, AssimArgs aa) {
   SFT_CUDA(h, launch_reduce<T>(mode, h->n_rtiles, h->stream, h->d_rtiles, h->d_desc, h->d_geod,
-                               h->d_cosp, h->d_sinp, ptr<const T>(h->state), lat_cut, aa,
+                               h->d_cosp, h->d_sinp, h->d_csf, ptr<const T>(h->state), lat_cut, aa,
                                h->d_partials));
   SFT_CUDA(h, launch_fold(mode, h->n_real, h->stream, h->d_rstart, h->d_partials, aa.wpar, h->d_red));
   return SFT_OK;

@@ -244,10 +244,12 @@ struct AssimArgs {
 };
 
 template <typename T>
+// cosp / sinp: cos, sin phi_k (FP64); csf: the same as (cos hi, cos lo,
+// sin hi, sin lo) float pairs, hi + lo = the FP64 value (FP32 states).
 cudaError_t launch_reduce(int mode, int n_tiles, cudaStream_t st, const RedTile* tiles,
                           const RealDesc* rd, const RowGeoD* geod, const double* cosp,
-                          const double* sinp, const T* state, double lat_cut, AssimArgs aa,
-                          double* partials);
+                          const double* sinp, const float4* csf, const T* state, double lat_cut,
+                          AssimArgs aa, double* partials);
 template <typename T>
 cudaError_t launch_rfe_sums(int n_tiles, cudaStream_t st, const RedTile* tiles, const RealDesc* rd,
                             const RowGeoD* geod, const RfeStep* rs, double* partials);

@@ -1091,12 +1091,43 @@ __device__ double block_min(double v, double* sm) {
 
 }  // namespace
 
+// Error-free transformations in FP32 (Knuth's TwoSum; the FMA form of
+// Dekker's TwoProduct): s + e equals a + b exactly, p + e equals a * b.
+// The _rn intrinsics keep the compiler from contracting a product into
+// these sums (an FMA there would break exactness).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// A compensated FP32 sum (Ogita, Rump and Oishi's Sum2): s + c tracks the
+// exact sum of the added terms; the error of c is of order n^2 u^2 sum |x|
+// for n terms (u = 2^-24), about 2e-13 sum |x| for a thread's 8 terms.
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float e;
+    two_sum(s, x, s, e);
+    c += e;
+  }
+  // x * (hi + lo), with hi + lo an FP64 value split into two floats
+  __device__ __forceinline__ void add_product(float x, float hi, float lo) {
+    const float p = __fmul_rn(x, hi);
+    const float ep = fmaf(x, hi, -p);  // x * hi - p, exactly
+    float e;
+    two_sum(s, p, s, e);
+    c += e + fmaf(x, lo, ep);
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __restrict__ rd,
               const RowGeoD* __restrict__ geod, const double* __restrict__ cosp,
-              const double* __restrict__ sinp, const T* __restrict__ state, double lat_cut,
-              AssimArgs aa, double* __restrict__ partials) {
+              const double* __restrict__ sinp, const float4* __restrict__ csf, const T* __restrict__ state,
+              double lat_cut, AssimArgs aa, double* __restrict__ partials) {
   __shared__ double sm[kThreads / 32];
   const RedTile tl = tiles[blockIdx.x];
   const RealDesc d = rd[tl.r];
@@ -1120,21 +1151,48 @@ reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __res
       // sums once: per cell only sum x, sum max(x, 0), sum x cos(phi) and
       // sum x sin(phi) run in FP64 (min / max are exact in T).
       double rs = 0.0, rp = 0.0, rc = 0.0, rn = 0.0;
-      for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
-        const T bv = row[k];
-        if (!isfinite(bv)) {
-          acc[10] += 1.0;
-          continue;
+      if constexpr (sizeof(T) == 4) {
+        // FP32 state: the thread's row sums as compensated FP32 sums (GB300's
+        // FP64 pipe is narrow), cos / sin phi as hi + lo float pairs; FP64
+        // from the row sums on
+        CSum ss, sp, sc, sn;
+        for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+          const float bv = float(row[k]);
+          if (!isfinite(bv)) {
+            acc[10] += 1.0;
+            continue;
+          }
+          const float4 cs = csf[d.col + k];  // (cos hi, cos lo, sin hi, sin lo)
+          ss.add(bv);
+          sp.add(bv > 0.f ? bv : 0.f);
+          sc.add_product(bv, cs.x, cs.y);
+          sn.add_product(bv, cs.z, cs.w);
+          tmn = bv < tmn ? bv : tmn;
+          tmx = bv > tmx ? bv : tmx;
+          const float ab = bv < 0.f ? -bv : bv;
+          tamn = ab < tamn ? ab : tamn;
         }
-        const double x = double(bv);
-        rs += x;
-        rp += bv > T(0) ? x : 0.0;
-        rc = fma(x, cosp[d.col + k], rc);
-        rn = fma(x, sinp[d.col + k], rn);
-        tmn = bv < tmn ? bv : tmn;
-        tmx = bv > tmx ? bv : tmx;
-        const T ab = bv < T(0) ? -bv : bv;
-        tamn = ab < tamn ? ab : tamn;
+        rs = ss.value();
+        rp = sp.value();
+        rc = sc.value();
+        rn = sn.value();
+      } else {
+        for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+          const T bv = row[k];
+          if (!isfinite(bv)) {
+            acc[10] += 1.0;
+            continue;
+          }
+          const double x = double(bv);
+          rs += x;
+          rp += bv > T(0) ? x : 0.0;
+          rc = fma(x, cosp[d.col + k], rc);
+          rn = fma(x, sinp[d.col + k], rn);
+          tmn = bv < tmn ? bv : tmn;
+          tmx = bv > tmx ? bv : tmx;
+          const T ab = bv < T(0) ? -bv : bv;
+          tamn = ab < tamn ? ab : tamn;
+        }
       }
       acc[0] += gd.area * rs;
       acc[1] += gd.area * rp;
@@ -1435,10 +1493,10 @@ cudaError_t launch_fix_poles(int n_real, cudaStream_t st, const RealDesc* rd, T*
 template <typename T>
 cudaError_t launch_reduce(int mode, int n_tiles, cudaStream_t st, const RedTile* tiles,
                           const RealDesc* rd, const RowGeoD* geod, const double* cosp,
-                          const double* sinp, const T* state, double lat_cut, AssimArgs aa,
-                          double* partials) {
+                          const double* sinp, const float4* csf, const T* state, double lat_cut,
+                          AssimArgs aa, double* partials) {
   if (n_tiles <= 0) return cudaSuccess;
-  reduce_kernel<T><<<n_tiles, kThreads, 0, st>>>(mode, tiles, rd, geod, cosp, sinp, state, lat_cut,
+  reduce_kernel<T><<<n_tiles, kThreads, 0, st>>>(mode, tiles, rd, geod, cosp, sinp, csf, state, lat_cut,
                                                  aa, partials);
   return cudaGetLastError();
 }
@@ -1491,8 +1549,8 @@ cudaError_t launch_apply(int mode, int n_tiles, cudaStream_t st, const RedTile* 
                                            const ShapeConst*, T*, T*, T*, AdvStage<T>);           \
   template cudaError_t launch_fix_poles<T>(int, cudaStream_t, const RealDesc*, T*, int);          \
   template cudaError_t launch_reduce<T>(int, int, cudaStream_t, const RedTile*, const RealDesc*,  \
-                                        const RowGeoD*, const double*, const double*, const T*,   \
-                                        double, AssimArgs, double*);                              \
+                                        const RowGeoD*, const double*, const double*,             \
+                                        const float4*, const T*, double, AssimArgs, double*);     \
   template cudaError_t launch_apply<T>(int, int, cudaStream_t, const RedTile*, const RealDesc*,   \
                                        const RowGeoD*, T*, AssimArgs, const double*);             \
   template cudaError_t launch_rfe_sums<T>(int, cudaStream_t, const RedTile*, const RealDesc*,     \

@@ -48,7 +48,7 @@ std::atomic<void*> g_scratch_addr[kMaxDevices];
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t desc, tiles, start, geod, cosp, sinp, partials, out, total;
+  size_t desc, tiles, start, geod, cosp, sinp, csf, partials, out, total;
   int n_tiles, band;
 };
 
@@ -63,6 +63,7 @@ Layout layout(int nt, int np) {
   L.geod = o;     o = align256(o + (size_t)nt * sizeof(RowGeoD));
   L.cosp = o;     o = align256(o + (size_t)np * sizeof(double));
   L.sinp = o;     o = align256(o + (size_t)np * sizeof(double));
+  L.csf = o;      o = align256(o + (size_t)np * sizeof(float4));
   L.partials = o; o = align256(o + (size_t)L.n_tiles * kDiagFields * sizeof(double));
   L.out = o;      o = align256(o + kDiagFields * sizeof(double));
   L.total = o;
@@ -106,9 +107,13 @@ __global__ void noalloc_tables_kernel(unsigned char* base, Layout L, int nt, int
   }
   double* cp = reinterpret_cast<double*>(base + L.cosp);
   double* sp = reinterpret_cast<double*>(base + L.sinp);
+  float4* cf = reinterpret_cast<float4*>(base + L.csf);
   for (int k = tid; k < np; k += nth) {
-    cp[k] = cos(k * dph);
-    sp[k] = sin(k * dph);
+    const double c = cos(k * dph), s = sin(k * dph);
+    cp[k] = c;
+    sp[k] = s;
+    const float ch = (float)c, sh = (float)s;
+    cf[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
   }
 }
 
@@ -155,14 +160,15 @@ extern "C" sft_status sft_flux_diagnostics_noalloc(const void* br_device, int32_
   const auto* geod = reinterpret_cast<const RowGeoD*>(b + L.geod);
   const auto* cosp = reinterpret_cast<const double*>(b + L.cosp);
   const auto* sinp = reinterpret_cast<const double*>(b + L.sinp);
+  const auto* csf = reinterpret_cast<const float4*>(b + L.csf);
   auto* partials = reinterpret_cast<double*>(b + L.partials);
   auto* res = reinterpret_cast<double*>(b + L.out);
   const double cut = lat_cut_deg * 3.14159265358979323846 / 180.0;
   AssimArgs aa{nullptr, nullptr, nullptr, nullptr};
   e = prec == SFT_FP32
-          ? launch_reduce<float>(RED_DIAG, L.n_tiles, st, tiles, desc, geod, cosp, sinp,
+          ? launch_reduce<float>(RED_DIAG, L.n_tiles, st, tiles, desc, geod, cosp, sinp, csf,
                                  static_cast<const float*>(br_device), cut, aa, partials)
-          : launch_reduce<double>(RED_DIAG, L.n_tiles, st, tiles, desc, geod, cosp, sinp,
+          : launch_reduce<double>(RED_DIAG, L.n_tiles, st, tiles, desc, geod, cosp, sinp, csf,
                                   static_cast<const double*>(br_device), cut, aa, partials);
   if (e != cudaSuccess) return noalloc_fail(SFT_ERR_CUDA, std::string("reduce: ") + cudaGetErrorString(e));
   e = launch_fold(RED_DIAG, 1, st, reinterpret_cast<const int*>(b + L.start), partials, nullptr, res);
