@@ -76,8 +76,14 @@ struct Config {
   // streams (realizations dealt alternately from the stage-sorted order), so
   // one chain's launch fills the SMs while the other's drains.
   int n_chains = 1;
+  // A chain's tiles are its members' cap blocks (two per member, in member
+  // order), then their interior blocks: a pass launches the caps of its
+  // active members first (dispatched in the first wave: a cap block runs
+  // longest) and then their interior blocks.
   int fbase[kMaxChains] = {};                 // first tile of each chain in d_ftiles
+  int fcaps[kMaxChains] = {};                 // cap tiles of each chain (the interior starts there)
   std::vector<int> fused_tiles[kMaxChains];   // [chain][j0] = tiles launched by the pass starting at stage j0
+  std::vector<int> fused_caps[kMaxChains];    // [chain][j0] = of which cap tiles
   int64_t fused_launches = 0;           // non-empty fused launches per step
   std::vector<double> dt;        // per wave member (wave order)
   std::vector<int> s;            // per wave member
@@ -554,10 +560,13 @@ void append_tiles(const sft_grid* h, int r, int tr, int run, std::vector<Tile>& 
   tiles.push_back(Tile{r, 0, 0, 2});
 }
 
-void append_fused_tiles(const sft_grid* h, int r, std::vector<Tile>& tiles) {
-  const ShapeInfo& s = h->shapes[h->reals[r].shape];
+void append_fused_caps(int r, std::vector<Tile>& tiles) {
   tiles.push_back(Tile{r, 0, 0, 1});
   tiles.push_back(Tile{r, 0, 0, 2});
+}
+
+void append_fused_interior(const sft_grid* h, int r, std::vector<Tile>& tiles) {
+  const ShapeInfo& s = h->shapes[h->reals[r].shape];
   // interior: (band, strip) work items, one per warp, WARPS per block
   const int n_strips = (s.np + fused::STRIP - 1) / fused::STRIP;
   const int n_bands = (s.nt - 2 - 2 * fused::PB + fused::BAND - 1) / fused::BAND;
@@ -629,24 +638,31 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     size_t pass_tiles = 0;
     {
       std::vector<Tile> tmp;
-      for (int i : order) append_fused_tiles(h, w.reals[i], tmp);
+      for (int i : order) {
+        append_fused_caps(w.reals[i], tmp);
+        append_fused_interior(h, w.reals[i], tmp);
+      }
       pass_tiles = tmp.size();
     }
     c->n_chains = pass_tiles >= (size_t)4 * h->n_sm ? std::min<int>(kMaxChains, (int)order.size()) : 1;
     std::vector<Tile> ft;
     for (int ch = 0; ch < c->n_chains; ++ch) {
       c->fbase[ch] = (int)ft.size();
-      std::vector<int> mem, fend;  // chain members (descending s) and their tile ends
+      std::vector<int> mem, fend;  // chain members (descending s) and their interior tile ends
       for (size_t q = ch; q < order.size(); q += c->n_chains) mem.push_back(order[q]);
+      for (int i : mem) append_fused_caps(w.reals[i], ft);
+      c->fcaps[ch] = (int)ft.size() - c->fbase[ch];
       for (int i : mem) {
-        append_fused_tiles(h, w.reals[i], ft);
-        fend.push_back((int)ft.size() - c->fbase[ch]);
+        append_fused_interior(h, w.reals[i], ft);
+        fend.push_back((int)ft.size() - c->fbase[ch] - c->fcaps[ch]);
       }
       c->fused_tiles[ch].assign(c->smax + 1, 0);
+      c->fused_caps[ch].assign(c->smax + 1, 0);
       for (int j0 = 2; j0 <= c->smax; j0 += fused::K) {
         int n = 0;
         while (n < (int)mem.size() && s[mem[n]] >= j0) ++n;
-        c->fused_tiles[ch][j0] = n == 0 ? 0 : fend[n - 1];
+        c->fused_caps[ch][j0] = 2 * n;
+        c->fused_tiles[ch][j0] = n == 0 ? 0 : 2 * n + fend[n - 1];
         if (n > 0) c->fused_launches += 1;
       }
     }
@@ -794,7 +810,8 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
       int in = 0;  // input pair (P[in], P[in+1]) = (delta_{j0-2}, delta_{j0-1})
       for (int j0 = 2; j0 <= c.smax; j0 += fused::K) {
         const int out = 2 - in;
-        SFT_CUDA(h, launch_rkl2_fused(c.fused_tiles[ch][j0], cs, c.d_ftiles + c.fbase[ch], h->d_desc,
+        SFT_CUDA(h, launch_rkl2_fused(c.fused_tiles[ch][j0], c.fused_caps[ch][j0], c.fcaps[ch], cs,
+                                      c.d_ftiles + c.fbase[ch], h->d_desc,
                                       c.d_sp, ptr<const RowGeo<float>>(h->d_geo), h->d_shc,
                                       ptr<const Coef<float>>(c.d_coef), ptr<float>(h->state),
                                       ptr<const float>(h->work[0]), P[in], P[in + 1], P[out],

@@ -199,8 +199,11 @@ inline bool shape_ok(int nt, int np) { return nt >= 2 * NB + 2 && np >= 16; }
 // Stages j0 .. j0+K-1 of every realization with s >= j0 (fewer, ending with
 // the final write B += delta_s, for a realization whose s ends inside the
 // pass).  Reads delta_{j0-2} (Dm2, zero when j0 == 2), delta_{j0-1} (Dm1), G;
-// writes delta_{j0+K-2} (Om2) and delta_{j0+K-1} (Om1).
-cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+// writes delta_{j0+K-2} (Om2) and delta_{j0+K-1} (Om1).  The launch runs
+// n_tiles blocks: the first n_caps over tiles[0 .. n_caps), the rest over the
+// interior tiles from tiles[cap_total] on.
+cudaError_t launch_rkl2_fused(int n_tiles, int n_caps, int cap_total, cudaStream_t st, const Tile* tiles,
+                              const RealDesc* rd,
                               const StepParam* sp, const RowGeo<float>* geo, const ShapeConst* shc,
                               const Coef<float>* coef, float* B, const float* G, const float* Dm2,
                               const float* Dm1, float* Om2, float* Om1, float* polar, int j0,

@@ -334,14 +334,24 @@ rkl2_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
 // upwind flux and the advective part of the LLF split); the dissipative
 // alpha B term keeps the unattenuated bound.
 //
+// A realization's advection constants in the state's type, converted once
+// per thread (FP64 conversions run on GB300's narrow FP64 pipe).
+template <typename T> struct AdvConst {
+  T ib0, eps_p, eps_t, auw;
+  bool weno, att;
+  __device__ explicit AdvConst(const StepParam& p)
+      : ib0(T(p.inv_b0)), eps_p(T(p.eps_p)), eps_t(T(p.eps_t)), auw(T(p.alpha_uw)),
+        weno(p.weno != 0), att(p.inv_b0 != 0.0) {}
+};
+
 // phi faces k-1/2 of a thread's N points, k = kc .. kc+N, from the row's
 // values e (columns kc-2 .. kc+N+1) and v_phi of the row.
 template <typename T, int N, bool ATT>
-__device__ __forceinline__ void phi_faces(const StepParam& p, T v, const T (&e)[N + 4], T auw, T (&F)[N + 1]) {
-  const T ib0 = T(p.inv_b0);
+__device__ __forceinline__ void phi_faces(const AdvConst<T>& q, T v, const T (&e)[N + 4], T (&F)[N + 1]) {
+  const T ib0 = q.ib0, auw = q.auw;
   auto att = [&](T x) -> T { return ATT ? T(1) - tanh(fabs(x) * ib0) : T(1); };
-  if (p.weno != 0) {
-    const T eps = T(p.eps_p);
+  if (q.weno) {
+    const T eps = q.eps_p;
     const T av = fabs(v);
     if (ATT) {
       T lm[N + 4], lp[N + 4];
@@ -372,9 +382,9 @@ __device__ __forceinline__ void phi_faces(const StepParam& p, T v, const T (&e)[
 // uses v at a cell's lower face, LP at its upper) when `weno`, else UW with
 // vface, v_theta at the face (taken from an unclamped row by the caller).
 template <typename T, int N, bool ATT>
-__device__ __forceinline__ void theta_face(const StepParam& p, const RowFlow<T> (&fl)[4], const T (&R)[4][N],
-                                           bool weno, T vface, T auw, T (&F)[N]) {
-  const T ib0 = T(p.inv_b0);
+__device__ __forceinline__ void theta_face(const AdvConst<T>& q, const RowFlow<T> (&fl)[4], const T (&R)[4][N],
+                                           bool weno, T vface, T (&F)[N]) {
+  const T ib0 = q.ib0, auw = q.auw;
   auto att = [&](T x) -> T { return ATT ? T(1) - tanh(fabs(x) * ib0) : T(1); };
   auto LM = [&](int m, T b) -> T {
     return ATT ? T(0.5) * (fl[m].vdn * att(b) * b + fl[m].alpha * b) : T(0.5) * b * (fl[m].vdn + fl[m].alpha);
@@ -382,7 +392,7 @@ __device__ __forceinline__ void theta_face(const StepParam& p, const RowFlow<T> 
   auto LP = [&](int m, T b) -> T {
     return ATT ? T(0.5) * (fl[m].vup * att(b) * b - fl[m].alpha * b) : T(0.5) * b * (fl[m].vup - fl[m].alpha);
   };
-  const T eps = T(p.eps_t);
+  const T eps = q.eps_t;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (weno)
@@ -458,7 +468,8 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
   int kc = tl.k0 + tx * N;
   if (kc < np) SFT_DCHECK(DBG_ADV_COL, kc, 0, min(np - 1, pitch - N));
   const bool act = kc < np;
-  const bool weno = p.weno != 0;
+  const AdvConst<T> q(p);
+  const bool weno = q.weno;
   // five-row windows: values of rows j-2 .. j+2 (clamped to the grid) and
   // flow rows (clamped to the interior)
   T R[5][N];
@@ -486,8 +497,8 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
       for (int i = 0; i < N; ++i) R4[m][i] = R[m][i];
     const bool wdn = weno && (jb - 1 >= 2) && (jb - 1 <= nt - 4);
     // the lower face of row jb: v from row jb's own table (row jb-1 may be a pole)
-    if (p.inv_b0 != 0.0) theta_face<T, N, true>(p, f4, R4, wdn, fl[2].vdn, auw, Fdn);
-    else theta_face<T, N, false>(p, f4, R4, wdn, fl[2].vdn, auw, Fdn);
+    if (q.att) theta_face<T, N, true>(q, f4, R4, wdn, fl[2].vdn, Fdn);
+    else theta_face<T, N, false>(q, f4, R4, wdn, fl[2].vdn, Fdn);
   }
   for (int j = jb; j < je; ++j) {
     load_row(4, j + 2);
@@ -509,12 +520,12 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
           for (int i = 0; i < N; ++i) R4[m][i] = R[m + 1][i];
         const bool wup = weno && (j >= 2) && (j <= nt - 4);
         T F[N + 1], Fup[N];
-        if (p.inv_b0 != 0.0) {
-          phi_faces<T, N, true>(p, fl[2].vp, e, auw, F);
-          theta_face<T, N, true>(p, f4, R4, wup, fl[2].vup, auw, Fup);
+        if (q.att) {
+          phi_faces<T, N, true>(q, fl[2].vp, e, F);
+          theta_face<T, N, true>(q, f4, R4, wup, fl[2].vup, Fup);
         } else {
-          phi_faces<T, N, false>(p, fl[2].vp, e, auw, F);
-          theta_face<T, N, false>(p, f4, R4, wup, fl[2].vup, auw, Fup);
+          phi_faces<T, N, false>(q, fl[2].vp, e, F);
+          theta_face<T, N, false>(q, f4, R4, wup, fl[2].vup, Fup);
         }
 #pragma unroll
         for (int i = 0; i < N; ++i) {
@@ -812,7 +823,7 @@ __device__ __forceinline__ void march_band(March& S, int tmin, int t_end, int kk
 }  // namespace
 
 __global__ void __launch_bounds__(fused::THREADS)
-rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd,
+rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const RealDesc* __restrict__ rd,
                   const StepParam* __restrict__ sp, const RowGeo<float>* __restrict__ geo,
                   const ShapeConst* __restrict__ shc, const Coef<float>* __restrict__ coef,
                   float* __restrict__ B, const float* __restrict__ G, const float* __restrict__ Dm2,
@@ -821,7 +832,8 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   using namespace fused;
   __shared__ double sm[THREADS / 32];
   __shared__ Coef<float> s_cf[K];
-  const Tile tl = tiles[blockIdx.x];
+  // blocks 0 .. n_caps-1: cap tiles; the rest: interior tiles after all the chain's caps
+  const Tile tl = tiles[(int)blockIdx.x < n_caps ? (int)blockIdx.x : (int)blockIdx.x + skip];
   const int kind = tl.kind & 3;
   const RealDesc d = rd[tl.r];
   const StepParam p = sp[tl.r];
@@ -1037,15 +1049,14 @@ cudaError_t prepare_rkl2_fused() {
                               (int)fused::kSmemBytes);
 }
 
-cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
-                              const StepParam* sp, const RowGeo<float>* geo, const ShapeConst* shc,
-                              const Coef<float>* coef, float* B, const float* G, const float* Dm2,
-                              const float* Dm1, float* Om2, float* Om1, float* polar, int j0,
-                              int* status) {
+cudaError_t launch_rkl2_fused(int n_tiles, int n_caps, int cap_total, cudaStream_t st, const Tile* tiles,
+                              const RealDesc* rd, const StepParam* sp, const RowGeo<float>* geo,
+                              const ShapeConst* shc, const Coef<float>* coef, float* B, const float* G,
+                              const float* Dm2, const float* Dm1, float* Om2, float* Om1, float* polar,
+                              int j0, int* status) {
   if (n_tiles <= 0) return cudaSuccess;
-  rkl2_fused_kernel<<<n_tiles, fused::THREADS, fused::kSmemBytes, st>>>(tiles, rd, sp, geo, shc, coef, B, G,
-                                                                   Dm2, Dm1, Om2, Om1, polar, j0,
-                                                                   status);
+  rkl2_fused_kernel<<<n_tiles, fused::THREADS, fused::kSmemBytes, st>>>(
+      tiles, n_caps, cap_total - n_caps, rd, sp, geo, shc, coef, B, G, Dm2, Dm1, Om2, Om1, polar, j0, status);
   return cudaGetLastError();
 }
 
