@@ -1028,7 +1028,7 @@ sft_status autotune(sft_handle h, Wave& w) {
     Coef<T>* d_coef = nullptr;
     Tile* d_tiles = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int best = 1;
+    int best = 8;
     float best_ms = 1e30f;
     cudaError_t err = cudaSuccess;
     err = dev_malloc(&d_sp, sp.size() * sizeof(StepParam));
@@ -1037,9 +1037,13 @@ sft_status autotune(sft_handle h, Wave& w) {
     if (err == cudaSuccess) err = cudaMemcpy(d_coef, coefs.data(), coefs.size() * sizeof(Coef<T>), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaEventCreate(&e0);
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    // candidates whose tile rows would leave half the threads past the row
+    // end are skipped (8 rows per tile always runs); two rounds over the
+    // candidates, each keeping its faster time, damp timing noise
     const int cand[4] = {1, 2, 4, 8};
-    for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci) {
-      const int tr = cand[ci];
+    for (int ci = 0; ci < 8 && err == cudaSuccess; ++ci) {
+      const int tr = cand[ci % 4];
+      if (tr != 8 && (kThreads / tr) * vec_width(h) >= 2 * sh.np) continue;
       std::vector<Tile> tiles;
       for (int r : members) append_tiles(h, r, tr, 1, tiles);
       cudaFree(d_tiles);
@@ -1438,9 +1442,12 @@ sft_status sft_set_state(sft_handle h, int32_t r, const void* br, int32_t on_dev
   const RealInfo& ri = h->reals[r];
   const ShapeInfo& s = h->shapes[ri.shape];
   char* dst = static_cast<char*>(h->state) + ri.off * h->elem;
-  SFT_CUDA(h, cudaMemcpy2DAsync(dst, s.pitch * h->elem, br, s.np * h->elem, s.np * h->elem, s.nt,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                h->stream));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (s.pitch == s.np)  // unpadded rows: one linear copy
+    SFT_CUDA(h, cudaMemcpyAsync(dst, br, (size_t)s.nt * s.np * h->elem, kind, h->stream));
+  else
+    SFT_CUDA(h, cudaMemcpy2DAsync(dst, s.pitch * h->elem, br, s.np * h->elem, s.np * h->elem, s.nt, kind,
+                                  h->stream));
   if (h->prec == SFT_FP32) {
     SFT_CUDA(h, launch_fix_poles<float>(h->n_real, h->stream, h->d_desc, ptr<float>(h->state), r));
   } else {
@@ -1456,9 +1463,12 @@ sft_status sft_get_state(sft_handle h, int32_t r, void* br, int32_t on_device) {
   const RealInfo& ri = h->reals[r];
   const ShapeInfo& s = h->shapes[ri.shape];
   const char* src = static_cast<const char*>(h->state) + ri.off * h->elem;
-  SFT_CUDA(h, cudaMemcpy2DAsync(br, s.np * h->elem, src, s.pitch * h->elem, s.np * h->elem, s.nt,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                h->stream));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (s.pitch == s.np)  // unpadded rows: one linear copy
+    SFT_CUDA(h, cudaMemcpyAsync(br, src, (size_t)s.nt * s.np * h->elem, kind, h->stream));
+  else
+    SFT_CUDA(h, cudaMemcpy2DAsync(br, s.np * h->elem, src, s.pitch * h->elem, s.np * h->elem, s.nt, kind,
+                                  h->stream));
   if (!on_device) return sync(h);
   return SFT_OK;
 }
