@@ -534,7 +534,8 @@ std::string check_tiles(const sft_grid* h, const std::vector<Tile>& tiles, bool 
     if (kind != 0) continue;
     if (fused_tiles) {
       const int n_strips = (d.np + fused::STRIP - 1) / fused::STRIP;
-      const int n_bands = (d.nt - 2 - 2 * fused::PB + fused::BAND - 1) / fused::BAND;
+      const int band = fused::band_rows(d.nt);
+      const int n_bands = (d.nt - 2 - 2 * fused::PB + band - 1) / band;
       if (t.j0 < 0 || t.j0 >= n_bands * n_strips) return "fused work item" + at;
     } else {
       const int lx = t.kind >> 8;
@@ -569,7 +570,8 @@ void append_fused_interior(const sft_grid* h, int r, std::vector<Tile>& tiles) {
   const ShapeInfo& s = h->shapes[h->reals[r].shape];
   // interior: (band, strip) work items, one per warp, WARPS per block
   const int n_strips = (s.np + fused::STRIP - 1) / fused::STRIP;
-  const int n_bands = (s.nt - 2 - 2 * fused::PB + fused::BAND - 1) / fused::BAND;
+  const int band = fused::band_rows(s.nt);
+  const int n_bands = (s.nt - 2 - 2 * fused::PB + band - 1) / band;
   for (int i0 = 0; i0 < n_bands * n_strips; i0 += fused::WARPS) tiles.push_back(Tile{r, i0, 0, 0});
 }
 

@@ -177,7 +177,7 @@ cudaError_t launch_adv_stage(int n_tiles, cudaStream_t st, const Tile* tiles, co
 namespace fused {
 constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
 constexpr int K = 8;             // RKL2 stages per pass
-constexpr int BAND = 128;        // rows of one interior band (a warp marches through it)
+constexpr int BAND = 256;        // most rows of one interior band (a warp marches through it)
 constexpr int LANES = 32;
 constexpr int HL = (K + 3) / 4;  // phi-halo lanes on each side of a strip (4 columns each, >= K)
 constexpr int STRIP = 4 * (LANES - 2 * HL);  // output columns of one warp strip (lanes HL..31-HL)
@@ -188,7 +188,10 @@ constexpr int NB = PB + K + 1;   // rows a cap block holds (pole row + PB + K ha
 constexpr int D = 4;             // rows of asynchronous-copy lookahead per warp (a power of 2)
 constexpr int DG = pow2_at_least(D + K);  // G ring depth: level m reads G m rows back
 constexpr int RING_F4 = (2 * D + DG) * LANES;   // float4 slots of one warp's rings
-constexpr int GROWS = BAND + 3 * K;             // geometry rows of one work item (rows tmin-K ..)
+constexpr int GROWS = BAND + 3 * K;             // geometry rows of one work item, at most (rows tmin-K ..)
+// Band height of a grid: 256 rows from 512 rows up (fewer band-overlap rows),
+// 128 below (more work items for small grids).
+__host__ __device__ constexpr int band_rows(int nt) { return nt >= 512 ? 256 : 128; }
 // per warp: rings, geometry (one float4 per row), coefficient table (DG rows x K levels x 2 float4)
 constexpr size_t kSmemBytes = sizeof(float) * 4 * (RING_F4 + GROWS + 2 * K * DG) * WARPS;
 static_assert((D & (D - 1)) == 0 && (DG & (DG - 1)) == 0 && DG >= D + K, "ring sizes");

@@ -964,12 +964,13 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const Re
   // interior: warp w of the block marches work item (tl.j0 + w) = (band, strip)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_strips = (np + STRIP - 1) / STRIP;
-  const int n_bands = (nt - 2 - 2 * PB + BAND - 1) / BAND;
+  const int band = band_rows(nt);
+  const int n_bands = (nt - 2 - 2 * PB + band - 1) / band;
   const int item = tl.j0 + warp;
   if (item >= n_bands * n_strips) return;  // whole warp
   const int strip = item % n_strips;
-  const int J0 = PB + 1 + (item / n_strips) * BAND;
-  const int J1 = min(J0 + BAND, nt - 1 - PB);
+  const int J0 = PB + 1 + (item / n_strips) * band;
+  const int J1 = min(J0 + band, nt - 1 - PB);
   int col = (strip * STRIP - 4 * HL + 4 * lane) % np;  // first of the lane's 4 columns, periodic
   col = col < 0 ? col + np : col;
   const bool vec = (np & 3) == 0;
@@ -993,14 +994,14 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const Re
   S.rc = rings + warp * RING_F4;
   S.ra = S.rc + D * LANES;
   S.rg = S.ra + D * LANES;
-  // band geometry, rows tmin-K .. tmin-K+GROWS-1 (clamped), then the
+  // band geometry, rows tmin-K .. tmin+band+2K-1 (clamped), then the
   // coefficient table ring
   float4* sg = rings + WARPS * RING_F4 + warp * (GROWS + 2 * K * DG);
   S.geo = sg;
   S.tab = sg + GROWS;
   S.gbase = tmin - K;
   const RowGeo<float>* grow = geo + d.geo;
-  for (int i = lane; i < GROWS; i += LANES) {
+  for (int i = lane; i < band + 3 * K; i += LANES) {
     const int row = min(max(S.gbase + i, 0), nt - 1);
     const float cN = grow[row].cN, cS = grow[row].cS, cE = grow[row].cE;
     sg[i] = make_float4(cN, cS, cE, -(cN + cS + 2.f * cE));
