@@ -452,6 +452,7 @@ def run_surrogate(args):
         "accepted_fraction": st_sur["accepted"] / st_sur["member_days"],
         "rejected_drift": st_sur["rejected_drift"], "rejected_spot": st_sur["rejected_spot"],
         "spot_checked": st_sur["spot_checked"],
+        "tile_rows": {"rollout": st_sur.get("tile_rows"), "plain": st_plain.get("tile_rows")},
         "spot_l2_median_by_day": st_sur["spot_l2_median"],
         "control_rotation_only": {"member_days_per_s": st_ctrl["member_days_per_s"],
                                   "accepted_fraction": st_ctrl["accepted"] / st_ctrl["member_days"],

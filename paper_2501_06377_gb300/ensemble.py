@@ -204,6 +204,7 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
     torch.cuda.synchronize()
     stats["seconds"] = time.perf_counter() - t0
     stats["member_days_per_s"] = stats["member_days"] / stats["seconds"]
+    stats["tile_rows"] = g.get_tile_rows(0)  # the autotuner's choice for this grid shape
     g.close()
     return S, stats
 
@@ -226,5 +227,6 @@ def plain(S0, P, days):
     for i in range(n):
         g.get_state(i, out[i])
     torch.cuda.synchronize()
+    tr = g.get_tile_rows(0)
     g.close()
-    return out, {"seconds": sec, "member_days_per_s": n * days / sec}
+    return out, {"seconds": sec, "member_days_per_s": n * days / sec, "tile_rows": tr}
