@@ -564,11 +564,12 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
 // from warp shuffles.  The HL lanes at each edge (4 HL >= K columns) are the
 // phi halo and the first and last K rows of the band the theta halo: their
 // values go stale from the edge inward, one point per level, and are never
-// stored.  No block barrier
-// after the start.
+// stored.  No block barrier after the start.
 // Caps: the NB = PB + K + 1 rows next to each pole, full ring width, in an
 // L2-resident global scratch, with the FP64 ring sum of App. A done by the
-// block at every level (the only place that needs the whole ring).
+// block at every level (the only place that needs the whole ring).  A
+// launch's first blocks are its cap blocks (the longest serial work), the
+// rest its interior blocks.
 // Interior bands start at row PB+1 = K+1, so their halo never reaches a pole.
 // HBM traffic per pass: read delta_{j-2}, delta_{j-1}, G, write two
 // increments: 20 B per cell per K stages instead of 16 B per stage.
