@@ -52,6 +52,8 @@ typedef struct {
 /* Create a network (weights initialised from seed) and its work buffers for
  * batches up to max_batch.  cuda_stream as in sft_create_grid. */
 sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out);
+
+/* Frees the network and its buffers after the work queued on its stream. */
 sft_status sfs_destroy(sfs_handle h);
 
 /* Number of FP32 parameters. */
@@ -59,6 +61,8 @@ int64_t sfs_num_params(sfs_handle h);
 
 /* Copy the flat parameter vector in / out (host arrays of sfs_num_params). */
 sft_status sfs_set_params(sfs_handle h, const float* host_params);
+
+/* The current flat parameter vector, copied out to host_params. */
 sft_status sfs_get_params(sfs_handle h, float* host_params);
 
 /* y[b] = surrogate one-day advance of x[b] with parameters p[b] (device

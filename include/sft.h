@@ -251,6 +251,8 @@ sft_status sft_flux_diagnostics(sft_handle h, double lat_cut_deg, sft_diag* out)
 
 /* Work counters; synchronises so profiled times are complete. */
 sft_status sft_get_stats(sft_handle h, sft_stats* out);
+
+/* Zeroes the work counters (the step state is untouched). */
 sft_status sft_reset_stats(sft_handle h);
 
 /* profile != 0: sft_step records CUDA events around its advection and RKL2
@@ -316,6 +318,8 @@ sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cf
  * sft_last_error(NULL).
  */
 #define SFT_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* The Sec. 2.6 diagnostics of one caller-owned device map, as described above. */
 sft_status sft_flux_diagnostics_noalloc(const void* br_device, int32_t ntheta, int32_t nphi,
                                         sft_prec prec, double lat_cut_deg, void* cuda_stream,
                                         sft_diag* out);

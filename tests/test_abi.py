@@ -77,3 +77,18 @@ def test_debug_library_builds_and_exports_the_header():
     raw = C.CDLL(path)
     missing = [n for n in sft.header_functions() if not hasattr(raw, n)]
     assert not missing, missing
+
+
+def test_every_declaration_is_documented():
+    """Each C-ABI entry point has its own comment block right above it
+    (argument meaning, layout, ownership and errors are stated there)."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for name in ("sft.h", "sfs.h"):
+        text = open(os.path.join(root, "include", name)).read()
+        decls = list(re.finditer(r"^(?:sft_status|int32_t|int64_t|const char\*|void|double)\s+"
+                                 r"((?:sft|sfs)_[a-z0-9_]+)\s*\(", text, flags=re.M))
+        assert len(decls) >= 8
+        bare = [m.group(1) for m in decls if not text[:m.start()].rstrip().endswith("*/")]
+        assert not bare, (name, bare)
