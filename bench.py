@@ -6,8 +6,9 @@ coefficients +-10 %, meridional amplitude U[10,20] m/s and eta U[250,750]
 km^2/s (seed 3), 8 seeded dipole + active-region start maps, CFL-limited
 steps toward a 27-day end time.  One bench "step" = one call of sft_step
 advancing every realization by one time step (SSPRK(4,3) WENO3-CS(h)
-advection + RKL2 diffusion, ~410-714 stages) plus the FP64 flux
-diagnostics of every realization.
+advection + RKL2 diffusion, ~410-714 stages) plus the flux diagnostics
+of every realization (FP64-accurate: compensated FP32 row sums, FP64
+across rows).
 
 value: realization-cell-updates/s (sum over realizations of ntheta*nphi per
 step / device time), inputs resident in HBM.  e2e: the same step driven
