@@ -174,3 +174,76 @@ def test_grid_nu_euler_limit_scales_inversely_with_alpha():
     g = O.Grid(65, 128)
     assert O.euler_dt_limit(g, O.grid_nu(g, 0.5)) == pytest.approx(
         2.0 * O.euler_dt_limit(g, O.grid_nu(g, 1.0)), rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.7.2: explicit forward-Euler diffusion (the paper's reference and
+# testing stepper), sub-cycled at the Euler limit
+# --------------------------------------------------------------------------
+def _fewest_substeps(dt, dte):
+    """Brute force: the smallest n with dt / n <= dte."""
+    n = 1
+    while dt / n > dte:
+        n += 1
+    return n
+
+
+@pytest.mark.parametrize("dt,dte", [(1.0, 1.0), (1.0, 0.3), (2.5, 0.25), (7.0, 0.07 * 1.0000001),
+                                    (0.01, 5.0)])
+def test_fe_diffusion_scalar_is_the_euler_power(dt, dte):
+    """On the scalar test dY/dt = z Y the sub-cycled stepper is exactly
+    (1 + z dt/n)^n with n the fewest sub-steps that respect the limit."""
+    n = _fewest_substeps(dt, dte)
+    z = np.array([-0.3, -1.7 + 0.4j, 0.2j, -3.0 / dte])
+    got = O.fe_diffusion_advance(np.ones_like(z), dt, lambda y: z * y, dte)
+    want = (1.0 + z * (dt / n)) ** n
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=0)
+
+
+def test_fe_diffusion_is_first_order_in_the_substep():
+    """Against exp(dt M) u0 of the assembled Eq. (diffusion_matrix) (the
+    exact semi-discrete solution, independent of any stepper), the error
+    halves with the sub-step: first order."""
+    from scipy.sparse.linalg import expm_multiply
+    g = O.Grid(17, 32)
+    nu = O.constant_nu(g, 0.02)
+    M = O.diffusion_matrix(g, nu)
+    u0 = O.unique_unknowns(I.initial_map(17, 32, seed=5))
+    T = 3.0
+    exact = expm_multiply(T * M, u0)
+    dte = O.euler_dt_limit(g, nu)
+    errs = []
+    for k in range(3):
+        u = O.fe_diffusion_advance(u0, T, lambda y: M @ y, dte / 2 ** k)
+        errs.append(np.abs(u - exact).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(0.9 <= o <= 1.1 for o in orders), orders
+
+
+def test_fe_diffusion_axial_dipole_decays_as_exp_minus_2nut():
+    """l = 1: the pole cap of cos(theta) follows exp(-2 nu t) (App. A cap,
+    Sec. 3.7.2 explicit Euler)."""
+    g = O.Grid(32, 64)
+    nu = O.constant_nu(g, NU500)
+    dte = O.euler_dt_limit(g, nu)
+    B = I.dipole(32, 64, 1.0)
+    out = O.fe_diffusion_advance(B, 672.0, lambda y: O.diffusion_operator(g, y, nu), dte)
+    assert out[0, 0] == pytest.approx(math.exp(-2.0 * NU500 * 672.0), rel=2e-4)
+
+
+def test_fe_diffusion_stable_at_the_limit_and_unstable_beyond():
+    """With sub-steps at the Gershgorin limit the stiffest mode never grows;
+    with sub-steps 5 % beyond 2/|lambda_max| (the true explicit-Euler limit)
+    it grows without bound."""
+    g = O.Grid(9, 12)
+    nu = O.constant_nu(g, 1.0)
+    M = O.diffusion_matrix(g, nu).toarray()
+    lam, V = np.linalg.eig(M)
+    i = np.argmax(np.abs(lam.real))
+    v = np.real(V[:, i])
+    dte = O.euler_dt_limit(g, nu)
+    stable = O.fe_diffusion_advance(v, 200 * dte, lambda y: M @ y, dte)
+    assert np.abs(stable).max() <= np.abs(v).max() * (1 + 1e-9)
+    h = 1.05 * 2.0 / abs(lam[i].real)
+    grown = O.fe_diffusion_advance(v, 200 * h, lambda y: M @ y, h)
+    assert np.abs(grown).max() > 1e3 * np.abs(v).max()

@@ -88,3 +88,13 @@ def test_rfe_run_realizes_the_rate_with_infinite_lifetime():
     short, net_s = _rfe_only(0.3, 10.0)
     assert short < 0.3 * unsigned                              # cancellation between samples
     assert abs(net_s) <= 1e-12 * short
+
+
+def test_splitmix64_reproduces_the_published_sequence():
+    """The output function on the states k * gamma (k = 1, 2, 3) is the
+    generator of Steele, Lea & Flood (2014) seeded with 0, whose first three
+    outputs are published with its reference implementation."""
+    gam = np.uint64(O.SPLITMIX_GAMMA)
+    with np.errstate(over="ignore"):
+        got = [int(O.splitmix64_output(np.uint64(k) * gam)) for k in (1, 2, 3)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
