@@ -311,15 +311,18 @@ sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cf
  * Scratch: one fixed file-scope device array of SFT_NOALLOC_SCRATCH_BYTES
  * (held by every GPU that loads the library until the process exits).  A map
  * whose tables and partial sums do not fit is rejected with SFT_ERR_ARG
- * (roughly up to 8192 x 16384).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU race; errors are reported through
- * sft_last_error(NULL).
+ * (roughly up to 8192 x 16384).  Every call looks up the array's address in
+ * the current context (cudaGetSymbolAddress, which allocates nothing).  With
+ * lazy module loading (CUDA's default) the first call in a context also
+ * loads the library's device code and commits the array's memory: make one
+ * call at start-up, before a memory pool reserves the device, or set
+ * CUDA_MODULE_LOADING=EAGER.  All calls share the array, so calls that
+ * overlap on the GPU race; errors are reported through sft_last_error(NULL).
  */
 #define SFT_NOALLOC_SCRATCH_BYTES (4u << 20)
 
-/* The Sec. 2.6 diagnostics of one caller-owned device map, as described above. */
+/* Flux diagnostics of one caller-owned device map without device allocation
+ * (no counterpart in the paper), as described above. */
 sft_status sft_flux_diagnostics_noalloc(const void* br_device, int32_t ntheta, int32_t nphi,
                                         sft_prec prec, double lat_cut_deg, void* cuda_stream,
                                         sft_diag* out);

@@ -13,17 +13,22 @@
 // partial sums and the folded result) lives in one file-scope __device__
 // array of SFT_NOALLOC_SCRATCH_BYTES.  Every GPU that loads libsft holds that
 // array until the process exits.  Host code cannot use the array's name as
-// a device address (in host code it names a host-side stand-in), so the
-// first call on each device, with that device current, asks the runtime for
-// the array's device address with cudaGetSymbolAddress and caches it; that
-// first call should therefore come before any stream capture.  Every call
-// shares the one array and overwrites all of it that it reads (nothing needs
-// to start at zero), so calls whose work overlaps on the GPU race: serialise
-// them (one stream, or synchronise between calls).
+// a device address (in host code it names a host-side stand-in), so every
+// call asks the runtime for the array's address in the current context with
+// cudaGetSymbolAddress (a lookup that allocates nothing), which stays right
+// after a cudaDeviceReset or inside a caller's own driver-API context.
+// With lazy module loading (CUDA's default) the first call in a context is
+// also the moment the runtime loads this library's device code and commits
+// the array's memory: a caller whose memory pool takes the device must make
+// one call at start-up, before the pool reserves its memory, or load the
+// library with CUDA_MODULE_LOADING=EAGER.  Every call shares the one array
+// and overwrites all of it that it reads (nothing needs to start at zero),
+// so calls whose work overlaps on the GPU race: serialise them (one stream,
+// or synchronise between calls).  A call returns only after its result has
+// reached the host: it waits for cuda_stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -39,11 +44,7 @@ using namespace sft;
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
 __device__ __align__(256) unsigned char g_noalloc_scratch[SFT_NOALLOC_SCRATCH_BYTES];
-
-std::atomic<void*> g_scratch_addr[kMaxDevices];
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -137,18 +138,12 @@ extern "C" sft_status sft_flux_diagnostics_noalloc(const void* br_device, int32_
                                          std::to_string(nphi) + " map needs " + std::to_string(L.total) +
                                          " bytes of scratch, more than the fixed " +
                                          std::to_string((size_t)SFT_NOALLOC_SCRATCH_BYTES) + "-byte array");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(SFT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(SFT_ERR_ARG, "noalloc diagnostics: device index too large");
-  // One-time set-up per device (the current one): the array's device address.
-  void* base = g_scratch_addr[dev].load();
-  if (!base) {
-    e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      return noalloc_fail(SFT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev].store(base);
-  }
+  // The array's device address in the current context (looked up on every
+  // call, never cached: a cached address goes stale when the context does).
+  void* base = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+  if (e != cudaSuccess)
+    return noalloc_fail(SFT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   unsigned char* b = static_cast<unsigned char*>(base);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   noalloc_tables_kernel<<<std::max(1, std::min(1024, (std::max(ntheta, nphi) + 255) / 256)), 256, 0, st>>>(

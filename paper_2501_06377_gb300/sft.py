@@ -374,13 +374,17 @@ class Grid:
 
 def flux_diagnostics_noalloc(br, lat_cut_deg=60.0, stream=None):
     """sft_flux_diagnostics_noalloc on a contiguous CUDA tensor [ntheta][nphi]
-    (float32 or float64).  Allocates no device memory."""
+    (float32 or float64).  Allocates no device memory.  stream: a torch
+    stream or raw handle; None = torch's current stream on br's device (the
+    one a map written by torch was produced on)."""
     lib = load()
     import torch
     if not (isinstance(br, torch.Tensor) and br.is_cuda and br.is_contiguous() and br.dim() == 2):
         raise TypeError("expected a contiguous 2-D CUDA tensor")
     prec = {torch.float32: SFT_FP32, torch.float64: SFT_FP64}[br.dtype]
-    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    if stream is None:
+        stream = torch.cuda.current_stream(br.device)
+    s = stream if isinstance(stream, int) else stream.cuda_stream
     out = sft_diag()
     st = lib.sft_flux_diagnostics_noalloc(C.c_void_p(br.data_ptr()), br.shape[0], br.shape[1], prec,
                                           float(lat_cut_deg), s, C.byref(out))

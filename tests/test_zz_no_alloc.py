@@ -5,7 +5,9 @@ This entry point is for callers that cannot allocate device memory while
 they run (a solver inside a model whose memory pool already owns the
 device, or a real-time pipeline that forbids cudaMalloc after start-up).
 The test makes two calls in a row on different maps and shapes, so stale
-scratch contents from the first call would show up in the second.  It sits
+scratch contents from the first call would show up in the second, then two
+more in the other order, across which the device's free memory must not
+change (the library's code and array are loaded by the first call).  It sits
 in its own file, collected last, and works alone in a fresh process.
 """
 import numpy as np
@@ -52,3 +54,12 @@ def test_noalloc_diagnostics_match_handle_twice(prec):
            flux_diagnostics_noalloc(maps[1], lat_cut_deg=60.0)]
     for a, b in zip(got, refs):
         _compare(a, b)
+    # once the library's device code is loaded (first call in the context),
+    # further calls take no device memory: the free figure does not move
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    again = [flux_diagnostics_noalloc(maps[1], lat_cut_deg=60.0),
+             flux_diagnostics_noalloc(maps[0], lat_cut_deg=60.0)]
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert again[0] == got[1] and again[1] == got[0]
