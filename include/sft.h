@@ -266,12 +266,13 @@ sft_status sft_set_profiling(sft_handle h, int32_t profile);
 sft_status sft_set_graphs(sft_handle h, int32_t use_graphs);
 
 /* RKL2 stages per kernel launch: 1 (one launch per stage) or 8 (temporal
- * blocking: eight stages per pass through HBM; bands of 128 rows marched by
- * warps with an eight-point halo, full-ring cap blocks).  The fused path
- * needs FP32 and every grid with ntheta >= 36 and nphi >= 16; it is the
- * default when available.  Both paths compute the same stages (the fused
- * interior folds the stencil into per-row coefficients: another rounding
- * order, agreement to FP32 rounding). */
+ * blocking: eight stages per pass through HBM; bands of rows marched by
+ * warps with an eight-point halo; per pole, one block evaluates the pole
+ * values of the pass over the whole ring).  The fused path needs FP32 and
+ * every grid with ntheta >= 20 and nphi >= 16; it is the default when
+ * available.  Both paths compute the same stages (the fused path folds the
+ * stencil into per-row coefficients: another rounding order, agreement to
+ * FP32 rounding). */
 sft_status sft_set_fusion(sft_handle h, int32_t stages_per_pass);
 
 /* Current RKL2 stages per launch (1 or 8). */

@@ -71,20 +71,19 @@ constexpr int kMaxConfigs = 24; // cached step configurations (tile tables, grap
 
 struct Config {
   bool fused = false;            // built for the fused RKL2 path
-  Tile* d_ftiles = nullptr;      // fused-kernel tiles of every chain (per realization: caps, then interior)
+  Tile* d_ftiles = nullptr;      // fused-pass tiles of every chain (pole blocks, then interior blocks)
   // The fused passes run as n_chains independent launch chains on their own
   // streams (realizations dealt alternately from the stage-sorted order), so
-  // one chain's launch fills the SMs while the other's drains.
+  // one chain's launches fill the SMs while the other's drain.
   int n_chains = 1;
-  // A chain's tiles are its members' cap blocks (two per member, in member
-  // order), then their interior blocks: a pass launches the caps of its
-  // active members first (dispatched in the first wave: a cap block runs
-  // longest) and then their interior blocks.
+  // A chain's tiles are its members' pole blocks (two per member, in member
+  // order), then their interior blocks; a pass launches the pole blocks of
+  // its active members (a prefix), then their interior blocks (a prefix).
   int fbase[kMaxChains] = {};                 // first tile of each chain in d_ftiles
-  int fcaps[kMaxChains] = {};                 // cap tiles of each chain (the interior starts there)
-  std::vector<int> fused_tiles[kMaxChains];   // [chain][j0] = tiles launched by the pass starting at stage j0
-  std::vector<int> fused_caps[kMaxChains];    // [chain][j0] = of which cap tiles
-  int64_t fused_launches = 0;           // non-empty fused launches per step
+  int fcaps[kMaxChains] = {};                 // pole tiles of each chain (the interior tiles start there)
+  std::vector<int> fused_tiles[kMaxChains];   // [chain][j0] = interior tiles of the pass starting at stage j0
+  std::vector<int> fused_caps[kMaxChains];    // [chain][j0] = pole tiles of that pass
+  int64_t fused_launches = 0;           // non-empty fused-pass launches per step (pole + interior)
   std::vector<double> dt;        // per wave member (wave order)
   std::vector<int> s;            // per wave member
   std::vector<int> tr;           // tile rows per shape at build time
@@ -133,7 +132,7 @@ struct sft_grid {
   int n_work = 3;              // 5 when the fused RKL2 path is possible
   bool fused_ok = false;       // FP32 and every shape has an interior band
   bool fused = false;          // use rkl2_fused_kernel (K stages per launch)
-  void* polar = nullptr;       // cap-block scratch of the fused path
+  void* polar = nullptr;       // ring-sum partials of the fused path (doubles)
   int64_t polar_elems = 0;
   RealDesc* d_desc = nullptr;
   std::vector<RealDesc> desc;  // host copy (geometry offsets change with grid-based nu)
@@ -261,6 +260,7 @@ void geo_rows(const ShapeInfo& s, std::vector<RowGeo<T>>& g, std::vector<RowGeoD
       r.cN = T(sdn / (s.dth * s.dth * st));
       r.cS = T(sup / (s.dth * s.dth * st));
       r.cE = T(1.0 / (s.dph * s.dph * st * st));
+      r.cC = -(r.cN + r.cS + T(2) * r.cE);
       r.inv_sdth = T(1.0 / (st * s.dth));
       r.inv_sdph = T(1.0 / (st * s.dph));
       r.sdn = T(sdn);
@@ -290,6 +290,7 @@ void geo_rows_grid_nu(const ShapeInfo& s, double alpha, std::vector<RowGeo<T>>& 
     r.cN = T(ndn * s.sin_h[j - 1] / (s.dth * s.dth * st));
     r.cS = T(nup * s.sin_h[j] / (s.dth * s.dth * st));
     r.cE = T(0.5 * (ndn + nup) / (s.dph * s.dph * st * st));
+    r.cC = -(r.cN + r.cS + T(2) * r.cE);
   }
 }
 
@@ -509,8 +510,8 @@ std::string check_desc(const sft_grid* h) {
     const int64_t cells = (int64_t)d.nt * d.pitch;
     if (d.off < 0 || d.off + cells > h->state_elems) return "state extent" + at;
     if (d.woff < 0 || d.woff + cells > h->work_elems) return "work extent" + at;
-    if (h->fused_ok && (d.poff < 0 || d.poff + 4ll * fused::NB * d.pitch > h->polar_elems))
-      return "cap scratch extent" + at;
+    if (h->fused_ok && (d.poff < 0 || d.poff + fused::part_elems(d.np) > h->polar_elems))
+      return "ring-sum partials extent" + at;
     if (d.geo < 0 || d.geo + d.nt > h->geo_rows) return "geometry rows" + at;
     if (d.flow < 0 || d.flow + d.nt > h->flow_rows) return "flow rows" + at;
     if (d.col < 0 || d.col + d.np > h->col_entries) return "longitude table" + at;
@@ -533,10 +534,7 @@ std::string check_tiles(const sft_grid* h, const std::vector<Tile>& tiles, bool 
     if (kind == 3) return "tile kind" + at;
     if (kind != 0) continue;
     if (fused_tiles) {
-      const int n_strips = (d.np + fused::STRIP - 1) / fused::STRIP;
-      const int band = fused::band_rows(d.nt);
-      const int n_bands = (d.nt - 2 - 2 * fused::PB + band - 1) / band;
-      if (t.j0 < 0 || t.j0 >= n_bands * n_strips) return "fused work item" + at;
+      if (t.j0 < 0 || t.j0 >= fused::n_bands(d.nt) * fused::n_strips(d.np)) return "fused work item" + at;
     } else {
       const int lx = t.kind >> 8;
       if (lx < 0 || (1 << lx) > kThreads) return "tile width" + at;
@@ -561,18 +559,17 @@ void append_tiles(const sft_grid* h, int r, int tr, int run, std::vector<Tile>& 
   tiles.push_back(Tile{r, 0, 0, 2});
 }
 
-void append_fused_caps(int r, std::vector<Tile>& tiles) {
+// The two pole-triangle blocks of realization r (north, south).
+void append_fused_poles(int r, std::vector<Tile>& tiles) {
   tiles.push_back(Tile{r, 0, 0, 1});
   tiles.push_back(Tile{r, 0, 0, 2});
 }
 
 void append_fused_interior(const sft_grid* h, int r, std::vector<Tile>& tiles) {
   const ShapeInfo& s = h->shapes[h->reals[r].shape];
-  // interior: (band, strip) work items, one per warp, WARPS per block
-  const int n_strips = (s.np + fused::STRIP - 1) / fused::STRIP;
-  const int band = fused::band_rows(s.nt);
-  const int n_bands = (s.nt - 2 - 2 * fused::PB + band - 1) / band;
-  for (int i0 = 0; i0 < n_bands * n_strips; i0 += fused::WARPS) tiles.push_back(Tile{r, i0, 0, 0});
+  // rows 1 .. nt-2: (band, strip) work items, one per warp, WARPS per block
+  const int items = fused::n_bands(s.nt) * fused::n_strips(s.np);
+  for (int i0 = 0; i0 < items; i0 += fused::WARPS) tiles.push_back(Tile{r, i0, 0, 0});
 }
 
 template <typename T>
@@ -640,10 +637,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     size_t pass_tiles = 0;
     {
       std::vector<Tile> tmp;
-      for (int i : order) {
-        append_fused_caps(w.reals[i], tmp);
-        append_fused_interior(h, w.reals[i], tmp);
-      }
+      for (int i : order) append_fused_interior(h, w.reals[i], tmp);
       pass_tiles = tmp.size();
     }
     c->n_chains = pass_tiles >= (size_t)4 * h->n_sm ? std::min<int>(kMaxChains, (int)order.size()) : 1;
@@ -652,7 +646,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
       c->fbase[ch] = (int)ft.size();
       std::vector<int> mem, fend;  // chain members (descending s) and their interior tile ends
       for (size_t q = ch; q < order.size(); q += c->n_chains) mem.push_back(order[q]);
-      for (int i : mem) append_fused_caps(w.reals[i], ft);
+      for (int i : mem) append_fused_poles(w.reals[i], ft);
       c->fcaps[ch] = (int)ft.size() - c->fbase[ch];
       for (int i : mem) {
         append_fused_interior(h, w.reals[i], ft);
@@ -664,7 +658,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
         int n = 0;
         while (n < (int)mem.size() && s[mem[n]] >= j0) ++n;
         c->fused_caps[ch][j0] = 2 * n;
-        c->fused_tiles[ch][j0] = n == 0 ? 0 : 2 * n + fend[n - 1];
+        c->fused_tiles[ch][j0] = n == 0 ? 0 : fend[n - 1];
         if (n > 0) c->fused_launches += 1;
       }
     }
@@ -803,6 +797,11 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
                                      h->d_status));
     float* P[4] = {ptr<float>(h->work[1]), ptr<float>(h->work[2]), ptr<float>(h->work[3]),
                    ptr<float>(h->work[4])};
+    // ring sums next to the poles of delta_1 and G for the first fused launch
+    for (int ch = 0; ch < c.n_chains; ++ch)
+      SFT_CUDA(h, launch_ring_sums(c.fused_caps[ch].size() > 2 ? c.fused_caps[ch][2] : 0, st,
+                                   c.d_ftiles + c.fbase[ch], h->d_desc, P[1], ptr<const float>(h->work[0]),
+                                   ptr<double>(h->polar)));
     if (c.n_chains > 1) {  // fork: the side chains start after stage 1
       SFT_CUDA(h, cudaEventRecord(h->fork, st));
       for (int ch = 1; ch < c.n_chains; ++ch) SFT_CUDA(h, cudaStreamWaitEvent(h->side[ch], h->fork, 0));
@@ -812,12 +811,11 @@ sft_status enqueue_step(sft_handle h, Config& c, bool record_events, bool captur
       int in = 0;  // input pair (P[in], P[in+1]) = (delta_{j0-2}, delta_{j0-1})
       for (int j0 = 2; j0 <= c.smax; j0 += fused::K) {
         const int out = 2 - in;
-        SFT_CUDA(h, launch_rkl2_fused(c.fused_tiles[ch][j0], c.fused_caps[ch][j0], c.fcaps[ch], cs,
-                                      c.d_ftiles + c.fbase[ch], h->d_desc,
-                                      c.d_sp, ptr<const RowGeo<float>>(h->d_geo), h->d_shc,
+        SFT_CUDA(h, launch_rkl2_fused(c.fused_tiles[ch][j0], cs, c.d_ftiles + c.fbase[ch] + c.fcaps[ch],
+                                      h->d_desc, c.d_sp, ptr<const RowGeo<float>>(h->d_geo), h->d_shc,
                                       ptr<const Coef<float>>(c.d_coef), ptr<float>(h->state),
-                                      ptr<const float>(h->work[0]), P[in], P[in + 1], P[out],
-                                      P[out + 1], ptr<float>(h->polar), j0, h->d_status));
+                                      ptr<const float>(h->work[0]), P[in], P[in + 1], P[out], P[out + 1],
+                                      ptr<double>(h->polar), in / 2, j0, h->d_status));
         in = out;
       }
     }
@@ -963,7 +961,8 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
   const int n_adv = (c->n_adv_tiles > 0 ? adv_stage_count(h) : 0) * (h->strang ? 2 : 1);
   // RKL2 passes (one fused pass = K stages, over both chains) and launches
   const int n_diff = c->fused ? (c->smax >= 1 ? 1 + (c->smax - 1 + fused::K - 1) / fused::K : 0) : c->smax;
-  const int64_t n_diff_launches = c->fused ? (c->smax >= 1 ? 1 + c->fused_launches : 0) : c->smax;
+  const int64_t n_diff_launches =
+      c->fused ? (c->smax >= 1 ? 1 + (c->smax >= 2 ? c->n_chains : 0) + c->fused_launches : 0) : c->smax;
   h->stats.kernel_launches += n_adv + n_diff_launches;
   h->stats.realization_steps += c->realization_steps;
   h->stats.cell_updates += c->cell_updates;
@@ -1360,16 +1359,17 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   }
   std::vector<int32_t> poff(n_real, 0);
   if (h->fused_ok) {
-    // cap scratch: 2 caps x 2 levels x NB rows per realization, per wave
+    // ring-sum partials of the rows next to the poles, per realization, per wave
     for (auto& w : h->waves) {
       int64_t used = 0;
       for (int r : w.reals) {
         poff[r] = (int32_t)used;
-        used += 4ll * fused::NB * h->shapes[h->reals[r].shape].pitch;
+        used += fused::part_elems(h->shapes[h->reals[r].shape].np);
       }
       h->polar_elems = std::max(h->polar_elems, used);
     }
-    CREATE_CUDA(dev_malloc(&h->polar, std::max<int64_t>(h->polar_elems, 32) * sizeof(float)));
+    CREATE_CUDA(dev_malloc(&h->polar, std::max<int64_t>(h->polar_elems, 32) * sizeof(double)));
+    CREATE_CUDA(cudaMemsetAsync(h->polar, 0, std::max<int64_t>(h->polar_elems, 32) * sizeof(double), h->stream));
     CREATE_CUDA(prepare_rkl2_fused());
   }
   sft_status st = prec == SFT_FP32 ? upload_tables<float>(h) : upload_tables<double>(h);
@@ -1766,7 +1766,7 @@ sft_status sft_set_fusion(sft_handle h, int32_t stages_per_pass) {
     return fail(h, SFT_ERR_ARG, "stages per pass must be 1 or " + std::to_string(fused::K));
   if (stages_per_pass == fused::K && !h->fused_ok)
     return fail(h, SFT_ERR_ARG, "fused RKL2 needs FP32 and grids with ntheta >= " +
-                                    std::to_string(2 * fused::NB + 2) + ", nphi >= 16");
+                                    std::to_string(2 * fused::K + 4) + ", nphi >= 16");
   h->fused = stages_per_pass == fused::K;
   return SFT_OK;
 }

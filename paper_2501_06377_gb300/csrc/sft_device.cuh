@@ -51,7 +51,7 @@ enum DebugSite : int {
   DBG_FUSED_FIRST = 6,    // rkl2_fused_kernel band: first loaded row in [0, nt-1]
   DBG_FUSED_LAST = 7,     // last loaded row in [first, nt-1]
   DBG_FUSED_COL = 8,      // a lane's first column in [0, np-1] (np-4 when vectorised)
-  DBG_FUSED_CAP = 9,      // first row of a cap block in [0, nt-NB]
+  DBG_FUSED_CAP = 9,      // unused
   DBG_RED_ROWS = 10,      // reduction / RFE tile rows within [0, nt]
 };
 
@@ -85,7 +85,7 @@ struct RealDesc {
                    // with a grid-based diffusivity folded into cN, cS, cE)
   int32_t flow;    // first row of this realization's flow table
   int32_t col;     // first entry of the shape's cos/sin(phi_k) tables
-  int32_t poff;    // element offset of this realization's polar-band scratch (fused RKL2)
+  int32_t poff;    // offset of this realization's ring-sum partials (doubles, fused RKL2)
 };
 
 // Per-row geometry of a shape (uniform grid, Sec. 3.2).
@@ -93,11 +93,11 @@ template <typename T> struct RowGeo {
   T cN;        // sin(th_{j-1/2}) / (dth^2 sin th_j)   (Eq. diffusion_matrix a_{j-1,k} / nu)
   T cS;        // sin(th_{j+1/2}) / (dth^2 sin th_j)   (a_{j+1,k} / nu)
   T cE;        // 1 / (dph^2 sin^2 th_j)               (a_{j,k+-1} / nu)
+  T cC;        // -(cN + cS + 2 cE) in T               (a_{j,j} / nu); cN..cC are one 16-B vector in FP32
   T inv_sdth;  // 1 / (sin th_j dth)
   T inv_sdph;  // 1 / (sin th_j dph)
   T sdn;       // sin th_{j-1/2}
   T sup;       // sin th_{j+1/2}
-  T pad;
 };
 
 // Per-row FP64 geometry for the reductions.
@@ -174,43 +174,68 @@ cudaError_t launch_adv_stage(int n_tiles, cudaStream_t st, const Tile* tiles, co
                              const ShapeConst* shc, T* state, T* work_base0, T* work_base1,
                              AdvStage<T> s);
 // Fused RKL2: K stages per launch (see rkl2_fused_kernel in sft_kernels.cu).
+#ifndef SFT_FUSED_K
+#define SFT_FUSED_K 8
+#endif
+#ifndef SFT_FUSED_MINB
+#define SFT_FUSED_MINB 2
+#endif
+#ifndef SFT_FUSED_BAND
+#define SFT_FUSED_BAND 256
+#endif
 namespace fused {
-constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
-constexpr int K = 8;             // RKL2 stages per pass
-constexpr int BAND = 256;        // most rows of one interior band (a warp marches through it)
+constexpr int K = SFT_FUSED_K;   // RKL2 stages per pass
 constexpr int LANES = 32;
 constexpr int HL = (K + 3) / 4;  // phi-halo lanes on each side of a strip (4 columns each, >= K)
 constexpr int STRIP = 4 * (LANES - 2 * HL);  // output columns of one warp strip (lanes HL..31-HL)
-constexpr int WARPS = 4;         // strips per block (two 128-thread blocks share an SM)
+constexpr int WARPS = 4;         // strips per block
 constexpr int THREADS = WARPS * LANES;
-constexpr int PB = K;            // rows next to each pole owned by the cap blocks
-constexpr int NB = PB + K + 1;   // rows a cap block holds (pole row + PB + K halo rows)
-constexpr int D = 4;             // rows of asynchronous-copy lookahead per warp (a power of 2)
-constexpr int DG = pow2_at_least(D + K);  // G ring depth: level m reads G m rows back
-constexpr int RING_F4 = (2 * D + DG) * LANES;   // float4 slots of one warp's rings
-constexpr int GROWS = BAND + 3 * K;             // geometry rows of one work item, at most (rows tmin-K ..)
+constexpr int MIN_BLOCKS = SFT_FUSED_MINB;  // blocks per SM the register budget is sized for
+#ifndef SFT_FUSED_D
+#define SFT_FUSED_D 8
+#endif
+constexpr int D = SFT_FUSED_D;   // rows of asynchronous-copy lookahead per warp (a power of 2)
+// G and coefficient rings: row r in slot r mod RG; slots 0..MG-1 are also
+// mirrored after the ring (slot RG + x), so the K rows t-1..t-K a row step
+// reads always sit at P - 1 .. P - K for one base slot P (no wrap).
+constexpr int RG = D + K;        // ring period: rows t-K .. t+D-1 live at once
+constexpr int MG = K - 1;        // mirrored slots
+constexpr int GSLOTS = RG + MG;  // slots of the G ring and of the coefficient table
+constexpr int RING_F4 = (2 * D + GSLOTS) * LANES;  // float4 slots of one warp's rings (C, A, G)
+constexpr int TAB_F4 = (GSLOTS + 1) * 2 * K;       // one warp's table: per slot K levels x (ka, kb), + a spare slot
 // Band height of a grid: 256 rows from 512 rows up (fewer band-overlap rows),
 // 128 below (more work items for small grids).
-__host__ __device__ constexpr int band_rows(int nt) { return nt >= 512 ? 256 : 128; }
-// per warp: rings, geometry (one float4 per row), coefficient table (DG rows x K levels x 2 float4)
-constexpr size_t kSmemBytes = sizeof(float) * 4 * (RING_F4 + GROWS + 2 * K * DG) * WARPS;
-static_assert((D & (D - 1)) == 0 && (DG & (DG - 1)) == 0 && DG >= D + K, "ring sizes");
-// A grid shape can use the fused path when the interior band is non-empty.
-inline bool shape_ok(int nt, int np) { return nt >= 2 * NB + 2 && np >= 16; }
+__host__ __device__ constexpr int band_rows(int nt) { return nt >= 512 ? SFT_FUSED_BAND : 128; }
+constexpr int POLE_F4 = (2 * K + 3) / 4;           // one warp's pole values (north, south)
+constexpr size_t kSmemBytes = sizeof(float4) * (RING_F4 + TAB_F4 + POLE_F4) * WARPS;
+static_assert((D & (D - 1)) == 0 && RG >= D + K && MG >= K - 1, "ring sizes");
+static_assert(4 * K <= LANES, "at most one coefficient of a row per lane");
+// Bands of a grid: rows 1 .. nt-2 in bands of band_rows(nt).
+__host__ __device__ constexpr int n_bands(int nt) { return (nt - 2 + band_rows(nt) - 1) / band_rows(nt); }
+__host__ __device__ constexpr int n_strips(int np) { return (np + STRIP - 1) / STRIP; }
+// A grid shape can use the fused path when the K rows next to each pole are
+// disjoint and inside one band, and a strip is at least its halo wide.
+inline bool shape_ok(int nt, int np) { return nt >= 2 * K + 4 && np >= 16; }
+// Per realization, the ring-sum partials of the rows next to the poles
+// (doubles): 2 buffers x 2 poles x 2 inputs, then G, x K rows x strips.
+inline int64_t part_elems(int np) { return 10ll * K * n_strips(np); }
 }  // namespace fused
 
 // Stages j0 .. j0+K-1 of every realization with s >= j0 (fewer, ending with
 // the final write B += delta_s, for a realization whose s ends inside the
-// pass).  Reads delta_{j0-2} (Dm2, zero when j0 == 2), delta_{j0-1} (Dm1), G;
-// writes delta_{j0+K-2} (Om2) and delta_{j0+K-1} (Om1).  The launch runs
-// n_tiles blocks: the first n_caps over tiles[0 .. n_caps), the rest over the
-// interior tiles from tiles[cap_total] on.
-cudaError_t launch_rkl2_fused(int n_tiles, int n_caps, int cap_total, cudaStream_t st, const Tile* tiles,
-                              const RealDesc* rd,
+// launch).  Reads delta_{j0-2} (Dm2, zero when j0 == 2), delta_{j0-1} (Dm1),
+// G; writes delta_{j0+K-2} (Om2) and delta_{j0+K-1} (Om1), rows 0 .. nt-1.
+// part: ring-sum partials (desc.poff), read from buffer pin, written to
+// buffer 1-pin for the next launch.  launch_ring_sums fills buffer 0 and the
+// G partials from stage 1's output and G before the first launch of a step
+// (tiles: a north and a south tile per realization).
+cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
                               const StepParam* sp, const RowGeo<float>* geo, const ShapeConst* shc,
                               const Coef<float>* coef, float* B, const float* G, const float* Dm2,
-                              const float* Dm1, float* Om2, float* Om1, float* polar, int j0,
+                              const float* Dm1, float* Om2, float* Om1, double* part, int pin, int j0,
                               int* status);
+cudaError_t launch_ring_sums(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                             const float* D1, const float* G, double* part);
 cudaError_t prepare_rkl2_fused();
 
 template <typename T>

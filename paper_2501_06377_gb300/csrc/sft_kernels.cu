@@ -551,39 +551,69 @@ adv_stage_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd
   }
 }
 
+// Error-free transformations in FP32 (Knuth's TwoSum; the FMA form of
+// Dekker's TwoProduct): s + e equals a + b exactly, p + e equals a * b.
+// The _rn intrinsics keep the compiler from contracting a product into
+// these sums (an FMA there would break exactness).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// A compensated FP32 sum (Ogita, Rump and Oishi's Sum2): s + c tracks the
+// exact sum of the added terms; the error of c is of order n^2 u^2 sum |x|
+// for n terms (u = 2^-24), about 2e-13 sum |x| for a thread's 8 terms.
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float e;
+    two_sum(s, x, s, e);
+    c += e;
+  }
+  // x * (hi + lo), with hi + lo an FP64 value split into two floats
+  __device__ __forceinline__ void add_product(float x, float hi, float lo) {
+    const float p = __fmul_rn(x, hi);
+    const float ep = fmaf(x, hi, -p);  // x * hi - p, exactly
+    float e;
+    two_sum(s, p, s, e);
+    c += e + fmaf(x, lo, ep);
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
 // ---------------------------------------------------------------------------
 // Fused RKL2 (temporal blocking): fused::K stages per launch, FP32.
 //
-// Interior: one warp owns a strip of 128 longitudes (a float4 per lane) and
-// marches down a band of rows.  For every RKL2 level (the two inputs
-// delta_{j-2}, delta_{j-1} and the K levels it computes) the lane keeps a
-// rolling window of three rows in registers; at each row step it takes one
-// new row of the inputs and computes level m at the row m above, so level K
-// leaves the pipeline K rows behind the loads.  The inputs stream through
-// per-warp shared-memory rings (cp.async, D rows ahead); phi neighbours come
-// from warp shuffles.  The HL lanes at each edge (4 HL >= K columns) are the
-// phi halo and the first and last K rows of the band the theta halo: their
-// values go stale from the edge inward, one point per level, and are never
-// stored.  No block barrier after the start.
-// Caps: the NB = PB + K + 1 rows next to each pole, full ring width, in an
-// L2-resident global scratch, with the FP64 ring sum of App. A done by the
-// block at every level (the only place that needs the whole ring).  A
-// launch's first blocks are its cap blocks (the longest serial work), the
-// rest its interior blocks.
-// Interior bands start at row PB+1 = K+1, so their halo never reaches a pole.
-// HBM traffic per pass: read delta_{j-2}, delta_{j-1}, G, write two
+// Rows 1 .. nt-2 are advanced in (band, strip) work items.  One warp owns a
+// strip of 128 longitudes (a float4 per lane) and marches down a band of
+// rows; for every RKL2 level (the two inputs delta_{j-2}, delta_{j-1} and
+// the K levels it computes) the lane keeps its last two rows in registers;
+// at each row step it takes one new row of the inputs and computes level m
+// at the row m above, so level K leaves the pipeline K rows behind the
+// loads.  The HL lanes at each edge (4 HL >= K columns) are the phi halo and
+// the K rows above and below the band the theta halo: their values go stale
+// from the edge inward, one point per level, and are never stored.  No block
+// barrier after the start.
+//
+// Poles (App. A): a pole is one cell whose update needs the FP64 ring sum
+// of the level below it over all longitudes, which no warp holds.  The
+// operator is the same on every longitude, so the ring sums S_l[i] (row i
+// counted from the pole) obey their own 1-D recurrence over the rows (the
+// phi terms cancel in the sum): the K pole values of a pass follow exactly
+// from the ring sums of the pass's inputs on the K rows next to each pole.
+// A warp whose rows reach a pole evaluates that recurrence in FP64 first
+// (pole_values), then takes the pole value at every level on the pole row
+// instead of computing it, and writes the pole row of the outputs for its
+// columns.  The ring sums come from per-strip partials: each warp that
+// writes one of the K rows next to a pole adds up its columns of both
+// outputs (compensated FP32, then FP64) for the next launch; before the
+// first launch of a step ring_sums_kernel forms them for stage 1's output
+// and for G.
+// HBM traffic per launch: read delta_{j-2}, delta_{j-1}, G, write two
 // increments: 20 B per cell per K stages instead of 16 B per stage.
-// The cap blocks use the per-point arithmetic of rkl2_stage_kernel; the
-// interior folds it into per-row coefficients (other rounding, same stage).
 // ---------------------------------------------------------------------------
 namespace {
-
-__device__ __forceinline__ float rkl2_point(const RowGeo<float>& g, const Coef<float>& cf, float mutdt,
-                                            float c, float up, float dn, float l, float r, float d2,
-                                            float gv) {
-  const float L = g.cN * (up - c) + g.cS * (dn - c) + g.cE * ((l - c) + (r - c));
-  return cf.mu * c + cf.nu * d2 + mutdt * L + cf.gsum * gv;
-}
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -603,6 +633,14 @@ __device__ __forceinline__ void async_cols(float4* dst, const float* row, int c0
     }
   }
 }
+// The 16-byte copy of async_cols issued only when `on` (a predicate, no branch).
+__device__ __forceinline__ void async_vec_if(float4* dst, const float* src, bool on) {
+  const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p cp.async.cg.shared.global [%0], [%1], 16;\n}\n" ::"r"(sa),
+      "l"(src), "r"((int)on)
+      : "memory");
+}
 __device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -613,11 +651,11 @@ __device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_group
 //   o = a0 c + a1 up + a2 dn + a3 (l + r) + nu d2 + gsum G,
 //   a1..a3 = mu~ nu dt (cN, cS, cE),  a0 = mu + mu~ nu dt cC,
 //   cC = -(cN + cS + 2 cE)
-// (the same stage as rkl2_point, other rounding and summation order), evaluated on (x, y) and
+// (the same stage as rkl2_stage_kernel, other rounding and summation order), evaluated on (x, y) and
 // (z, w) pairs with the packed f32x2 FMA: the same IEEE operations per
-// element as the scalar forms.  A row's coefficients for all K levels are
-// formed once per row by the warp, one per lane, and read back as pairs
-// ka = (a1, a1, a2, a2), kb = (a3, a3, a0, a0).
+// element as the scalar forms (point_update below).  A row's coefficients
+// for all K levels are formed once per row by the warp, one per lane, and
+// read back as pairs ka = (a1, a1, a2, a2), kb = (a3, a3, a0, a0).
 struct LevelNG {  // per-level constants, each duplicated into a pair
   float2 nu, gs;
 };
@@ -648,109 +686,212 @@ __device__ __forceinline__ float4 level_update(const LevelNG& q, float4 ka, floa
   return make_float4(o01.x, o01.y, o23.x, o23.y);
 }
 
-// Lane state of the interior march.  Win[l][slot] holds level l (0..K-1) at
-// the row whose index mod 3 is slot; level l's window holds rows t-l-2..t-l.
-// The level j-2 input is only needed pointwise one row later (d2m1), level K
-// only at its output step.  The inputs arrive through per-warp shared-memory
-// rings filled D rows ahead by cp.async (each lane copies its own float4, so
-// a lane only ever reads what it copied itself); G keeps K more rows because
-// level m reads it m rows behind the loads.  The band's row geometry (cN,
-// cS, cE, cC per row) is staged once per work item in shared memory; at
-// each row step every lane forms one of the row's 4K level coefficients
-// (level lane/4, coefficient lane%4) into a table ring indexed like G's.
+// Lane state of the interior march.  W[l][q] holds level l (0..K-1; level 0
+// is the input delta_{j-1}) at the row whose index mod 3 is q: level l's
+// window holds its last three rows, and its new row replaces the one three
+// rows up, which no level needs any more (so the state never moves between
+// registers).  Level m is computed at row t-m; it reads level m-1 at rows
+// t-m-1, t-m, t-m+1 (the last computed earlier in the same step), level m-2
+// at row t-m and G at row t-m.  The inputs arrive through per-warp
+// shared-memory rings filled D rows ahead by cp.async (each lane copies its
+// own float4, so a lane only ever reads what it copied itself); G and the
+// coefficient table sit in rings of period RG whose first MG slots are
+// mirrored after the ring, so the K rows a step reads (t-1 .. t-K) are at
+// fixed offsets below one base slot: no per-level index arithmetic.  Every
+// lane forms one of the K x 4 level coefficients of each new row (level
+// lane/4, coefficient lane mod 4) from the row's geometry, prefetched from
+// global memory one row ahead.
 struct March {
-  float4 Win[fused::K][3];
-  float4 d2m1;               // delta_{j-2} at row t-1
-  float4 *rc, *ra, *rg;      // rings: C, A (D rows), G (DG rows)
-  const float4* geo;         // (cN, cS, cE, cC); row r at r - gbase
-  float4* tab;               // coefficient table: DG rows x K levels x (ka, kb)
-  int gbase;
+  float4 W[fused::K][3];
+  float4 a_prev;             // delta_{j-2} at row t-1
+  float4 *rc, *ra, *rg;      // rings: C, A (D rows), G (GSLOTS rows); this lane's slot 0
+  float4* tab;               // coefficient table: GSLOTS rows x K levels x (ka, kb)
+  const float* geo;          // this lane's geometry component (cN, cS, cE or cC) of row 0
+  const float* pole;         // pole values of levels 1..K: north at [0..K), south at [K..2K)
+  double* part_out;          // ring-sum partials for the next launch (this realization, output buffer)
+  const float *nC, *nA, *nG; // this lane's columns of the inputs at the next row to request
+  float gnext;               // that component of the next row to tabulate
   float kmul, kadd;          // this lane's coefficient: kmul * geometry + kadd
+  int s;                     // ring slot of the current row t (t mod RG)
+  int rmax;                  // last row that exists and is loaded (min(t_end, nt-1))
+  int strip, ns;             // this work item's strip, strips per ring
   LevelNG lv[fused::K];      // per-level constants (registers)
 };
 
-// This lane's coefficient of row r (all K levels of a row: one per lane).
-__device__ __forceinline__ void table_row(March& S, int r, int lane) {
-  static_assert(4 * fused::K == fused::LANES, "one coefficient per lane");
-  const float gc = reinterpret_cast<const float*>(S.geo + (r - S.gbase))[lane & 3];
-  const float v = fmaf(S.kmul, gc, S.kadd);
-  reinterpret_cast<float2*>(S.tab)[(r & (fused::DG - 1)) * fused::LANES + lane] = make_float2(v, v);
+// Partials layout of one realization (doubles, at desc.poff): ring sums of
+// the launch inputs C = delta_{j-1} and A = delta_{j-2} on rows 1..K from
+// each pole, per strip, in two buffers (the launch reads one and fills the
+// other for the next), then those of G.
+__host__ __device__ constexpr int64_t part_io(int buf, int pole, int arr, int row, int strip, int ns) {
+  return ((((int64_t)buf * 2 + pole) * 2 + arr) * fused::K + (row - 1)) * ns + strip;
+}
+__host__ __device__ constexpr int64_t part_g(int pole, int row, int strip, int ns) {
+  return ((int64_t)8 * fused::K + (int64_t)pole * fused::K + (row - 1)) * ns + strip;
+}
+
+// Warp sum of compensated partials (s, c); every lane returns the total.
+__device__ __forceinline__ double warp_csum(CSum v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, v.s, o), c2 = __shfl_xor_sync(0xffffffffu, v.c, o);
+    float e;
+    two_sum(v.s, s2, v.s, e);
+    v.c += c2 + e;
+  }
+  return v.value();
+}
+
+// The pole values P_1 .. P_kk of one pole for this launch (written to
+// out[0..kk)), from the ring sums of the inputs: App. A's cap update with the
+// FP64 ring sum, and the ring sums S_m[i] of the rows i = 1 .. kk-m from
+// the pole by the ring-summed stage (the phi neighbours cancel:
+// sum_k (l + r) = 2 S).  Lane i < K carries row i+1.  Returns P_kk in FP64.
+__device__ double pole_values(bool north, const RealDesc& d, const StepParam& p, const Coef<float>* coef, int j0,
+                              int kk, const RowGeo<float>* geo, const ShapeConst& shc, const float* gC,
+                              const float* gA, const float* gG, bool zero_m2, const double* part, int pin,
+                              float* out, int lane) {
+  using namespace fused;
+  const int ns = n_strips(d.np), pole = north ? 0 : 1;
+  const int g0 = north ? 0 : d.nt - 1, dir = north ? 1 : -1;
+  // lane q < 3K: array q / K (C, A, G) on row 1 + q % K, summed over the strips in order
+  double sum = 0.0;
+  if (lane < 3 * K) {
+    const int a = lane / K, i = 1 + lane % K;
+    const double* src = part + (a < 2 ? part_io(pin, pole, a, i, 0, ns) : part_g(pole, i, 0, ns));
+    if (!(a == 1 && zero_m2))
+      for (int s = 0; s < ns; ++s) sum += src[s];
+  }
+  const int q = lane < K ? lane : K - 1;
+  double s1 = __shfl_sync(0xffffffffu, sum, q);          // S_{m-1}[q+1]
+  double s2 = __shfl_sync(0xffffffffu, sum, K + q);      // S_{m-2}[q+1]
+  const double sg = __shfl_sync(0xffffffffu, sum, 2 * K + q);
+  const RowGeo<float> g = geo[d.geo + g0 + dir * (q + 1)];
+  const double cp = north ? g.cN : g.cS;   // the neighbour towards the pole
+  const double ca = north ? g.cS : g.cN;   // the neighbour away from it
+  const double cc = double(g.cC) + 2.0 * double(g.cE);
+  const double npd = d.np;
+  const float nudt = float(p.nudt);
+  const double lp_fac = shc.pole_diff * p.cap_nu;
+  const double gp = double(gG[(int64_t)g0 * d.pitch]);
+  double pm1 = double(gC[(int64_t)g0 * d.pitch]);
+  double pm2 = zero_m2 ? 0.0 : double(gA[(int64_t)g0 * d.pitch]);
+  double last = 0.0;
+  for (int m = 1; m <= kk; ++m) {
+    const Coef<float> cf = coef[p.coef + j0 + m - 1];
+    const double ring = __shfl_sync(0xffffffffu, s1, 0);  // S_{m-1}[1]
+    last = double(cf.mu) * pm1 + double(cf.nu) * pm2 +
+           double(cf.mut) * double(nudt) * (lp_fac * (ring - npd * pm1)) + double(cf.gsum) * gp;
+    const float pv = float(last);
+    double up = __shfl_up_sync(0xffffffffu, s1, 1);
+    const double dn = __shfl_down_sync(0xffffffffu, s1, 1);
+    if (lane == 0) up = npd * pm1;
+    const double md = double(cf.mut) * double(nudt);
+    const double sn = double(cf.mu) * s1 + double(cf.nu) * s2 + md * (cp * up + ca * dn + cc * s1) +
+                      double(cf.gsum) * sg;
+    s2 = s1;
+    s1 = sn;
+    pm2 = pm1;
+    pm1 = double(pv);
+    if (lane == 0) out[m - 1] = pv;
+  }
+  return last;
 }
 
 // Issue the asynchronous copies of row r's inputs into the rings (one commit
-// group; empty past the band's last row t_end, which keeps the group count
-// uniform).
+// group; empty past the last loaded row, which keeps the group count
+// uniform) and advance the row pointers.  xs = r mod RG, the row's G slot
+// (mirrored below MG).  VEC: one predicated 16-byte copy per array.
 template <bool VEC>
-__device__ __forceinline__ void march_issue(March& S, int r, int t_end, const float* gA, const float* gC,
-                                            const float* gG, int pitch, int np, int col, bool zero_m2,
-                                            int lane) {
-  if (r <= t_end) {
-    const int64_t ro = (int64_t)r * pitch;
-    const int sl = (r & (fused::D - 1)) * fused::LANES + lane;
-    async_cols(S.rc + sl, gC + ro, col, np, VEC);
-    if (!zero_m2) async_cols(S.ra + sl, gA + ro, col, np, VEC);
-    async_cols(S.rg + (r & (fused::DG - 1)) * fused::LANES + lane, gG + ro, col, np, VEC);
+__device__ __forceinline__ void march_issue(March& S, int r, int xs, int pitch, int np, int col, bool zero_m2) {
+  using namespace fused;
+  const int sl = (r & (D - 1)) * LANES;
+  const bool on = r <= S.rmax;
+  if (VEC) {
+    async_vec_if(S.rc + sl, S.nC, on);
+    async_vec_if(S.ra + sl, S.nA, on && !zero_m2);
+    async_vec_if(S.rg + xs * LANES, S.nG, on);
+    async_vec_if(S.rg + (xs + RG) * LANES, S.nG, on && xs < MG);
+  } else if (on) {
+    async_cols(S.rc + sl, S.nC - col, col, np, false);
+    if (!zero_m2) async_cols(S.ra + sl, S.nA - col, col, np, false);
+    async_cols(S.rg + xs * LANES, S.nG - col, col, np, false);
+    if (xs < MG) async_cols(S.rg + (xs + RG) * LANES, S.nG - col, col, np, false);
   }
   async_commit();
+  S.nC += pitch;
+  S.nA += pitch;
+  S.nG += pitch;
 }
 
 // One row step t (phase P = t mod 3).  FULL: all K levels run (kk == K).
-// Rows above the first loaded one (t - m < tmin during the first K steps)
-// are computed from stale ring slots and zero windows; they only feed levels
-// at rows that never reach an output (level m is needed from row tmin + m).
-template <int P, bool FULL, bool VEC>
-__device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, const float* gA,
-                                          const float* gC, const float* gG, int pitch, int np, int col,
-                                          bool zero_m2, int J0, bool fin, float* oA, float* oC,
-                                          float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
+// EDGE: a step near a pole: level m takes the pole value where it sits on
+// a pole row (t - m == 0 or nt - 1), and an output row among the K next to
+// a pole adds its strip's ring-sum partials for the next launch.  Rows above
+// the first loaded one (t - m < tmin during the first K steps of a band
+// away from the poles) and rows past the south pole are computed from stale
+// ring slots and zero windows; they only feed levels at rows that never
+// reach an output.
+template <int P, bool FULL, bool VEC, bool EDGE>
+__device__ __forceinline__ void march_row(March& S, int t, int kk, int nt, int pitch, int np, int col,
+                                          bool zero_m2, int J0, bool fin, float* oA, float* oC, float* Bs,
+                                          bool lane_out, int n_out, bool& bad, int lane) {
   using namespace fused;
-  // request row t+D-1 (into the slots of rows t-1 / t-1-K, already consumed),
+  // request row t+D-1 (into the C/A slots of row t-1, already consumed),
   // then wait until row t has landed: D groups are in flight at most
-  march_issue<VEC>(S, t + D - 1, t_end, gA, gC, gG, pitch, np, col, zero_m2, lane);
+  {
+    int xs = S.s + (D - 1);
+    xs = xs >= RG ? xs - RG : xs;
+    march_issue<VEC>(S, t + D - 1, xs, pitch, np, col, zero_m2);
+  }
   async_wait<D - 1>();
-  const int cs = (t & (D - 1)) * LANES + lane;
-  S.Win[0][P] = S.rc[cs];
+  const int cs = (t & (D - 1)) * LANES;
+  S.W[0][P] = S.rc[cs];
   const float4 a_t = zero_m2 ? make_float4(0.f, 0.f, 0.f, 0.f) : S.ra[cs];
+  const int P0 = S.s >= K ? S.s : S.s + RG;     // row t-m of G and the table: slot P0 - m
+  const float4* gb = S.rg + P0 * LANES;
+  const float4* kb = S.tab + P0 * (2 * K);
   float4 top = make_float4(0.f, 0.f, 0.f, 0.f);  // level K at row t-K
-  const int tg = t & (DG - 1);                    // G and table ring slot of row t
 #pragma unroll
   for (int m = 1; m <= K; ++m) {
     if (FULL || m <= kk) {
-      const int sc = ((P - m) % 3 + 3) % 3;       // slot of row t-m in level m-1's window
-      const int su = ((P - m - 1) % 3 + 3) % 3;   // row t-m-1
-      const int sd = ((P - m + 1) % 3 + 3) % 3;   // row t-m+1
-      const int rm = (tg - m) & (DG - 1);         // ring slot of row t-m
-      const float4 d2 = m == 1 ? S.d2m1 : S.Win[m - 2][sc];
-      const float4 gv = S.rg[rm * LANES + lane];
-      const float4* kr = S.tab + (rm * K + m - 1) * 2;
-      const float4 o = level_update(S.lv[m - 1], kr[0], kr[1], S.Win[m - 1][sc], S.Win[m - 1][su],
-                                    S.Win[m - 1][sd], d2, gv);
-      if (m < K) S.Win[m][sc] = o;
+      const int sc = ((P - m) % 3 + 3) % 3;      // slot of row t-m
+      const int su = ((P - m - 1) % 3 + 3) % 3;  // row t-m-1
+      const int sd = ((P - m + 1) % 3 + 3) % 3;  // row t-m+1 (level m-1's newest)
+      const float4 d2 = m == 1 ? S.a_prev : S.W[m - 2][sc];
+      const float4 gv = gb[-m * LANES];
+      const float4* kr = kb - m * (2 * K) + 2 * (m - 1);
+      float4 o = level_update(S.lv[m - 1], kr[0], kr[1], S.W[m - 1][sc], S.W[m - 1][su], S.W[m - 1][sd], d2, gv);
+      if (EDGE) {
+        if (t - m == 0) {
+          const float v = S.pole[m - 1];
+          o = make_float4(v, v, v, v);
+        } else if (t - m == nt - 1) {
+          const float v = S.pole[K + m - 1];
+          o = make_float4(v, v, v, v);
+        }
+      }
+      if (m < K) S.W[m][sc] = o;
       else top = o;
     }
   }
-  constexpr bool vec = VEC;
-  S.d2m1 = a_t;
-  // row t's coefficients, first read at step t+1; they replace row t-DG's
-  table_row(S, t, lane);
-  __syncwarp();
+  S.a_prev = a_t;
   // leave the pipeline: level kk (and kk-1) at row t - kk (always < J1)
   const int orow = t - (FULL ? K : kk);
-  if (orow >= J0 && lane_out) {
-    // slots are compile-time (unrolled m, template P) so the state stays in registers
-    float4 lk = top, lk1 = S.Win[K - 1][((P - K) % 3 + 3) % 3];
-    if (!FULL) {
+  // slots are compile-time (unrolled m, template P) so the state stays in registers
+  float4 lk = top, lk1 = S.W[K - 1][((P - K) % 3 + 3) % 3];
+  if (!FULL) {
 #pragma unroll
-      for (int m = 1; m < K; ++m)
-        if (m == kk) {
-          lk = S.Win[m][((P - m) % 3 + 3) % 3];
-          lk1 = S.Win[m - 1][((P - m) % 3 + 3) % 3];
-        }
-    }
+    for (int m = 1; m < K; ++m)
+      if (m == kk) {
+        lk = S.W[m][((P - m) % 3 + 3) % 3];
+        lk1 = S.W[m - 1][((P - m) % 3 + 3) % 3];
+      }
+  }
+  if (orow >= J0 && lane_out) {
     const int64_t go = (int64_t)orow * pitch + col;
     if (fin) {
-      float4 b = n_out == 4 && vec ? ld4(Bs + go) : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (n_out == 4 && vec) {
+      if (n_out == 4 && VEC) {
+        float4 b = ld4(Bs + go);
         b.x += lk.x; b.y += lk.y; b.z += lk.z; b.w += lk.w;
         bad |= !isfinite(b.x) || !isfinite(b.y) || !isfinite(b.z) || !isfinite(b.w);
         st4(Bs + go, b);
@@ -766,7 +907,7 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, co
           }
         }
       }
-    } else if (n_out == 4 && vec) {
+    } else if (n_out == 4 && VEC) {
       st4(oC + go, lk);
       st4(oA + go, lk1);
     } else {
@@ -781,68 +922,117 @@ __device__ __forceinline__ void march_row(March& S, int t, int kk, int t_end, co
       }
     }
   }
+  // ring-sum partials of the rows next to a pole (uniform over the warp)
+  if (EDGE && !fin && orow >= J0 && (orow <= K || orow >= nt - 1 - K)) {
+    CSum sc, sa;
+    const float vc[4] = {lk.x, lk.y, lk.z, lk.w}, va[4] = {lk1.x, lk1.y, lk1.z, lk1.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (e < n_out) {
+        sc.add(vc[e]);
+        sa.add(va[e]);
+      }
+    const double tc = warp_csum(sc), ta = warp_csum(sa);
+    if (lane == 0) {
+      const int pole = orow <= K ? 0 : 1, row = orow <= K ? orow : nt - 1 - orow;
+      S.part_out[part_io(0, pole, 0, row, S.strip, S.ns)] = tc;
+      S.part_out[part_io(0, pole, 1, row, S.strip, S.ns)] = ta;
+    }
+  }
+  // row t's coefficients (first read at step t+1) into slot t mod RG (and its mirror)
+  {
+    const float v = fmaf(S.kmul, S.gnext, S.kadd);
+    float2* tb = reinterpret_cast<float2*>(S.tab) + lane;
+    if (4 * K == LANES || lane < 4 * K) {
+      tb[S.s * (4 * K)] = make_float2(v, v);
+      // the mirror copy, or a spare slot after the ring (no branch)
+      tb[(S.s < MG ? S.s + RG : GSLOTS) * (4 * K)] = make_float2(v, v);
+    }
+    S.gnext = S.geo[(int64_t)min(t + 1, nt - 1) * (sizeof(RowGeo<float>) / sizeof(float))];
+  }
+  S.s = S.s + 1 == RG ? 0 : S.s + 1;
+  __syncwarp();
 }
 
-// The row loop of one work item: rows tmin..t_end, unrolled by 3 so that the
-// window phase t mod 3 is a template argument.
-template <bool FULL, bool VEC>
-__device__ __forceinline__ void march_band(March& S, int tmin, int t_end, int kk, const float* gA,
-                                           const float* gC, const float* gG, int pitch, int np, int col,
-                                           bool zero_m2, int J0, bool fin, float* oA, float* oC,
-                                           float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
-    for (int r = tmin; r < tmin + fused::D - 1; ++r)  // D-1 rows of lookahead before the first step
-    march_issue<VEC>(S, r, t_end, gA, gC, gG, pitch, np, col, zero_m2, lane);
-#define SFT_MARCH(PH, TT)                                                                        \
-  march_row<PH, FULL, VEC>(S, TT, kk, t_end, gA, gC, gG, pitch, np, col, zero_m2, J0, fin, oA, oC, \
-                           Bs, lane_out, n_out, bad, lane)
-  int t = tmin;
+// Row steps t0 .. t1-1, unrolled by 3 so that the window phase t mod 3 is a
+// template argument.
+template <bool FULL, bool VEC, bool EDGE>
+__device__ __forceinline__ void march_run(March& S, int t0, int t1, int kk, int nt, int pitch, int np, int col,
+                                          bool zero_m2, int J0, bool fin, float* oA, float* oC, float* Bs,
+                                          bool lane_out, int n_out, bool& bad, int lane) {
+#define SFT_MARCH(PH, TT)                                                                                    \
+  march_row<PH, FULL, VEC, EDGE>(S, TT, kk, nt, pitch, np, col, zero_m2, J0, fin, oA, oC, Bs, lane_out, n_out, \
+                                 bad, lane)
+  int t = t0;
   const int ph = t % 3;
-  if (ph == 1) {
+  if (t < t1 && ph == 1) {
     SFT_MARCH(1, t);
     ++t;
   }
-  if (ph != 0 && t <= t_end) {
+  if (t < t1 && ph != 0) {
     SFT_MARCH(2, t);
     ++t;
   }
-  for (; t + 2 <= t_end; t += 3) {
+  for (; t + 2 < t1; t += 3) {
     SFT_MARCH(0, t);
     SFT_MARCH(1, t + 1);
     SFT_MARCH(2, t + 2);
   }
-  if (t <= t_end) {
+  if (t < t1) {
     SFT_MARCH(0, t);
     ++t;
   }
-  if (t <= t_end) {
-    SFT_MARCH(1, t);
-    ++t;
-  }
+  if (t < t1) SFT_MARCH(1, t);
 #undef SFT_MARCH
+}
+
+// The row loop of one work item: rows tmin..t_end.  The steps near a pole
+// (where a level can sit on the pole row, or an output row is one of the K
+// next to a pole) run the EDGE instance: the first kk + K + 1 steps of the
+// band starting at the north pole, the steps from nt-1-K+kk of a band
+// reaching the south pole.
+template <bool FULL, bool VEC>
+__device__ __forceinline__ void march_band(March& S, int tmin, int t_end, int kk, int nt, int pitch, int np,
+                                           int col, bool zero_m2, int J0, bool fin, float* oA, float* oC,
+                                           float* Bs, bool lane_out, int n_out, bool& bad, int lane) {
+  using namespace fused;
+  S.s = tmin % RG;
+  for (int i = 0; i < D - 1; ++i) {  // D-1 rows of lookahead before the first step
+    int xs = S.s + i;
+    xs = xs >= RG ? xs - RG : xs;
+    march_issue<VEC>(S, tmin + i, xs, pitch, np, col, zero_m2);
+  }
+  S.gnext = S.geo[(int64_t)tmin * (sizeof(RowGeo<float>) / sizeof(float))];
+  const int n_end = tmin == 0 ? min(kk + K + 1, t_end + 1) : tmin;
+  const int s_beg = t_end >= nt - 1 - K + kk ? max(n_end, nt - 1 - K + kk) : t_end + 1;
+#define SFT_RUN(E, A, B_)                                                                                  \
+  march_run<FULL, VEC, E>(S, A, B_, kk, nt, pitch, np, col, zero_m2, J0, fin, oA, oC, Bs, lane_out, n_out, bad, \
+                          lane)
+  SFT_RUN(true, tmin, n_end);
+  SFT_RUN(false, n_end, s_beg);
+  SFT_RUN(true, s_beg, t_end + 1);
+#undef SFT_RUN
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(fused::THREADS)
-rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const RealDesc* __restrict__ rd,
+__global__ void __launch_bounds__(fused::THREADS, fused::MIN_BLOCKS)
+rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd,
                   const StepParam* __restrict__ sp, const RowGeo<float>* __restrict__ geo,
                   const ShapeConst* __restrict__ shc, const Coef<float>* __restrict__ coef,
                   float* __restrict__ B, const float* __restrict__ G, const float* __restrict__ Dm2,
                   const float* __restrict__ Dm1, float* __restrict__ Om2, float* __restrict__ Om1,
-                  float* __restrict__ polar, int j0, int* __restrict__ status) {
+                  double* __restrict__ part, int pin, int j0, int* __restrict__ status) {
   using namespace fused;
-  __shared__ double sm[THREADS / 32];
   __shared__ Coef<float> s_cf[K];
-  // blocks 0 .. n_caps-1: cap tiles; the rest: interior tiles after all the chain's caps
-  const Tile tl = tiles[(int)blockIdx.x < n_caps ? (int)blockIdx.x : (int)blockIdx.x + skip];
-  const int kind = tl.kind & 3;
+  const Tile tl = tiles[blockIdx.x];
   const RealDesc d = rd[tl.r];
   const StepParam p = sp[tl.r];
   if (j0 > p.s) return;  // uniform over the block
-  const int kk = min(K, p.s - j0 + 1);  // levels of this realization in this pass
+  const int kk = min(K, p.s - j0 + 1);  // levels of this realization in this launch
   if (threadIdx.x < K) s_cf[threadIdx.x] = coef[p.coef + j0 + min((int)threadIdx.x, kk - 1)];
   __syncthreads();
-  const bool fin = j0 + kk - 1 == p.s;  // the pass ends the realization's super-step
+  const bool fin = j0 + kk - 1 == p.s;  // the launch ends the realization's super-step
   const float nudt = float(p.nudt);
   const int pitch = d.pitch, np = d.np, nt = d.nt;
   const float* gG = G + d.woff;
@@ -853,125 +1043,15 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const Re
   float* Bs = B + d.off;
   const bool zero_m2 = j0 == 2;  // delta_0 = 0
 
-  if (kind != 0) {
-    // Every loop below goes row by row and gives each thread CU columns at a
-    // time: their loads are all issued before the stores, so CU scratch (L2)
-    // round trips are in flight per thread instead of one.
-    constexpr int CU = 8;
-    const bool north = kind == 1;
-    int base = north ? 0 : nt - NB;  // global row of local row 0
-    SFT_DCHECK(DBG_FUSED_CAP, base, 0, nt - NB);
-    float* prv = polar + d.poff + (north ? 0 : 2 * NB * pitch);  // level m-2, updated to m
-    float* cur = prv + NB * pitch;                                // level m-1
-    for (int i = 0; i < NB; ++i) {
-      const int64_t go = (int64_t)(base + i) * pitch, lo = (int64_t)i * pitch;
-      for (int k0 = threadIdx.x; k0 < np; k0 += CU * THREADS) {
-        float vc[CU], va[CU];
-#pragma unroll
-        for (int q = 0; q < CU; ++q) {
-          const int k = min(k0 + q * THREADS, np - 1);  // columns past np repeat np-1, not stored
-          vc[q] = gC[go + k];
-          va[q] = zero_m2 ? 0.f : gA[go + k];
-        }
-#pragma unroll
-        for (int q = 0; q < CU; ++q) {
-          const int k = k0 + q * THREADS;
-          if (k < np) {
-            cur[lo + k] = vc[q];
-            prv[lo + k] = va[q];
-          }
-        }
-      }
-    }
-    __syncthreads();
-    const int ip = north ? 0 : NB - 1;  // pole row (local)
-    const int ia = north ? 1 : NB - 2;  // ring next to the pole
-    double pole_last = 0.0;
-    for (int m = 1; m <= kk; ++m) {
-      const Coef<float> cf = coef[p.coef + j0 + m - 1];
-      const float mutdt = cf.mut * nudt;
-      const int i_lo = north ? 1 : m, i_hi = north ? NB - 1 - m : NB - 2;
-      const double yp = double(cur[(int64_t)ip * pitch]);
-      const double pp = double(prv[(int64_t)ip * pitch]);
-      const double gp = double(gG[(int64_t)(base + ip) * pitch]);
-      double acc = 0.0;
-      for (int k = threadIdx.x; k < np; k += blockDim.x) acc += double(cur[(int64_t)ia * pitch + k]) - yp;
-      const double Lp = shc[d.shape].pole_diff * p.cap_nu * block_sum(acc, sm);
-      for (int i = i_lo; i <= i_hi; ++i) {
-        const float* cr = cur + (int64_t)i * pitch;
-        float* pr = prv + (int64_t)i * pitch;
-        const float* gr = gG + (int64_t)(base + i) * pitch;
-        const RowGeo<float> g = geo[d.geo + base + i];
-        for (int k0 = threadIdx.x; k0 < np; k0 += CU * THREADS) {
-          float vc[CU], vu[CU], vd[CU], vl[CU], vr[CU], vp[CU], vg[CU];
-#pragma unroll
-          for (int q = 0; q < CU; ++q) {
-            const int k = min(k0 + q * THREADS, np - 1);
-            vc[q] = cr[k];
-            vu[q] = cr[k - pitch];
-            vd[q] = cr[k + pitch];
-            vl[q] = cr[k == 0 ? np - 1 : k - 1];
-            vr[q] = cr[k == np - 1 ? 0 : k + 1];
-            vp[q] = pr[k];
-            vg[q] = gr[k];
-          }
-#pragma unroll
-          for (int q = 0; q < CU; ++q) {
-            const int k = k0 + q * THREADS;
-            if (k < np) pr[k] = rkl2_point(g, cf, mutdt, vc[q], vu[q], vd[q], vl[q], vr[q], vp[q], vg[q]);
-          }
-        }
-      }
-      pole_last = double(cf.mu) * yp + double(cf.nu) * pp + double(cf.mut) * double(nudt) * Lp +
-                  double(cf.gsum) * gp;
-      const float vpole = float(pole_last);
-      for (int k = threadIdx.x; k < np; k += THREADS) prv[(int64_t)ip * pitch + k] = vpole;
-      __syncthreads();
-      float* t = cur;
-      cur = prv;
-      prv = t;
-    }
-    const int o_lo = north ? 0 : NB - 1 - PB, o_hi = north ? PB : NB - 1;
-    bool bad = false;
-    for (int i = o_lo; i <= o_hi; ++i) {
-      const int64_t go = (int64_t)(base + i) * pitch, lo = (int64_t)i * pitch;
-      for (int k0 = threadIdx.x; k0 < np; k0 += CU * THREADS) {
-        float vc[CU], va[CU];
-#pragma unroll
-        for (int q = 0; q < CU; ++q) {
-          const int k = min(k0 + q * THREADS, np - 1);
-          vc[q] = cur[lo + k];
-          va[q] = fin ? Bs[go + k] : prv[lo + k];
-        }
-#pragma unroll
-        for (int q = 0; q < CU; ++q) {
-          const int k = k0 + q * THREADS;
-          if (k >= np) continue;
-          if (fin) {
-            const float v = i == ip ? float(double(va[q]) + pole_last) : va[q] + vc[q];
-            bad |= !isfinite(v);
-            Bs[go + k] = v;
-          } else {
-            oC[go + k] = vc[q];
-            oA[go + k] = va[q];
-          }
-        }
-      }
-    }
-    if (bad) atomicOr(status, 1);
-    return;
-  }
-
-  // interior: warp w of the block marches work item (tl.j0 + w) = (band, strip)
+  // warp w of the block marches work item (tl.j0 + w) = (band, strip)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_strips = (np + STRIP - 1) / STRIP;
+  const int ns = n_strips(np);
   const int band = band_rows(nt);
-  const int n_bands = (nt - 2 - 2 * PB + band - 1) / band;
   const int item = tl.j0 + warp;
-  if (item >= n_bands * n_strips) return;  // whole warp
-  const int strip = item % n_strips;
-  const int J0 = PB + 1 + (item / n_strips) * band;
-  const int J1 = min(J0 + band, nt - 1 - PB);
+  if (item >= n_bands(nt) * ns) return;  // whole warp
+  const int strip = item % ns;
+  const int J0 = 1 + (item / ns) * band;
+  const int J1 = min(J0 + band, nt - 1);
   int col = (strip * STRIP - 4 * HL + 4 * lane) % np;  // first of the lane's 4 columns, periodic
   col = col < 0 ? col + np : col;
   const bool vec = (np & 3) == 0;
@@ -980,36 +1060,59 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const Re
   const bool lane_out = lane >= HL && lane < LANES - HL && first_out < np;
   const int n_out = lane_out ? min(4, np - first_out) : 0;
   extern __shared__ __align__(16) float4 rings[];
-  const int tmin = J0 - K;        // first row loaded
-  const int t_end = J1 - 1 + kk;  // last row loaded
+  const int tmin = max(J0 - K, 0);  // first row loaded
+  const int t_end = J1 - 1 + kk;    // last row step (rows past nt-1 are not loaded)
 #ifdef SFT_DEBUG
-  // every row the band loads or writes lies in [tmin, t_end]; a band or a
+  // every row the band loads or writes lies in [tmin, nt-1]; a band or a
   // column outside the realization skips the work item (whole warp: the
   // march shuffles across lanes) after its check is recorded
   const bool dbg_bad = dbg_check(DBG_FUSED_FIRST, tmin, 0, nt - 1) != tmin ||
-                       dbg_check(DBG_FUSED_LAST, t_end, tmin, nt - 1) != t_end ||
+                       dbg_check(DBG_FUSED_LAST, J1, J0, nt - 1) != J1 ||
                        dbg_check(DBG_FUSED_COL, col, 0, vec ? np - 4 : np - 1) != col;
   if (__any_sync(0xffffffffu, dbg_bad)) return;
 #endif
   March S;
-  S.rc = rings + warp * RING_F4;
+  S.rc = rings + warp * RING_F4 + lane;
   S.ra = S.rc + D * LANES;
   S.rg = S.ra + D * LANES;
-  // band geometry, rows tmin-K .. tmin+band+2K-1 (clamped), then the
-  // coefficient table ring
-  float4* sg = rings + WARPS * RING_F4 + warp * (GROWS + 2 * K * DG);
-  S.geo = sg;
-  S.tab = sg + GROWS;
-  S.gbase = tmin - K;
-  const RowGeo<float>* grow = geo + d.geo;
-  for (int i = lane; i < band + 3 * K; i += LANES) {
-    const int row = min(max(S.gbase + i, 0), nt - 1);
-    const float cN = grow[row].cN, cS = grow[row].cS, cE = grow[row].cE;
-    sg[i] = make_float4(cN, cS, cE, -(cN + cS + 2.f * cE));
+  S.tab = rings + WARPS * RING_F4 + warp * TAB_F4;
+  float* spole = reinterpret_cast<float*>(rings + WARPS * (RING_F4 + TAB_F4)) + warp * 2 * K;
+  S.pole = spole;
+  S.geo = reinterpret_cast<const float*>(geo + d.geo) + (lane & 3);
+  S.rmax = min(t_end, nt - 1);
+  S.strip = strip;
+  S.ns = ns;
+  S.part_out = part + d.poff + part_io(1 - pin, 0, 0, 1, 0, ns);
+  // pole values of this launch for the poles the band's rows reach (a level
+  // on the pole row) or whose pole row the band owns (the first band the
+  // north pole, the last band the south pole): the owner writes the pole
+  // row of the outputs for this strip's columns
+  for (int pole = 0; pole < 2; ++pole) {
+    const bool north = pole == 0;
+    const bool own = north ? J0 == 1 : J1 == nt - 1;
+    if (!own && (north ? tmin != 0 : t_end < nt)) continue;
+    const double last = pole_values(north, d, p, coef, j0, kk, geo, shc[d.shape], gC, gA, gG, zero_m2,
+                                    part + d.poff, pin, spole + pole * K, lane);
+    __syncwarp();
+    if (!own) continue;
+    const float pk = spole[pole * K + kk - 1];
+    const float pk1 = kk >= 2 ? spole[pole * K + kk - 2] : gC[(int64_t)(north ? 0 : nt - 1) * pitch];
+    const int64_t ro = (int64_t)(north ? 0 : nt - 1) * pitch;
+    for (int e = 0; e < n_out; ++e) {
+      const int c = first_out + e;
+      if (fin) {
+        const float v = float(double(Bs[ro + c]) + last);
+        if (!isfinite(v)) atomicOr(status, 1);
+        Bs[ro + c] = v;
+      } else {
+        oC[ro + c] = pk;
+        oA[ro + c] = pk1;
+      }
+    }
   }
   {
     // lane = 4 (level - 1) + coefficient: a1 = md cN, a2 = md cS, a3 = md cE, a0 = mu + md cC
-    const Coef<float> c = s_cf[lane >> 2];
+    const Coef<float> c = s_cf[min(lane >> 2, K - 1)];
     S.kmul = c.mut * nudt;
     S.kadd = (lane & 3) == 3 ? c.mu : 0.f;
   }
@@ -1018,22 +1121,20 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const Re
     const Coef<float> c = s_cf[m];
     S.lv[m] = LevelNG{make_float2(c.nu, c.nu), make_float2(c.gsum, c.gsum)};
   }
-  __syncwarp();
-  // coefficients of the K rows above the first loaded one (read by the
-  // pipeline's first steps, whose results never reach an output)
-  for (int r = tmin - K; r < tmin; ++r) table_row(S, r, lane);
-  __syncwarp();
 #pragma unroll
   for (int l = 0; l < K; ++l)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) S.Win[l][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  S.d2m1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < 3; ++q) S.W[l][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.a_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.nC = gC + (int64_t)tmin * pitch + col;
+  S.nA = gA + (int64_t)tmin * pitch + col;
+  S.nG = gG + (int64_t)tmin * pitch + col;
   bool bad = false;
   // (kk == K, np % 4 == 0) is the hot instance; the others serve the last
-  // pass of a realization and grids whose rows are not float4-aligned
-#define SFT_BAND(F, V)                                                                              \
-  march_band<F, V>(S, tmin, t_end, kk, gA, gC, gG, pitch, np, col, zero_m2, J0, fin, oA, oC, Bs, \
-                   lane_out, n_out, bad, lane)
+  // launch of a realization and grids whose rows are not float4-aligned
+#define SFT_BAND(F, V)                                                                                          \
+  march_band<F, V>(S, tmin, t_end, kk, nt, pitch, np, col, zero_m2, J0, fin, oA, oC, Bs, lane_out, n_out, bad, \
+                   lane)
   if (vec) {
     if (kk == K) SFT_BAND(true, true);
     else SFT_BAND(false, true);
@@ -1046,19 +1147,61 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, int n_caps, int skip, const Re
   if (bad) atomicOr(status, 1);
 }
 
+// Ring-sum partials of the rows 1..K from each pole for the first fused
+// launch of a step: of stage 1's output delta_1 (input C of that launch,
+// buffer 0) and of G (all launches of the step).  One block per (pole
+// tile, row): tiles hold a north (kind 1) and a south (kind 2) tile per
+// realization; warp w forms strips w, w+4, ... over the same columns as the
+// interior's work items.
+__global__ void __launch_bounds__(fused::THREADS)
+ring_sums_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ rd, const float* __restrict__ D1,
+                 const float* __restrict__ G, double* __restrict__ part) {
+  using namespace fused;
+  const Tile tl = tiles[blockIdx.x / K];
+  const int pole = (tl.kind & 3) == 1 ? 0 : 1, row = 1 + blockIdx.x % K;
+  const RealDesc d = rd[tl.r];
+  const int ns = n_strips(d.np);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ro = d.woff + (int64_t)(pole == 0 ? row : d.nt - 1 - row) * d.pitch;
+  for (int s = warp; s < ns; s += WARPS) {
+    CSum sc, sg;
+    if (lane < LANES - 2 * HL) {
+      const int c0 = s * STRIP + 4 * lane;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (c0 + e < d.np) {
+          sc.add(D1[ro + c0 + e]);
+          sg.add(G[ro + c0 + e]);
+        }
+    }
+    const double tc = warp_csum(sc), tg = warp_csum(sg);
+    if (lane == 0) {
+      part[d.poff + part_io(0, pole, 0, row, s, ns)] = tc;
+      part[d.poff + part_g(pole, row, s, ns)] = tg;
+    }
+  }
+}
+
 cudaError_t prepare_rkl2_fused() {
   return cudaFuncSetAttribute(rkl2_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)fused::kSmemBytes);
 }
 
-cudaError_t launch_rkl2_fused(int n_tiles, int n_caps, int cap_total, cudaStream_t st, const Tile* tiles,
-                              const RealDesc* rd, const StepParam* sp, const RowGeo<float>* geo,
-                              const ShapeConst* shc, const Coef<float>* coef, float* B, const float* G,
-                              const float* Dm2, const float* Dm1, float* Om2, float* Om1, float* polar,
-                              int j0, int* status) {
+cudaError_t launch_ring_sums(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                             const float* D1, const float* G, double* part) {
   if (n_tiles <= 0) return cudaSuccess;
-  rkl2_fused_kernel<<<n_tiles, fused::THREADS, fused::kSmemBytes, st>>>(
-      tiles, n_caps, cap_total - n_caps, rd, sp, geo, shc, coef, B, G, Dm2, Dm1, Om2, Om1, polar, j0, status);
+  ring_sums_kernel<<<n_tiles * fused::K, fused::THREADS, 0, st>>>(tiles, rd, D1, G, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rkl2_fused(int n_tiles, cudaStream_t st, const Tile* tiles, const RealDesc* rd,
+                              const StepParam* sp, const RowGeo<float>* geo, const ShapeConst* shc,
+                              const Coef<float>* coef, float* B, const float* G, const float* Dm2,
+                              const float* Dm1, float* Om2, float* Om1, double* part, int pin, int j0,
+                              int* status) {
+  if (n_tiles <= 0) return cudaSuccess;
+  rkl2_fused_kernel<<<n_tiles, fused::THREADS, fused::kSmemBytes, st>>>(tiles, rd, sp, geo, shc, coef, B, G, Dm2,
+                                                                         Dm1, Om2, Om1, part, pin, j0, status);
   return cudaGetLastError();
 }
 
@@ -1103,37 +1246,6 @@ __device__ double block_min(double v, double* sm) {
 }
 
 }  // namespace
-
-// Error-free transformations in FP32 (Knuth's TwoSum; the FMA form of
-// Dekker's TwoProduct): s + e equals a + b exactly, p + e equals a * b.
-// The _rn intrinsics keep the compiler from contracting a product into
-// these sums (an FMA there would break exactness).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// A compensated FP32 sum (Ogita, Rump and Oishi's Sum2): s + c tracks the
-// exact sum of the added terms; the error of c is of order n^2 u^2 sum |x|
-// for n terms (u = 2^-24), about 2e-13 sum |x| for a thread's 8 terms.
-struct CSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    float e;
-    two_sum(s, x, s, e);
-    c += e;
-  }
-  // x * (hi + lo), with hi + lo an FP64 value split into two floats
-  __device__ __forceinline__ void add_product(float x, float hi, float lo) {
-    const float p = __fmul_rn(x, hi);
-    const float ep = fmaf(x, hi, -p);  // x * hi - p, exactly
-    float e;
-    two_sum(s, p, s, e);
-    c += e + fmaf(x, lo, ep);
-  }
-  __device__ __forceinline__ double value() const { return double(s) + double(c); }
-};
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)

@@ -294,8 +294,9 @@ def test_error_codes():
 ])
 def test_fused_rkl2_matches_single_stage_launches(shapes):
     """K RKL2 stages per launch (register march over bands with a K-point
-    halo, full-ring cap blocks) against one launch per stage: the same stages
-    in another rounding order, so the maps agree to FP32 rounding."""
+    halo; pole values from the ring-summed recurrence) against one launch per
+    stage: the same stages in another rounding order, so the maps agree to
+    FP32 rounding."""
     outs = {}
     for fused in (False, True):
         g, params, maps = _batch(shapes, "fp32", seed=31)
