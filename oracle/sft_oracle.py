@@ -440,6 +440,68 @@ def rkl2_advance(Y0, dt, L, s):
     return Ym1
 
 
+# --------------------------------------------------------------------------
+# Sec. 3.7.2: RKG2(3/2) super time stepping (the paper's default; its
+# coefficients are only cited).  Reading: the second-order scheme built like
+# RKL2 on the Gegenbauer polynomials C_j = C_j^(3/2) instead of the Legendre
+# polynomials: R_j(z) = a_j + b_j C_j(1 + w1 z), with w1 and b_j fixed by
+# R_s(0) = R_s'(0) = R_s''(0) = 1 (second order), the three-term Gegenbauer
+# recurrence j C_j(x) = (2j+1) x C_{j-1}(x) - (j+1) C_{j-2}(x) giving the
+# stages, and b_0 = b_1 = b_2 as RKL2 takes them.  From C_j(1) =
+# (j+1)(j+2)/2, C_j'(1) = j(j+1)(j+2)(j+3)/8 and C_j''(1) =
+# (j-1)j(j+1)(j+2)(j+3)(j+4)/48:  w1 = 6/((s-1)(s+4)),
+# b_j = 4(j-1)(j+4)/(3j(j+1)(j+2)(j+3)), a_j = 1 - b_j C_j(1), stable for
+# z in [-(s-1)(s+4)/3, 0], i.e. dt <= dt_E (s^2+3s-4)/6.
+# --------------------------------------------------------------------------
+def rkg2_stage_count(dt, dt_euler):
+    """Smallest s >= 2 with dt <= dt_euler (s^2 + 3s - 4)/6."""
+    if not math.isfinite(dt_euler):
+        return 2
+    s = max(2, math.ceil(0.5 * (-3.0 + math.sqrt(25.0 + 24.0 * dt / dt_euler))))
+    while (s * s + 3 * s - 4) * dt_euler < 6.0 * dt:
+        s += 1
+    while s > 2 and ((s - 1) ** 2 + 3 * (s - 1) - 4) * dt_euler >= 6.0 * dt:
+        s -= 1
+    return s
+
+
+def rkg2_coefficients(s):
+    """RKG2(3/2) coefficients for s stages, arrays indexed by stage j = 0..s:
+    mu, nu, mut (mu-tilde), gt (gamma-tilde), as rkl2_coefficients."""
+    w1 = 6.0 / ((s - 1.0) * (s + 4.0))
+    b = np.empty(s + 1)
+    for j in range(2, s + 1):
+        b[j] = 4.0 * (j - 1.0) * (j + 4.0) / (3.0 * j * (j + 1.0) * (j + 2.0) * (j + 3.0))
+    b[0] = b[1] = b[2]
+    cj1 = np.array([(j + 1.0) * (j + 2.0) / 2.0 for j in range(s + 1)])   # C_j(1)
+    a = 1.0 - b * cj1
+    mu = np.zeros(s + 1)
+    nu = np.zeros(s + 1)
+    mut = np.zeros(s + 1)
+    gt = np.zeros(s + 1)
+    mut[1] = 3.0 * b[1] * w1          # C_1'(1) b_1 w1
+    for j in range(2, s + 1):
+        mu[j] = (2.0 * j + 1.0) / j * b[j] / b[j - 1]
+        nu[j] = -(j + 1.0) / j * b[j] / b[j - 2]
+        mut[j] = mu[j] * w1
+        gt[j] = -a[j - 1] * mut[j]
+    return mu, nu, mut, gt
+
+
+def rkg2_advance(Y0, dt, L, s):
+    """One RKG2(3/2) super-step of s stages for dY/dt = L(Y): the stage
+    recurrence of rkl2_advance with the RKG2 coefficients."""
+    mu, nu, mut, gt = rkg2_coefficients(s)
+    LY0 = L(Y0)
+    Ym2 = Y0
+    Ym1 = Y0 + mut[1] * dt * LY0
+    for j in range(2, s + 1):
+        Y = (mu[j] * Ym1 + nu[j] * Ym2 + (1.0 - mu[j] - nu[j]) * Y0
+             + mut[j] * dt * L(Ym1) + gt[j] * dt * LY0)
+        Ym2, Ym1 = Ym1, Y
+    return Ym1
+
+
 def fe_diffusion_advance(B, dt, L, dt_euler):
     """Explicit forward Euler diffusion (Sec. 3.7.2, reference/testing),
     sub-cycled at the Euler limit."""
@@ -654,7 +716,7 @@ class Params:
     nu: float = 500.0
     adv_space: str = "weno3"     # "weno3" | "upwind"
     adv_time: str = "ssprk43"    # "ssprk43" | "ssprk33" | "fe"
-    diffusion: str = "rkl2"      # "rkl2" | "fe" | "off"
+    diffusion: str = "rkl2"      # "rkl2" | "rkg2" | "fe" | "off"
     advection: bool = True
     alpha_uw: float = 1.0
     safety: float = 0.9
@@ -705,6 +767,8 @@ class Realization:
     def _D(self, B, dt):
         if self.p.diffusion == "rkl2":
             return rkl2_advance(B, dt, self.L, rkl2_stage_count(dt, self.dt_euler))
+        if self.p.diffusion == "rkg2":
+            return rkg2_advance(B, dt, self.L, rkg2_stage_count(dt, self.dt_euler))
         if self.p.diffusion == "fe":
             return fe_diffusion_advance(B, dt, self.L, self.dt_euler)
         return B

@@ -247,3 +247,79 @@ def test_fe_diffusion_stable_at_the_limit_and_unstable_beyond():
     h = 1.05 * 2.0 / abs(lam[i].real)
     grown = O.fe_diffusion_advance(v, 200 * h, lambda y: M @ y, h)
     assert np.abs(grown).max() > 1e3 * np.abs(v).max()
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.7.2: RKG2(3/2), the paper's default super time stepper
+# --------------------------------------------------------------------------
+def _rkg2_scalar(s, z, record=None):
+    z = np.asarray(z, dtype=np.complex128)
+
+    def L(y):
+        if record is not None:
+            record.append(np.array(y))
+        return z * y
+    return O.rkg2_advance(np.ones_like(z), 1.0, L, s)
+
+
+@pytest.mark.parametrize("s", [2, 3, 5, 16, 81, 400])
+def test_rkg2_is_the_shifted_gegenbauer_polynomial(s):
+    """The s-stage recurrence equals a + b C_s(1 + w1 z), C_s the Gegenbauer
+    polynomial with parameter 3/2 (scipy), with w1 = C_s'(1)/C_s''(1),
+    b = C_s''(1)/C_s'(1)^2, a = 1 - b C_s(1): the derivatives from
+    d/dx C_n^(l) = 2 l C_{n-1}^(l+1) evaluated by scipy at x = 1."""
+    from scipy.special import eval_gegenbauer as C
+    c1 = 3.0 * C(s - 1, 2.5, 1.0)
+    c2 = 15.0 * C(s - 2, 3.5, 1.0) if s >= 2 else 0.0
+    w1, b = c1 / c2, c2 / c1 ** 2
+    a = 1.0 - b * C(s, 1.5, 1.0)
+    z = np.linspace(-2.0 / w1, 0.0, 997)
+    want = a + b * C(s, 1.5, 1.0 + w1 * z)
+    got = _rkg2_scalar(s, z).real
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 7, 16, 50, 145, 600])
+def test_rkg2_stable_on_its_interval_with_bounded_stages(s):
+    """|R_s(z)| <= 1 on [-(s-1)(s+4)/3, 0], and so is every internal stage
+    (internal stability)."""
+    z = np.linspace(-(s - 1.0) * (s + 4.0) / 3.0, 0.0, 4001)
+    stages = []
+    out = _rkg2_scalar(s, z, stages)
+    assert np.abs(out).max() <= 1.0 + 1e-9
+    assert max(np.abs(y).max() for y in stages) <= 1.0 + 1e-9
+    # and it is not stable much beyond the interval (odd s ends at R = -1 + 2a_s... > -1)
+    zz = np.array([-(s - 1.0) * (s + 4.0) / 3.0 * 1.3])
+    assert abs(_rkg2_scalar(s, zz)[0]) > 1.0
+
+
+@pytest.mark.parametrize("s", [2, 5, 40])
+def test_rkg2_is_second_order(s):
+    for z in (1e-2, 2e-3):
+        err = abs(_rkg2_scalar(s, [-z])[0] - (1 - z + z * z / 2))
+        assert err < 0.5 * z ** 3
+
+
+def test_rkg2_stage_count_is_minimal():
+    for ratio in (0.3, 1.0, 1.01, 7.9, 20888.0, 1.4e7):
+        s = O.rkg2_stage_count(ratio, 1.0)
+        assert (s * s + 3 * s - 4) / 6.0 >= ratio
+        assert s == 2 or ((s - 1) ** 2 + 3 * (s - 1) - 4) / 6.0 < ratio
+
+
+def test_soccer_ball_one_rkg2_step_matches_paper(paper_values):
+    """Sec. 3.7.2: one 672 hr RKG2(3/2) step of the diffusion-only soccer ball
+    at 512x1024 ends with HH = 6.3e-5 (RKL2: 8.0e-5), and takes more stages
+    than RKL2 in the ratio of the printed run times (0.55 s / 0.45 s)."""
+    v = paper_values["soccer_ball_rkg2_one_step_hh"]
+    nu = v["nu_km2_s"] * O.KM2_S_TO_RS2_HR
+    g = O.Grid(v["nt"], v["np"])
+    M = O.diffusion_matrix(g, O.constant_nu(g, nu))
+    dte = 1.0 / np.abs(M.diagonal()).max()
+    s = O.rkg2_stage_count(v["t_hours"], dte)
+    u0 = O.unique_unknowns(I.soccer_ball(g.nt, g.np))
+    u = O.rkg2_advance(u0, v["t_hours"], lambda y: M @ y, s)
+    ex = O.unique_unknowns(I.soccer_ball(g.nt, g.np, nu, v["t_hours"]))
+    assert O.hh_metric(u, ex) == pytest.approx(v["value"], rel=v["rel_tol"])
+    r = paper_values["rkg2_over_rkl2_time"]
+    assert s / O.rkl2_stage_count(v["t_hours"], dte) == pytest.approx(r["value"], rel=r["rel_tol"])
