@@ -82,8 +82,10 @@ typedef enum { SFT_FP32 = 0, SFT_FP64 = 1 } sft_prec;
 enum { SFT_ADV_WENO3_CSH = 0, SFT_ADV_UPWIND = 1 };
 /* advection time scheme (Sec. 3.6.2) */
 enum { SFT_TIME_SSPRK43 = 0, SFT_TIME_SSPRK33 = 1, SFT_TIME_FE = 2 };
-/* diffusion time scheme (Sec. 3.7.2) */
-enum { SFT_DIFF_RKL2 = 0, SFT_DIFF_OFF = 1 };
+/* diffusion time scheme (Sec. 3.7.2): the RKL2 super time stepper
+ * (s = min{s >= 2 : dt <= dt_E (s^2+s-2)/4} stages), RKG2(3/2) (the
+ * paper's default; s = min{s >= 2 : dt <= dt_E (s^2+3s-4)/6}), or none */
+enum { SFT_DIFF_RKL2 = 0, SFT_DIFF_OFF = 1, SFT_DIFF_RKG2 = 2 };
 /* operator splitting of one step (Sec. 3.5): Lie, Eq. (num_opsplit_nostrang):
  * A(dt) then D(dt); Strang, Eq. (num_opsplit_strang) with the source the
  * identity: A(dt/2), D(dt), A(dt/2) -- the flow then allows twice the step */
@@ -213,8 +215,8 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params);
 
 /*
  * Advance every realization to t_target_hours (Sec. 3.4, 3.5): each time
- * step is dt_r = min(t_target - t_r, CFL limit of r); advection then RKL2
- * diffusion with s_r = min{s >= 2 : dt_r <= dt_E,r (s^2+s-2)/4} stages.
+ * step is dt_r = min(t_target - t_r, CFL limit of r); advection then the
+ * super time stepped diffusion (RKL2 or RKG2(3/2), s_r stages as above).
  * All realizations step in lockstep (one batched launch per stage); a
  * realization that has reached the target idles.  max_steps > 0 stops after
  * that many loop iterations.  *steps_taken (may be NULL) receives the number

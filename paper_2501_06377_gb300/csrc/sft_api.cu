@@ -398,6 +398,48 @@ int rkl2_stages(double dt, double dte) {
   return s;
 }
 
+// RKG2(3/2) stage count (Sec. 3.7.2): smallest s >= 2 with
+// dt <= dt_E (s^2 + 3s - 4) / 6.
+int rkg2_stages(double dt, double dte) {
+  if (!(dt > 0.0)) return 0;
+  if (!std::isfinite(dte)) return 0;
+  int s = (int)std::ceil(0.5 * (-3.0 + std::sqrt(25.0 + 24.0 * dt / dte)));
+  if (s < 2) s = 2;
+  while ((double)(s * (int64_t)s + 3 * s - 4) * dte < 6.0 * dt) ++s;
+  while (s > 2 && (double)((s - 1) * (int64_t)(s - 1) + 3 * (s - 1) - 4) * dte >= 6.0 * dt) --s;
+  return s;
+}
+
+// Stage count of a realization's diffusion scheme for a step of dt hours.
+int sts_stages(int scheme, double dt, double dte) {
+  return scheme == SFT_DIFF_RKL2 ? rkl2_stages(dt, dte) : scheme == SFT_DIFF_RKG2 ? rkg2_stages(dt, dte) : 0;
+}
+
+// RKG2(3/2) coefficients for stages 0..s in the increment form of rkl2_coefs:
+// the RKL2 construction on the Gegenbauer polynomials C_j^(3/2),
+// R_j(z) = a_j + b_j C_j(1 + w1 z), w1 = 6 / ((s-1)(s+4)),
+// b_j = 4(j-1)(j+4) / (3j(j+1)(j+2)(j+3)) (b_0 = b_1 = b_2), C_j(1) =
+// (j+1)(j+2)/2, a_j = 1 - b_j C_j(1); the stages follow the recurrence
+// j C_j(x) = (2j+1) x C_{j-1}(x) - (j+1) C_{j-2}(x).
+template <typename T>
+void rkg2_coefs(int s, std::vector<Coef<T>>& out) {
+  const double w1 = 6.0 / ((s - 1.0) * (s + 4.0));
+  auto b = [](int j) {
+    const double jj = j < 2 ? 2.0 : (double)j;
+    return 4.0 * (jj - 1.0) * (jj + 4.0) / (3.0 * jj * (jj + 1.0) * (jj + 2.0) * (jj + 3.0));
+  };
+  auto a = [&](int j) { return 1.0 - b(j) * (j + 1.0) * (j + 2.0) / 2.0; };
+  out.push_back(Coef<T>{T(0), T(0), T(0), T(0)});  // stage 0 unused
+  out.push_back(Coef<T>{T(0), T(0), T(3.0 * b(1) * w1), T(0)});
+  for (int j = 2; j <= s; ++j) {
+    const double mu = (2.0 * j + 1.0) / j * b(j) / b(j - 1);
+    const double nu = -(j + 1.0) / j * b(j) / b(j - 2);
+    const double mut = mu * w1;
+    const double gt = -a(j - 1) * mut;
+    out.push_back(Coef<T>{T(mu), T(nu), T(mut), T(mut + gt)});
+  }
+}
+
 // RKL2 coefficients (Meyer, Balsara & Aslam 2014) for stages 0..s, stored in
 // the increment form used by rkl2_stage_kernel: {mu_j, nu_j, mu~_j, mu~_j + gamma~_j}.
 template <typename T>
@@ -618,7 +660,8 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     p.inv_b0 = ri.fp.atten_b0 > 0.0 ? 1.0 / ri.fp.atten_b0 : 0.0;
     p.cap_nu = ri.cap_nu;
     p.coef = (int)coefs.size();
-    if (s[i] > 0) rkl2_coefs<T>(s[i], coefs);
+    if (s[i] > 0 && ri.fp.diffusion == SFT_DIFF_RKG2) rkg2_coefs<T>(s[i], coefs);
+    else if (s[i] > 0) rkl2_coefs<T>(s[i], coefs);
     else coefs.push_back(Coef<T>{});
     const double cells = (double)sh.nt * sh.np;
     if (ri.fp.advection) c->cells_adv += cells;
@@ -871,7 +914,7 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
         ri.rfe.lifetime_hours > 0.0)
       lim = std::min(lim, ri.rfe.lifetime_hours);  // a step spans at most two source segments
     dt[i] = rem <= lim ? rem : lim;
-    s[i] = ri.fp.diffusion == SFT_DIFF_RKL2 ? rkl2_stages(dt[i], ri.dt_euler) : 0;
+    s[i] = sts_stages(ri.fp.diffusion, dt[i], ri.dt_euler);
     *any = true;
   }
   if (!*any) return SFT_OK;
@@ -1171,7 +1214,7 @@ sft_status set_flows_t(sft_handle h, const sft_flow_params* params) {
     ri.nu = grid_nu ? 1.0 : p.nu * kKm2sToRs2Hr;  // grid-based nu lives in the geometry block
     ri.cap_nu = grid_nu ? grid_nu_face(s, p.nu_grid_alpha, 0) : 1.0;
     ri.dt_cfl = p.advection ? cfl_limit(s, f, p) : INFINITY;
-    ri.dt_euler = p.diffusion != SFT_DIFF_RKL2 ? INFINITY
+    ri.dt_euler = p.diffusion == SFT_DIFF_OFF ? INFINITY
                   : (grid_nu ? euler_limit_grid(s, p.nu_grid_alpha) : euler_limit(s, ri.nu));
     ri.has_flows = true;
   }
@@ -1504,7 +1547,7 @@ sft_status sft_set_flows(sft_handle h, const sft_flow_params* params) {
       return fail(h, SFT_ERR_ARG, "bad adv_space");
     if (p.adv_time < SFT_TIME_SSPRK43 || p.adv_time > SFT_TIME_FE)
       return fail(h, SFT_ERR_ARG, "bad adv_time");
-    if (p.diffusion != SFT_DIFF_RKL2 && p.diffusion != SFT_DIFF_OFF)
+    if (p.diffusion != SFT_DIFF_RKL2 && p.diffusion != SFT_DIFF_RKG2 && p.diffusion != SFT_DIFF_OFF)
       return fail(h, SFT_ERR_ARG, "bad diffusion");
     if (!(p.nu >= 0.0) || !(p.cfl_safety > 0.0) || !std::isfinite(p.d0 + p.d2 + p.d4 + p.m1 + p.m3 + p.m5))
       return fail(h, SFT_ERR_ARG, "bad flow parameters (nu >= 0, cfl_safety > 0, finite)");
@@ -1797,7 +1840,7 @@ sft_status sft_step_plan(sft_handle h, int32_t r, double dt_hours, double* dt_cf
   const RealInfo& ri = h->reals[r];
   if (dt_cfl) *dt_cfl = ri.dt_cfl;
   if (dt_euler) *dt_euler = ri.dt_euler;
-  if (stages) *stages = ri.fp.diffusion == SFT_DIFF_RKL2 ? rkl2_stages(dt_hours, ri.dt_euler) : 0;
+  if (stages) *stages = sts_stages(ri.fp.diffusion, dt_hours, ri.dt_euler);
   return SFT_OK;
 }
 

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "SFT_OK", 1: "SFT_ERR_ARG", 2: "SFT_ERR_OOM", 3: "SFT_ERR_CUD
 SFT_FP32, SFT_FP64 = 0, 1
 ADV_SPACE = {"weno3": 0, "upwind": 1}
 ADV_TIME = {"ssprk43": 0, "ssprk33": 1, "fe": 2}
-DIFFUSION = {"rkl2": 0, "off": 1}
+DIFFUSION = {"rkl2": 0, "off": 1, "rkg2": 2}
 SPLITTING = {"lie": 0, "strang": 1}
 
 

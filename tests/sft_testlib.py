@@ -8,7 +8,7 @@ from paper_2501_06377_gb300.sft import FlowParams
 def oracle_params(fp: FlowParams) -> O.Params:
     return O.Params(d0=fp.d0, d2=fp.d2, d4=fp.d4, m1=fp.m1, m3=fp.m3, m5=fp.m5, nu=fp.nu,
                     adv_space=fp.adv_space, adv_time=fp.adv_time,
-                    diffusion="rkl2" if fp.diffusion == "rkl2" else "off",
+                    diffusion=fp.diffusion if fp.diffusion in ("rkl2", "rkg2") else "off",
                     advection=fp.advection, alpha_uw=fp.alpha_uw, safety=fp.cfl_safety,
                     eps_w="h" if fp.eps_w <= 0 else fp.eps_w, atten_b0=fp.atten_b0,
                     splitting=fp.splitting, nu_grid_alpha=fp.nu_grid_alpha)

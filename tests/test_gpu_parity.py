@@ -506,3 +506,42 @@ def test_state_larger_than_the_hbm_budget_is_refused():
     with pytest.raises(SFTError) as e:
         Grid([(257, 512)] * 4, "fp32", hbm_budget=1 << 20)
     assert "OOM" in str(e.value) or "budget" in str(e.value).lower()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fused", [True, False])
+def test_rkg2_matches_oracle(prec, fused):
+    """RKG2(3/2) diffusion (Sec. 3.7.2, the paper's default stepper) with
+    advection, uneven shapes, against the oracle at the parity bars; the
+    FP32 path through the fused launches and through one launch per stage."""
+    shapes = [(37, 64), (64, 136), (41, 520)]
+    g, params, maps = _batch(shapes, prec, seed=21, diffusion="rkg2")
+    if prec == "fp32":
+        kf = g.get_fusion()
+        g.set_fusion(kf if fused else 1)
+    elif fused:
+        pytest.skip("the FP64 path has no fused launches")
+    T = 30.0
+    g.step(T)
+    for r, s in enumerate(shapes):
+        ref = oracle_run(s, params[r], maps[r], T)
+        assert g.step_plan(r, 1.0)[2] == O.rkg2_stage_count(1.0, ref.dt_euler)
+        got = g.get_state(r)
+        bar = 1e-12 if prec == "fp64" else 1e-5
+        assert rel_linf(got, ref.B) <= bar, (s, rel_linf(got, ref.B))
+
+
+def test_rkg2_soccer_ball_one_step_matches_the_paper():
+    """Sec. 3.7.2: one 672 h RKG2(3/2) step of the diffusion-only soccer ball
+    at 512x1024 (FP64 on the GPU) ends with HH = 6.3e-5, in 4588 stages."""
+    nt, np_ = 512, 1024
+    nu = 500.0
+    B0 = I.soccer_ball(nt, np_)
+    fp = FlowParams(nu=nu, advection=False, diffusion="rkg2")
+    g = Grid([(nt, np_)], "fp64")
+    g.set_state(0, B0)
+    g.set_flows([fp])
+    assert g.step_plan(0, 672.0)[2] == 4588
+    g.step(672.0)
+    ex = I.soccer_ball(nt, np_, nu * O.KM2_S_TO_RS2_HR, 672.0)
+    assert O.hh_metric(g.get_state(0), ex) == pytest.approx(6.3e-5, rel=0.05)
