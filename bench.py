@@ -20,6 +20,16 @@ two increments; stage 1 3 words) over the CUDA-event time of the RKL2
 region.  cpu_baseline: the FP64 oracle on a bounded sample, one
 realization per host core (spawned processes).
 
+flux_drift: the largest change of a realization's total signed flux over
+the timed steps relative to its unsigned flux (FP64 diagnostics).  c1: the
+single-realization FP64 configuration (128x256, 27 days) on the GPU, its
+device time and flux drift, and (with the CPU leg) the same run by the FP64
+oracle on a host core with the relative L-inf difference of the final maps.
+surrogate: the learned-surrogate ensemble (512 members x 27 days at
+256x512, surrogate + judge + fallback against the plain solver and a
+rotation-only control) with a reduced training set (--sur-pairs,
+--sur-epochs; bench.py --surrogate runs the full training alone).
+
 Multi-GPU (torchrun): realizations are independent, so each rank runs its
 own 64-realization ensemble (weak scaling, no collective on the data path);
 the timing is the max over ranks.
@@ -44,14 +54,14 @@ import numpy as np  # noqa: E402
 NT, NP, NREAL = 1024, 2048, 64
 
 # DRAM traffic of rkl2_fused_kernel from one ncu capture (16 x 1024x2048
-# ensemble, one pass over all 16 realizations, eight stages, 256-row bands):
-# dram__bytes_read + dram__bytes_write = 1.0588 x the launch's algorithmic
-# bytes (reads +13.6 %: band-overlap rows; writes -5.6 %: dirty lines still
-# in L2 when the launch ends).  Reported per pass as ratio x algorithmic
-# bytes, and only while the kernel sources (comments aside) hash to the
-# profiled ones.
-FUSED_TRAFFIC = {"ratio": 1.0588, "profile": "profiles/rkl2_fused_kernel_ncu_16x1024x2048.md",
-                 "sha256": "f34defb27bf614d589ac09ec7008249055e1ca8f04887ce75d8f58266574a296"}
+# ensemble, one launch over all 16 realizations, eight stages, 256-row bands,
+# pole values from the ring-sum recurrence): dram__bytes_read +
+# dram__bytes_write = 0.9734 x the launch's algorithmic bytes (reads +5 %:
+# band-overlap rows; writes -14 %: dirty lines still in L2 when the launch
+# ends).  Reported per launch as ratio x algorithmic bytes, and only while the
+# kernel sources (comments aside) hash to the profiled ones; otherwise null.
+FUSED_TRAFFIC = {"ratio": 0.9734, "profile": "profiles/rkl2_fused_kernel_ncu_16x1024x2048.md",
+                 "sha256": "c9ee8174458e7301fae12647d2e98027d0d90b70791d8a9425e0e990766206a7"}
 KERNEL_SOURCES = ("paper_2501_06377_gb300/csrc/sft_kernels.cu", "paper_2501_06377_gb300/csrc/sft_device.cuh")
 
 
@@ -150,6 +160,48 @@ def make_inputs(nreal, rank, atten_b0=0.0, splitting="lie"):
     return params, maps
 
 
+C1_SHAPE = (128, 256)
+C1_WORKLOAD = ("plain SFT: 1 realization, FP64, 128x256, Omega(lat) = 13.38 - 2.30 sin^2 - 1.62 sin^4 "
+               "deg/day in the Carrington frame, 15 m/s sin(2 lat) poleward, eta = 500 km^2/s, 10 G dipole "
+               "+ 12 seeded pairs flux balanced, 27 days at CFL steps")
+
+
+def c1_inputs():
+    """The single-realization FP64 configuration: flow parameters and start map."""
+    import sft_inputs as I
+    d = I.omega_to_dr_coeffs(*I.DEFAULT_OMEGA)
+    flow = dict(d0=d[0], d2=d[1], d4=d[2], m1=30.0, m3=0.0, m5=0.0, nu=500.0)
+    return flow, I.initial_map(*C1_SHAPE, seed=1)
+
+
+def run_c1_gpu():
+    """C1 on the GPU: the 27-day run (second of two; the first builds the step
+    graphs), CUDA-event time on the grid's stream, the flux-balanced start map
+    and the final map (host FP64)."""
+    import torch
+    from paper_2501_06377_gb300.sft import FlowParams, Grid
+    flow, B0 = c1_inputs()
+    st = torch.cuda.Stream()
+    g = Grid([C1_SHAPE], "fp64", stream=st)
+    g.set_flows([FlowParams(**flow)])
+    for _ in range(2):
+        g.set_time(0.0)
+        g.set_state(0, B0)
+        g.balance_flux()
+        start = g.get_state(0)
+        d0 = g.diagnostics()[0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        n = g.step(27 * 24.0)
+        e1.record(st)
+        st.synchronize()
+        d1 = g.diagnostics()[0]
+    final = g.get_state(0)
+    g.close()
+    return {"workload": C1_WORKLOAD, "gpu_ms": e0.elapsed_time(e1), "steps": n,
+            "flux_drift": abs(d1["flux_signed"] - d0["flux_signed"]) / d0["flux_pos"]}, start, final
+
+
 # --------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # --------------------------------------------------------------------------
@@ -193,6 +245,17 @@ def _oracle_worker(job):
     return oracle_sample(job[1], job[0])
 
 
+def _c1_oracle_worker(start):
+    """The FP64 oracle over the C1 run from the given (flux-balanced) map:
+    (seconds, final map)."""
+    import oracle as O
+    flow, _ = c1_inputs()
+    r = O.Realization(O.Grid(*C1_SHAPE), O.Params(**flow), start)
+    t0 = time.perf_counter()
+    r.advance(27 * 24.0)
+    return time.perf_counter() - t0, r.B
+
+
 class OraclePool:
     """The oracle over host cores: one realization per process (the ensemble
     is parallel over realizations), worker processes started with spawn
@@ -207,8 +270,12 @@ class OraclePool:
             os.environ[v] = "1"
         self.pool = mp.get_context("spawn").Pool(self.procs)
 
-    def sample(self, n_stages):
+    def sample(self, n_stages, c1_start=None):
+        """One sample over the workers; with c1_start, one more worker task runs
+        the C1 oracle from that map alongside (returned as self.c1)."""
+        c1 = self.pool.apply_async(_c1_oracle_worker, (c1_start,)) if c1_start is not None else None
         res = self.pool.map(_oracle_worker, [(i, n_stages) for i in range(self.procs)])
+        self.c1 = c1.get() if c1 is not None else None
         v = sum(x[0] for x in res)
         ms = statistics.median(x[1] for x in res)
         el = max(x[3] for x in res)
@@ -300,6 +367,7 @@ def run_gpu(args, rank, world, local_rank):
         one_step()
     g.reset_stats()
     g.set_profiling(True)
+    d_start = g.diagnostics()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local_rank) as clk:
@@ -312,6 +380,9 @@ def run_gpu(args, rank, world, local_rank):
         barrier()
     ms = e0.elapsed_time(e1)
     sim_hours = sum(g.get_time()) - t_before  # simulated hours advanced, summed over realizations
+    d_end = g.diagnostics()
+    # total signed flux drift over the timed steps, FP64 diagnostics, worst realization
+    flux_drift = max(abs(b["flux_signed"] - a["flux_signed"]) / a["flux_pos"] for a, b in zip(d_start, d_end))
     st = g.stats()
     ms = max_over_ranks(ms)
     updates = st["cell_updates"] * world
@@ -340,14 +411,27 @@ def run_gpu(args, rank, world, local_rank):
         barrier()
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps)
     bytes_state = nreal * NT * NP * 4
+    c1 = c1_start = c1_final = None
+    if rank == 0 and not args.no_c1:
+        c1, c1_start, c1_final = run_c1_gpu()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool = OraclePool()
         try:
-            v, cms, desc, el = pool.sample(64)
+            v, cms, desc, el = pool.sample(64, c1_start)
         finally:
             pool.close()
         cpu = {"value": v, "unit": "cell-updates/s", "cores": pool.procs, "kind": "oracle", "sample": desc}
+        if pool.c1 is not None and c1 is not None:
+            c1_s, c1_ref = pool.c1
+            c1["oracle_s"] = c1_s
+            c1["rel_linf_vs_oracle"] = float(np.abs(c1_final - c1_ref).max() / np.abs(c1_ref).max())
+            c1["bar"] = 1e-12
+    sur = None
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        sur = surrogate_eval(args.sur_pairs, args.sur_epochs, args.members, args.days)
+        sur["note"] = ("reduced training for the default run (%d pairs x %d epochs; bench.py --surrogate "
+                       "trains on %d x %d)" % (args.sur_pairs, args.sur_epochs, args.pairs, args.epochs))
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -383,12 +467,17 @@ def run_gpu(args, rank, world, local_rank):
             "e2e": {"value": cells_per_step * world / (e2e_ms * 1e-3), "unit": "cell-updates/s",
                     "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state,
                     "ms_per_step": e2e_ms},
+            "flux_drift": flux_drift,
             "gpu_launches": int(st["kernel_launches"] + 2 * st["global_steps"]),
             "gpu_launches_per_step": launches_per_step + 2,
             "clocks": clocks,
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if c1:
+            line["c1"] = c1
+        if sur:
+            line["surrogate"] = sur
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -398,19 +487,17 @@ def run_gpu(args, rank, world, local_rank):
 # --------------------------------------------------------------------------
 # learned surrogate + judge + fallback (256 x 512 ensemble, one-day steps)
 # --------------------------------------------------------------------------
-def run_surrogate(args):
+def surrogate_eval(pairs, epochs, members, days):
     """Train the surrogate on solver-generated one-day pairs, then advance
-    an ensemble for args.days days with judge and fallback, against the plain
-    batched solver and a rotation-only control (trained correction removed)."""
+    an ensemble for `days` days with judge and fallback, against the plain
+    batched solver and a rotation-only control (trained correction removed).
+    Returns the result record (member-days/s, errors, judge counts, timings)."""
     import torch
     import sft_inputs as I
-    from paper_2501_06377_gb300 import build as B
     from paper_2501_06377_gb300 import ensemble as E
     from paper_2501_06377_gb300.sft import Grid
     from paper_2501_06377_gb300.surrogate import Surrogate
 
-    B.build()
-    torch.cuda.set_device(0)
     t_all = time.perf_counter()
     nbase = 64
     g = Grid([(E.H, E.W)] * nbase, "fp32")
@@ -418,66 +505,74 @@ def run_surrogate(args):
     for i in range(nbase):
         g.set_state(i, I.initial_map(E.H, E.W, seed=1000 + i).astype(np.float32))
     g.balance_flux()
-    for i in range(nbase):
-        g.get_state(i, base[i])
+    g.get_states(np.arange(nbase), base)
     torch.cuda.synchronize()
     g.close()
     t0 = time.perf_counter()
-    X, Y, P = E.make_pairs(base, args.pairs, seed=5)
+    X, Y, P = E.make_pairs(base, pairs, seed=5)
     t_pairs = time.perf_counter() - t0
     net = Surrogate(channels=64, modes=48, blocks=4, max_batch=32, seed=1)
     c0 = net.counters()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = E.train(net, X, Y, P, epochs=args.epochs, batch=32, lr=2e-3)
+    hist = E.train(net, X, Y, P, epochs=epochs, batch=32, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     c1 = net.counters()
     del X, Y
     # evaluation ensemble: unseen start maps (rolled), unseen parameters
     rng = np.random.default_rng(11)
-    Pm = torch.from_numpy(E.draw_params(args.members, 11).astype(np.float32)).cuda()
-    S0 = torch.stack([torch.roll(base[int(rng.integers(nbase))], int(rng.integers(E.W)), dims=1)
-                      for _ in range(args.members)]).contiguous()
-    ref, st_plain = E.plain(S0, Pm, args.days)
-    out, st_sur = E.rollout(net, S0, Pm, args.days)
-    err = net.rel_l2(out, ref) if args.members <= net.max_batch else np.concatenate(
-        [net.rel_l2(out[i:i + 32].contiguous(), ref[i:i + 32].contiguous()) for i in range(0, args.members, 32)])
+    Pm = torch.from_numpy(E.draw_params(members, 11).astype(np.float32)).cuda()
+    S0 = E.rolled(base, rng.integers(nbase, size=members), rng.integers(E.W, size=members))
+    ref, st_plain = E.plain(S0, Pm, days)
+    out, st_sur = E.rollout(net, S0, Pm, days)
+    err = np.concatenate([net.rel_l2(out[i:i + 32].contiguous(), ref[i:i + 32].contiguous())
+                          for i in range(0, members, 32)])
     # control: the same network with its learned correction switched off
-    w = net.get_params()
-    ctrl = Surrogate(channels=64, modes=48, blocks=4, max_batch=32, seed=1)
-    wz = w.copy()
-    n_we, n_be = 48 * 64, 64
-    wz[n_we + n_be:n_we + n_be + 64 * 16 + 16] = 0.0   # Wd, bd
-    ctrl.set_params(wz)
-    out_c, st_ctrl = E.rollout(ctrl, S0, Pm, args.days)
+    ctrl = E.rotation_only(net)
+    out_c, st_ctrl = E.rollout(ctrl, S0, Pm, days)
     err_c = np.concatenate([ctrl.rel_l2(out_c[i:i + 32].contiguous(), ref[i:i + 32].contiguous())
-                            for i in range(0, args.members, 32)])
-    line = {
-        "metric": "ensemble simulated member-days/s (surrogate + judge + fallback vs plain solver)",
-        "value": st_sur["member_days_per_s"], "unit": "member-days/s",
+                            for i in range(0, members, 32)])
+    return {
+        "member_days_per_s": st_sur["member_days_per_s"],
         "plain_member_days_per_s": st_plain["member_days_per_s"],
         "speedup_vs_plain": st_sur["member_days_per_s"] / st_plain["member_days_per_s"],
-        "day_rollout_rel_l2_vs_plain": {"days": args.days, "median": float(np.median(err)),
+        "day_rollout_rel_l2_vs_plain": {"days": days, "median": float(np.median(err)),
                                         "p90": float(np.percentile(err, 90)), "max": float(err.max())},
         "accepted_fraction": st_sur["accepted"] / st_sur["member_days"],
         "rejected_drift": st_sur["rejected_drift"], "rejected_spot": st_sur["rejected_spot"],
         "spot_checked": st_sur["spot_checked"],
-        "tile_rows": {"rollout": st_sur.get("tile_rows"), "plain": st_plain.get("tile_rows")},
         "spot_l2_median_by_day": st_sur["spot_l2_median"],
+        "rollout_phase_s": st_sur["phase_s"],
+        "tile_rows": {"rollout": st_sur.get("tile_rows"), "plain": st_plain.get("tile_rows")},
         "control_rotation_only": {"member_days_per_s": st_ctrl["member_days_per_s"],
                                   "accepted_fraction": st_ctrl["accepted"] / st_ctrl["member_days"],
-                                  "rel_l2_median": float(np.median(err_c)), "rel_l2_max": float(err_c.max())},
-        "train": {"pairs": args.pairs, "epochs": args.epochs, "seconds": t_train,
+                                  "spot_l2_median": float(np.median(st_ctrl["spot_l2_median"])),
+                                  "rel_l2_median_vs_plain": float(np.median(err_c)),
+                                  "note": "its proposals fail the judge, so its members follow the plain solver"},
+        "train": {"pairs": pairs, "epochs": epochs, "seconds": t_train,
                   "pair_generation_seconds": t_pairs, "params": net.num_params(),
                   "gemm_tflops": (c1["gemm_flops"] - c0["gemm_flops"]) / t_train / 1e12,
                   "loss_history": hist[::max(1, len(hist) // 12)]},
-        "config": {"workload": "learned surrogate: %d members x 256x512 FP32, %d days, 1-day proposals, "
-                               "judge: flux drift > 1e-4 or spot-check L2 > 2%%, plain-solver fallback"
-                               % (args.members, args.days),
-                   "members": args.members, "days": args.days, "net": "C=64, M=48 modes, L=4, BF16 GEMMs"},
+        "members": members, "days": days,
+        "judge": "flux drift > 1e-4 or spot-check L2 > 2% (32 members a day), plain-solver fallback",
         "seconds_total": time.perf_counter() - t_all,
     }
+
+
+def run_surrogate(args):
+    """The learned-surrogate ensemble alone, at the full training size."""
+    import torch
+    from paper_2501_06377_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    r = surrogate_eval(args.pairs, args.epochs, args.members, args.days)
+    line = {"metric": "ensemble simulated member-days/s (surrogate + judge + fallback vs plain solver)",
+            "value": r["member_days_per_s"], "unit": "member-days/s", **r,
+            "config": {"workload": "learned surrogate: %d members x 256x512 FP32, %d days, 1-day proposals, "
+                                   "judge: flux drift > 1e-4 or spot-check L2 > 2%%, plain-solver fallback"
+                                   % (args.members, args.days),
+                       "members": args.members, "days": args.days, "net": "C=64, M=48 modes, L=4, BF16 GEMMs"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -562,6 +657,11 @@ def main():
     ap.add_argument("--members", type=int, default=512)
     ap.add_argument("--days", type=int, default=27)
     ap.add_argument("--epochs", type=int, default=16)
+    ap.add_argument("--no-c1", action="store_true", help="skip the single-realization FP64 run")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the (reduced-training) surrogate ensemble of the default run")
+    ap.add_argument("--sur-pairs", type=int, default=8000, help="training pairs of the default run's surrogate")
+    ap.add_argument("--sur-epochs", type=int, default=12, help="training epochs of the default run's surrogate")
     ap.add_argument("--smoother", action="store_true",
                     help="grid-based-diffusivity map smoother instead of the solver benchmark")
     ap.add_argument("--maps", type=int, default=64)

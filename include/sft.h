@@ -204,6 +204,24 @@ sft_status sft_get_state(sft_handle h, int32_t r, void* br, int32_t on_device);
  * when r = -1 (checkpoint/resume). */
 sft_status sft_set_time(sft_handle h, int32_t r, double t_hours);
 
+/* Batched forms of sft_set_state / sft_get_state / sft_set_time for a subset
+ * of realizations (an ensemble member subset, Sec. 2.5): idx[0..n) are
+ * realization indices (host array, distinct for sft_set_states), all of one
+ * grid shape; maps is one packed array of n maps in caller layout, map q
+ * (for realization idx[q]) at element q * ntheta * nphi, on the device when
+ * on_device, else in host memory; t_hours[q] (host) is idx[q]'s time.  One
+ * call issues every copy on the handle's stream and, for sft_set_states, one
+ * pole fix-up launch; sft_get_states with host memory synchronises.  The
+ * first bad index or argument fails the call before any copy
+ * (SFT_ERR_ARG). */
+sft_status sft_set_states(sft_handle h, int32_t n, const int32_t* idx, const void* maps, int32_t on_device);
+
+/* The maps of realizations idx[0..n) into the packed array maps (see above). */
+sft_status sft_get_states(sft_handle h, int32_t n, const int32_t* idx, void* maps, int32_t on_device);
+
+/* The times of realizations idx[0..n) to t_hours[0..n) (see above). */
+sft_status sft_set_times(sft_handle h, int32_t n, const int32_t* idx, const double* t_hours);
+
 /* Per-realization simulated times (host array of n_real doubles). */
 sft_status sft_get_time(sft_handle h, double* t_hours);
 

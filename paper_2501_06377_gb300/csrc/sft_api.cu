@@ -1518,6 +1518,86 @@ sft_status sft_get_state(sft_handle h, int32_t r, void* br, int32_t on_device) {
   return SFT_OK;
 }
 
+// Checks a member subset for the batched state calls: indices in range,
+// one grid shape (returned in *shape), distinct when `distinct`.
+static sft_status check_subset(sft_handle h, int32_t n, const int32_t* idx, bool distinct, int* shape) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (n < 0 || (n > 0 && !idx)) return fail(h, SFT_ERR_ARG, "bad member subset");
+  *shape = -1;
+  std::vector<char> seen(distinct ? h->n_real : 0, 0);
+  for (int q = 0; q < n; ++q) {
+    const int r = idx[q];
+    if (r < 0 || r >= h->n_real) return fail(h, SFT_ERR_ARG, "realization index out of range");
+    const int sh = h->reals[r].shape;
+    if (*shape >= 0 && sh != *shape) return fail(h, SFT_ERR_ARG, "member subset mixes grid shapes");
+    *shape = sh;
+    if (distinct) {
+      if (seen[r]) return fail(h, SFT_ERR_ARG, "repeated realization in the subset");
+      seen[r] = 1;
+    }
+  }
+  return SFT_OK;
+}
+
+sft_status sft_set_states(sft_handle h, int32_t n, const int32_t* idx, const void* maps, int32_t on_device) {
+  int shape = -1;
+  sft_status st = check_subset(h, n, idx, true, &shape);
+  if (st != SFT_OK) return st;
+  if (n == 0) return SFT_OK;
+  if (!maps) return fail(h, SFT_ERR_ARG, "maps is NULL");
+  const ShapeInfo& s = h->shapes[shape];
+  const size_t map_bytes = (size_t)s.nt * s.np * h->elem;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int q = 0; q < n; ++q) {
+    char* dst = static_cast<char*>(h->state) + h->reals[idx[q]].off * h->elem;
+    const char* src = static_cast<const char*>(maps) + q * map_bytes;
+    if (s.pitch == s.np)
+      SFT_CUDA(h, cudaMemcpyAsync(dst, src, map_bytes, kind, h->stream));
+    else
+      SFT_CUDA(h, cudaMemcpy2DAsync(dst, s.pitch * h->elem, src, s.np * h->elem, s.np * h->elem, s.nt, kind,
+                                    h->stream));
+  }
+  // pole rows from their k = 0 entries, every realization in one launch (idempotent elsewhere)
+  if (h->prec == SFT_FP32)
+    SFT_CUDA(h, launch_fix_poles<float>(h->n_real, h->stream, h->d_desc, ptr<float>(h->state), -1));
+  else
+    SFT_CUDA(h, launch_fix_poles<double>(h->n_real, h->stream, h->d_desc, ptr<double>(h->state), -1));
+  return SFT_OK;
+}
+
+sft_status sft_get_states(sft_handle h, int32_t n, const int32_t* idx, void* maps, int32_t on_device) {
+  int shape = -1;
+  sft_status st = check_subset(h, n, idx, false, &shape);
+  if (st != SFT_OK) return st;
+  if (n == 0) return SFT_OK;
+  if (!maps) return fail(h, SFT_ERR_ARG, "maps is NULL");
+  const ShapeInfo& s = h->shapes[shape];
+  const size_t map_bytes = (size_t)s.nt * s.np * h->elem;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int q = 0; q < n; ++q) {
+    const char* src = static_cast<const char*>(h->state) + h->reals[idx[q]].off * h->elem;
+    char* dst = static_cast<char*>(maps) + q * map_bytes;
+    if (s.pitch == s.np)
+      SFT_CUDA(h, cudaMemcpyAsync(dst, src, map_bytes, kind, h->stream));
+    else
+      SFT_CUDA(h, cudaMemcpy2DAsync(dst, s.np * h->elem, src, s.pitch * h->elem, s.np * h->elem, s.nt, kind,
+                                    h->stream));
+  }
+  if (!on_device) return sync(h);
+  return SFT_OK;
+}
+
+sft_status sft_set_times(sft_handle h, int32_t n, const int32_t* idx, const double* t_hours) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (n < 0 || (n > 0 && (!idx || !t_hours))) return fail(h, SFT_ERR_ARG, "NULL argument");
+  for (int q = 0; q < n; ++q) {
+    if (idx[q] < 0 || idx[q] >= h->n_real) return fail(h, SFT_ERR_ARG, "realization index out of range");
+    if (!std::isfinite(t_hours[q])) return fail(h, SFT_ERR_ARG, "time must be finite");
+  }
+  for (int q = 0; q < n; ++q) h->reals[idx[q]].t = t_hours[q];
+  return SFT_OK;
+}
+
 sft_status sft_set_time(sft_handle h, int32_t r, double t_hours) {
   if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
   if (r < -1 || r >= h->n_real) return fail(h, SFT_ERR_ARG, "realization index out of range");

@@ -63,6 +63,17 @@ def _grid(n, params, stream=None):
     return g
 
 
+def rolled(base_maps, which, shifts):
+    """base_maps[which[q]] rolled by shifts[q] longitudes (torch.roll along
+    phi for every q at once), as one packed [n, H, W] tensor."""
+    import torch
+    k = torch.arange(W, device=base_maps.device)
+    s = torch.as_tensor(np.asarray(shifts), device=base_maps.device)
+    cols = (k[None, :] - s[:, None]) % W
+    sel = base_maps[torch.as_tensor(np.asarray(which), device=base_maps.device)]
+    return torch.gather(sel, 2, cols[:, None, :].expand(-1, H, -1)).contiguous()
+
+
 def make_pairs(base_maps, n_pairs, seed=5, chunk=512, max_start_day=9):
     """(X, Y, P): X, Y [n, H, W] float32 CUDA tensors one day apart, P [n, 5]."""
     import torch
@@ -74,17 +85,14 @@ def make_pairs(base_maps, n_pairs, seed=5, chunk=512, max_start_day=9):
     for c0 in range(0, n_pairs, chunk):
         n = min(chunk, n_pairs - c0)
         g = _grid(n, P[c0:c0 + n])
-        for i in range(n):
-            m = base_maps[int(rng.integers(nb))]
-            g.set_state(i, torch.roll(m, int(rng.integers(W)), dims=1).contiguous())
+        members = np.arange(n)
+        g.set_states(members, rolled(base_maps, rng.integers(nb, size=n), rng.integers(W, size=n)))
         d0 = int(rng.integers(0, max_start_day + 1))
         if d0:
             g.step(d0 * DAY)
-        for i in range(n):
-            g.get_state(i, X[c0 + i])
+        g.get_states(members, X[c0:c0 + n])
         g.step((d0 + 1) * DAY)
-        for i in range(n):
-            g.get_state(i, Y[c0 + i])
+        g.get_states(members, Y[c0:c0 + n])
         torch.cuda.synchronize()
         g.close()
     return X, Y, torch.from_numpy(P.astype(np.float32)).cuda()
@@ -112,6 +120,20 @@ def train(net: Surrogate, X, Y, P, epochs=10, batch=32, lr=2e-3, wd=1e-4, seed=0
     return hist
 
 
+def rotation_only(net: Surrogate):
+    """The rotation-only control: a copy of net whose learned correction is
+    switched off (decoder Wd, bd zeroed; parameter order of include/sfs.h:
+    We[48][C], be[C], Wd[C][16], bd[16], ...), so that it proposes the map
+    rotated by the day's differential rotation and nothing else."""
+    w = net.get_params()
+    C = net.channels
+    o = 48 * C + C
+    w[o:o + C * 16 + 16] = 0.0
+    ctrl = Surrogate(channels=net.channels, modes=net.modes, blocks=net.blocks, max_batch=net.max_batch, seed=0)
+    ctrl.set_params(w)
+    return ctrl
+
+
 def propose(net: Surrogate, S, P, out):
     for c0 in range(0, S.shape[0], net.max_batch):
         c1 = min(S.shape[0], c0 + net.max_batch)
@@ -123,77 +145,104 @@ def _fluxes(net: Surrogate, maps):
     return net.flux(maps)
 
 
+def _dev_index(a):
+    """A host index or mask array on the device without a synchronising copy
+    (pinned host buffer, non-blocking upload on the current stream)."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().to("cuda", non_blocking=True)
+
+
+def _advance_subset(g, gs, S, members, t0, t1):
+    """Queue the plain solver's day [t0, t1] for the given members (every
+    other member idles at t1) on the grid's stream gs, after the maps of S
+    written so far on the current stream."""
+    import torch
+    g.set_time(t1)
+    if len(members):
+        sel = S.index_select(0, _dev_index(np.asarray(members, dtype=np.int64))).contiguous()
+        gs.wait_stream(torch.cuda.current_stream())
+        g.set_states(members, sel)
+        g.set_times(members, t0)
+    g.step(t1)
+
+
+def _fetch(g, gs, members):
+    """The grid's maps of the given members as one packed tensor, usable on the
+    current stream."""
+    import torch
+    out = torch.empty((len(members), H, W), device="cuda")
+    gs.wait_stream(torch.cuda.current_stream())
+    g.get_states(members, out)
+    torch.cuda.current_stream().wait_stream(gs)
+    return out
+
+
 def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, seed=7, max_fail=0.25):
     """Surrogate + judge + plain-solver fallback.  Returns (final maps, stats).
 
     A day on which more than ``max_fail`` of the spot checks fail rejects
     every proposal of that day (the unchecked members cannot be trusted
-    either); otherwise only the failing members fall back."""
+    either); otherwise only the failing members fall back.  stats["phase_s"]
+    splits the host time of the days: queueing the spot checks' solver day,
+    the proposals and their flux sums (running while the solver day does),
+    waiting for and fetching the solver's maps, and the rest (spot-check
+    L2, updates, flux sums of the accepted maps)."""
     import torch
     n = S0.shape[0]
     params = P.cpu().numpy().astype(np.float64)
-    g = _grid(n, params)
+    gs = torch.cuda.Stream()
+    g = _grid(n, params, stream=gs)
     S = S0.clone()
     prop = torch.empty_like(S)
     rng = np.random.default_rng(seed)
     stats = {"member_days": 0, "accepted": 0, "rejected_drift": 0, "rejected_spot": 0, "spot_checked": 0}
+    ph = {"queue_spot_day": 0.0, "proposals_and_flux": 0.0, "fetch_solver_maps": 0.0, "rest": 0.0}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     phi_old, abs_old = _fluxes(net, S)
     for day in range(days):
+        ta = time.perf_counter()
         t_day0, t_day1 = day * DAY, (day + 1) * DAY
-        chk = rng.choice(n, size=min(spot, n), replace=False)
+        chk = np.sort(rng.choice(n, size=min(spot, n), replace=False))
         run = np.zeros(n, dtype=bool)
         run[chk] = True
         # the plain solver's day for the spot-checked members is queued first
         # (sft_step returns without waiting) so that it runs on the grid's
         # stream while the surrogate proposes on its own
-        for i in range(n):
-            if run[i]:
-                g.set_state(i, S[i])
-            g.set_time(t_day0 if run[i] else t_day1, i)
-        g.step(t_day1)
+        _advance_subset(g, gs, S, chk, t_day0, t_day1)
+        tb = time.perf_counter()
         propose(net, S, P, prop)
         phi_new, abs_new = _fluxes(net, prop)
+        tc = time.perf_counter()
         drift = np.abs(phi_new - phi_old) / np.maximum(abs_old, 1e-300)
         bad = drift > drift_tol
         extra = bad & ~run
         if extra.any():  # drift-rejected members outside the spot check: their own plain day
-            for i in range(n):
-                if extra[i]:
-                    g.set_state(i, S[i])
-                g.set_time(t_day0 if extra[i] else t_day1, i)
-            g.step(t_day1)
+            _advance_subset(g, gs, S, np.flatnonzero(extra), t_day0, t_day1)
             run |= extra
-        plain = torch.empty((int(run.sum()), H, W), device="cuda")
         idx = np.flatnonzero(run)
-        for q, i in enumerate(idx):
-            g.get_state(int(i), plain[q])
+        plain = _fetch(g, gs, idx)
+        torch.cuda.current_stream().synchronize()
+        td = time.perf_counter()
         # spot check: relative L2 of the proposal against the solver's day
         pos = {int(i): q for q, i in enumerate(idx)}
-        chk_plain = plain[[pos[int(i)] for i in chk]].contiguous()
-        chk_prop = prop[torch.from_numpy(chk).cuda()].contiguous()
+        chk_plain = plain.index_select(0, _dev_index(np.array([pos[int(i)] for i in chk], dtype=np.int64)))
+        chk_prop = prop.index_select(0, _dev_index(chk.astype(np.int64)))
         err = net.rel_l2(chk_prop, chk_plain)
         spot_bad = np.zeros(n, dtype=bool)
         spot_bad[chk[err > l2_tol]] = True
         if np.mean(err > l2_tol) > max_fail:
             # untrustworthy day: every member advances with the plain solver
-            rest = ~run
-            for i in np.flatnonzero(rest):
-                g.set_state(int(i), S[int(i)])
-                g.set_time(t_day0, int(i))
-            for i in np.flatnonzero(run):
-                g.set_time(t_day1, int(i))
-            g.step(t_day1)
-            for i in np.flatnonzero(rest):
-                g.get_state(int(i), S[int(i)])
+            rest = np.flatnonzero(~run)
+            if len(rest):
+                _advance_subset(g, gs, S, rest, t_day0, t_day1)
+                S.index_copy_(0, _dev_index(rest.astype(np.int64)), _fetch(g, gs, rest))
             spot_bad[:] = True
             stats["days_rejected"] = stats.get("days_rejected", 0) + 1
         use_plain = bad | spot_bad | run  # solver result available for every member it ran on
-        for q, i in enumerate(idx):
-            S[int(i)] = plain[q]
-        keep = torch.from_numpy(~use_plain).cuda()
-        S[keep] = prop[keep]
+        S.index_copy_(0, _dev_index(idx.astype(np.int64)), plain)
+        keep = _dev_index(~use_plain)
+        torch.where(keep[:, None, None], prop, S, out=S)
         stats["member_days"] += n
         stats["accepted"] += int((~use_plain).sum())
         stats["rejected_drift"] += int(bad.sum())
@@ -201,9 +250,15 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
         stats["spot_checked"] += len(chk)
         stats.setdefault("spot_l2_median", []).append(float(np.median(err)))
         phi_old, abs_old = _fluxes(net, S)
+        te = time.perf_counter()
+        ph["queue_spot_day"] += tb - ta
+        ph["proposals_and_flux"] += tc - tb
+        ph["fetch_solver_maps"] += td - tc
+        ph["rest"] += te - td
     torch.cuda.synchronize()
     stats["seconds"] = time.perf_counter() - t0
     stats["member_days_per_s"] = stats["member_days"] / stats["seconds"]
+    stats["phase_s"] = ph
     stats["tile_rows"] = g.get_tile_rows(0)  # the autotuner's choice for this grid shape
     g.close()
     return S, stats
@@ -214,8 +269,8 @@ def plain(S0, P, days):
     import torch
     n = S0.shape[0]
     g = _grid(n, P.cpu().numpy().astype(np.float64))
-    for i in range(n):
-        g.set_state(i, S0[i])
+    members = np.arange(n)
+    g.set_states(members, S0.contiguous())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for day in range(days):
@@ -224,8 +279,7 @@ def plain(S0, P, days):
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     out = torch.empty_like(S0)
-    for i in range(n):
-        g.get_state(i, out[i])
+    g.get_states(members, out)
     torch.cuda.synchronize()
     tr = g.get_tile_rows(0)
     g.close()

@@ -104,6 +104,9 @@ _SIGS = {
     "sft_wave_size": (C.c_int32, [C.c_void_p]),
     "sft_step_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "sft_set_states": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_int32]),
+    "sft_get_states": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_int32]),
+    "sft_set_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "sft_flux_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int,
                                                C.c_double, C.c_void_p, C.POINTER(sft_diag)]),
     "sft_debug_checks": (C.c_int, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint32), C.c_int32]),
@@ -286,6 +289,34 @@ class Grid:
         else:
             for i, ti in enumerate(t):
                 self._check(self.lib.sft_set_time(self.h, i, float(ti)))
+
+    def _subset(self, idx):
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32).ravel())
+        return idx, idx.ctypes.data_as(C.POINTER(C.c_int32))
+
+    def set_states(self, idx, maps):
+        """sft_set_states: maps[q] (a packed [n, ntheta, nphi] array or tensor)
+        into realizations idx[q]."""
+        idx, pi = self._subset(idx)
+        if isinstance(maps, np.ndarray):
+            maps = np.ascontiguousarray(maps, dtype=self.dtype)
+        p, dev, keep = _ptr(maps)
+        self._check(self.lib.sft_set_states(self.h, len(idx), pi, C.c_void_p(p), dev))
+        del keep
+
+    def get_states(self, idx, out):
+        """sft_get_states: realizations idx[q] into out[q] (packed, contiguous)."""
+        idx, pi = self._subset(idx)
+        p, dev, keep = _ptr(out)
+        self._check(self.lib.sft_get_states(self.h, len(idx), pi, C.c_void_p(p), dev))
+        del keep
+        return out
+
+    def set_times(self, idx, t):
+        """sft_set_times: realization idx[q] to time t[q] (or all to scalar t)."""
+        idx, pi = self._subset(idx)
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(t, dtype=np.float64), idx.shape))
+        self._check(self.lib.sft_set_times(self.h, len(idx), pi, t.ctypes.data_as(C.POINTER(C.c_double))))
 
     def get_time(self):
         out = (C.c_double * self.n_real)()

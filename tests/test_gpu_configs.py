@@ -43,7 +43,7 @@ def _oracle_assim(g, B, obs, mu):
     return O.assimilate(g, B, obs, F, AP.flux_balance)
 
 
-def test_c2_hourly_assimilation_512x1024():
+def test_c2_hourly_assimilation_512x1024(record_precision):
     shape = (512, 1024)
     fp = _c2_flow()
     st = I.ObservationStream(*shape, seed=2)
@@ -60,6 +60,7 @@ def test_c2_hourly_assimilation_512x1024():
         g.assimilate(obs, mu, False, AP)
         ref.B = _oracle_assim(ref.g, ref.B, obs.astype(np.float64), mu.astype(np.float64))
     got = g.get_state(0)
+    record_precision("C2 512x1024 FP32, 3 h with hourly assimilation", rel_linf(got, ref.B), 1e-5)
     assert rel_linf(got, ref.B) <= 1e-5, rel_linf(got, ref.B)
     assert np.abs(got - B0).max() > 1.0   # the observations did enter
 
@@ -70,7 +71,7 @@ def _uneven(shapes_counts, seed=3):
     return shapes, [params_from_draw(d) for d in draws]
 
 
-def test_c4_uneven_batch_per_shape_observations():
+def test_c4_uneven_batch_per_shape_observations(record_precision):
     shapes, params = _uneven([((64, 128), 4), ((128, 256), 3), ((90, 180), 2)])
     distinct = [(64, 128), (128, 256), (90, 180)]
     streams = {s: I.ObservationStream(*s, seed=2) for s in distinct}
@@ -90,8 +91,10 @@ def test_c4_uneven_batch_per_shape_observations():
         for r, s in enumerate(shapes):
             refs[r].advance(float(hour))
             refs[r].B = _oracle_assim(refs[r].g, refs[r].B, obs[s].astype(np.float64), mu[s].astype(np.float64))
+    errs = [rel_linf(g.get_state(r), refs[r].B) for r in range(len(shapes))]
+    record_precision("C4 reduced: 9 realizations, 3 shapes, FP32, 3 h with per-shape assimilation", max(errs), 1e-5)
     for r in range(len(shapes)):
-        assert rel_linf(g.get_state(r), refs[r].B) <= 1e-5, (r, rel_linf(g.get_state(r), refs[r].B))
+        assert errs[r] <= 1e-5, (r, errs[r])
 
 
 FULL_C4 = [((256, 512), 128), ((512, 1024), 96), ((1440, 2880), 32)]
@@ -111,7 +114,7 @@ def _run_full_c4(budget=0):
     return g, shapes, params, d0, d1, n
 
 
-def test_c4_full_size_uneven_batch():
+def test_c4_full_size_uneven_batch(record_precision):
     """256 realizations, 199.8 M cells, one hour: each realization takes
     ceil(1 h / its CFL step) steps; total flux is conserved; a sampled 256x512 realization
     matches the oracle; an HBM budget for about a third of the work arrays
@@ -126,6 +129,9 @@ def test_c4_full_size_uneven_batch():
         assert abs(b["flux_signed"] - a["flux_signed"]) <= 1e-5 * a["flux_pos"]
     ref = O.Realization(O.Grid(256, 512), oracle_params(params[0]), I.dipole(256, 512).astype(np.float32).astype(np.float64))
     ref.advance(1.0)
+    drift = max(abs(b["flux_signed"] - a["flux_signed"]) / a["flux_pos"] for a, b in zip(d0, d1))
+    record_precision("C4 full size: 256 realizations, 199.8 M cells, FP32, 1 h (256x512 sampled)",
+                     rel_linf(g.get_state(0), ref.B), 1e-5, drift)
     assert rel_linf(g.get_state(0), ref.B) <= 1e-5
     sample = [0, 127, 128, 223, 224, 255]
     full = {r: g.get_state(r) for r in sample}
@@ -138,7 +144,7 @@ def test_c4_full_size_uneven_batch():
         np.testing.assert_array_equal(gw.get_state(r), full[r])
 
 
-def test_c3_full_size_step_sampled():
+def test_c3_full_size_step_sampled(record_precision):
     """One step of 64 x 1024x2048 (the benchmarked ensemble); realization 0
     against the oracle (one CFL step, ~580 RKL2 stages at 2 M cells)."""
     nt, np_ = 1024, 2048
@@ -157,4 +163,7 @@ def test_c3_full_size_step_sampled():
         assert abs(b["flux_signed"] - a["flux_signed"]) <= 1e-5 * a["flux_pos"]
     ref = O.Realization(O.Grid(nt, np_), oracle_params(params[0]), maps[0].astype(np.float64))
     ref.advance(27 * 24.0, max_steps=1)
+    drift = max(abs(b["flux_signed"] - a["flux_signed"]) / a["flux_pos"] for a, b in zip(d0, d1))
+    record_precision("C3 64x1024x2048 FP32, one CFL step (realization 0 sampled)",
+                     rel_linf(g.get_state(0), ref.B), 1e-5, drift)
     assert rel_linf(g.get_state(0), ref.B) <= 1e-5, rel_linf(g.get_state(0), ref.B)

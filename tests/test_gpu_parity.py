@@ -67,7 +67,7 @@ def test_other_advection_schemes_match_oracle(space, time):
         assert rel_linf(g.get_state(r), ref.B) <= 1e-12
 
 
-def test_c1_dipole_and_pairs_27_days_fp64():
+def test_c1_dipole_and_pairs_27_days_fp64(record_precision):
     """128x256 FP64, one realization, the default-rotation/meridional/eta=500
     setup, dipole + 12 seeded pairs flux balanced, 27 days at CFL dt."""
     shape = (128, 256)
@@ -83,8 +83,10 @@ def test_c1_dipole_and_pairs_27_days_fp64():
     g.set_flows([fp])
     g.step(27 * 24.0)
     ref = oracle_run(shape, fp, refB0, 27 * 24.0)
-    assert rel_linf(g.get_state(0), ref.B) <= 1e-12
     diag = g.diagnostics()[0]
+    record_precision("C1 128x256 FP64, 27 days", rel_linf(g.get_state(0), ref.B), 1e-12,
+                     abs(diag["flux_signed"]) / diag["flux_pos"], steps=diag["steps"])
+    assert rel_linf(g.get_state(0), ref.B) <= 1e-12
     assert abs(diag["flux_signed"]) <= 1e-12 * diag["flux_pos"]
 
 
@@ -510,7 +512,7 @@ def test_state_larger_than_the_hbm_budget_is_refused():
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("fused", [True, False])
-def test_rkg2_matches_oracle(prec, fused):
+def test_rkg2_matches_oracle(prec, fused, record_precision):
     """RKG2(3/2) diffusion (Sec. 3.7.2, the paper's default stepper) with
     advection, uneven shapes, against the oracle at the parity bars; the
     FP32 path through the fused launches and through one launch per stage."""
@@ -528,6 +530,8 @@ def test_rkg2_matches_oracle(prec, fused):
         assert g.step_plan(r, 1.0)[2] == O.rkg2_stage_count(1.0, ref.dt_euler)
         got = g.get_state(r)
         bar = 1e-12 if prec == "fp64" else 1e-5
+        record_precision("RKG2 %s %dx%d %s, 30 h" % (prec, s[0], s[1], "fused" if fused else "per stage"),
+                         rel_linf(got, ref.B), bar)
         assert rel_linf(got, ref.B) <= bar, (s, rel_linf(got, ref.B))
 
 
