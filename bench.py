@@ -577,6 +577,96 @@ def run_surrogate(args):
     return 0
 
 
+def _hh(X, Y):
+    """The paper's HH error metric (Sec. 2.6, Eq. hh) in FP64 on the device."""
+    X, Y = X.double(), Y.double()
+    return float((((X - Y) ** 2).sum() / (X.abs() * Y.abs()).sum()).sqrt())
+
+
+C4_SHAPES = [((256, 512), 128), ((512, 1024), 96), ((1440, 2880), 32)]
+
+
+def run_config(args):
+    """The long assimilative runs, one JSON line each.
+
+    c2: one 512x1024 FP32 realization started from the dipole, hourly
+    mu-weighted flux-balanced assimilation of the hidden-truth stream
+    (Earth-facing hemisphere) for args.days days (365), beside a free run
+    from the same start without assimilation; reports the final HH against
+    the truth, the largest net-flux imbalance seen, and the run time.
+    c4: the uneven batch (256 realizations in three grid shapes, 199.8 M
+    cells), per-realization parameters, hourly assimilation of one truth
+    stream per grid shape, args.days days (90); reports the flux imbalance,
+    the HH against the truth per shape, and realization-hours/s."""
+    import torch
+    import sft_inputs as I
+    from paper_2501_06377_gb300 import build as B
+    from paper_2501_06377_gb300.sft import AssimParams, FlowParams, Grid
+    B.build()
+    torch.cuda.set_device(0)
+    ap = AssimParams(alpha_mu=4.0, mu_lim=0.1, lat_lim_deg=90.0, flux_balance=True)
+    off = AssimParams(alpha_mu=4.0, mu_lim=2.0, lat_lim_deg=90.0, flux_balance=True)  # mu <= 1 < 2: F = 0
+    if args.config == "c2":
+        days = args.days if args.days != 27 else 365
+        shapes = [(512, 1024)] * 2
+        d = I.omega_to_dr_coeffs(*I.DEFAULT_OMEGA)
+        params = [FlowParams(d0=d[0], d2=d[1], d4=d[2], m1=30.0, m3=0.0, m5=0.0, nu=500.0)] * 2
+        aps = [ap, off]
+        streams = {(512, 1024): I.ObservationStream(512, 1024, seed=2, days=days + 1)}
+        mode = 0
+    else:
+        days = args.days if args.days != 27 else 90
+        shapes = [sh for sh, n in C4_SHAPES for _ in range(n)]
+        params = [FlowParams(*dr) for dr in I.draw_realization_params(len(shapes), seed=3)]
+        aps = [ap] * len(shapes)
+        streams = {sh: I.ObservationStream(*sh, seed=2, days=days + 1) for sh, _ in C4_SHAPES}
+        mode = 2
+    distinct = list(dict.fromkeys(shapes))
+    g = Grid(shapes, "fp32")
+    for r, sh in enumerate(shapes):
+        g.set_state(r, I.dipole(*sh).astype(np.float32))
+    g.set_flows(params)
+    worst = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_truth = 0.0
+    for hour in range(1, 24 * days + 1):
+        g.step(float(hour))
+        ta = time.perf_counter()
+        obs = torch.cat([streams[sh].truth_torch(float(hour)).float().reshape(-1) for sh in distinct])
+        mu = torch.cat([streams[sh].mu_torch(float(hour)).float().reshape(-1) for sh in distinct])
+        t_truth += time.perf_counter() - ta
+        g.assimilate(obs, mu, mode, aps)
+        if hour % 24 == 0:
+            for dg in g.diagnostics():
+                worst = max(worst, abs(dg["flux_signed"]) / dg["flux_pos"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    T = 24.0 * days
+    truth = {sh: streams[sh].truth_torch(T).float() for sh in distinct}
+    hh = {}
+    for r, sh in enumerate(shapes):
+        m = torch.from_numpy(g.get_state(r)).cuda()
+        hh.setdefault(sh, []).append(_hh(m, truth[sh]))
+    st = g.stats()
+    line = {"metric": "assimilative run (%s): simulated realization-hours/s" % args.config,
+            "value": len(shapes) * T / wall, "unit": "realization-hours/s", "days": days,
+            "wall_s": wall, "truth_generation_s": t_truth, "steps": st["global_steps"],
+            "max_net_flux_over_unsigned": worst, "dtype": "f32", "data": "synthetic",
+            "assimilation": "hourly, alpha_mu = 4, mu_lim = 0.1, no latitude cut, flux balanced (Eq. fluxbal)"}
+    if args.config == "c2":
+        line["hh_vs_truth"] = {"assimilated": hh[(512, 1024)][0], "free_run": hh[(512, 1024)][1]}
+        line["config"] = {"workload": "C2: 512x1024 FP32, 1 realization, %d days, hourly assimilation of a "
+                                      "hidden-truth stream (1 new pair/day, Earth-facing hemisphere), from the "
+                                      "dipole only; a free run beside it" % days}
+    else:
+        line["hh_vs_truth_median_by_shape"] = {"%dx%d" % sh: float(np.median(v)) for sh, v in hh.items()}
+        line["config"] = {"workload": "C4: 256 realizations (128 x 256x512, 96 x 512x1024, 32 x 1440x2880), "
+                                      "FP32, %d days, hourly assimilation of one truth stream per shape" % days}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_smoother(args):
     """The flux-preserving map smoother (grid-based diffusivity, Eq. diffgrid):
     a batch of 512x1024 FP32 maps, alpha_nu = 0.5, diffusion only, one hour
@@ -657,6 +747,8 @@ def main():
     ap.add_argument("--members", type=int, default=512)
     ap.add_argument("--days", type=int, default=27)
     ap.add_argument("--epochs", type=int, default=16)
+    ap.add_argument("--config", choices=["c2", "c4"], default=None,
+                    help="a long assimilative run instead of the benchmark (c2: 365 days, c4: 90 days)")
     ap.add_argument("--no-c1", action="store_true", help="skip the single-realization FP64 run")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the (reduced-training) surrogate ensemble of the default run")
@@ -674,6 +766,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.config:
+        return run_config(args)
     if args.surrogate:
         return run_surrogate(args)
     if args.smoother:

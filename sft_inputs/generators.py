@@ -202,6 +202,58 @@ class ObservationStream:
                               sigma_scale=s, lon_shift_deg=[sh])
         return B
 
+    def truth_torch(self, t_hours, device="cuda", chunk=32):
+        """truth(t_hours) evaluated with torch (FP64) on `device`: the same
+        dipole and pair lobes, all live regions of a chunk at once.  For
+        year-long hourly streams, where the host version is too slow."""
+        import torch
+        day = t_hours / 24.0
+        th = torch.as_tensor(self.theta, dtype=torch.float64, device=device)
+        ph = torch.as_tensor(self.phi, dtype=torch.float64, device=device)
+        lat = (0.5 * math.pi - th)[None, :, None]
+        sl, cl = torch.sin(lat), torch.cos(lat)
+        B = (10.0 * torch.cos(th))[:, None].expand(self.nt, self.np).clone()
+        lobes = []  # (amplitude, lat, lon, sigma) of every live lobe
+        for i, p in enumerate(self.pairs):
+            age = day - i
+            if age < 0:
+                break
+            s2 = math.sin(math.radians(p.lat)) ** 2
+            rate = DEFAULT_OMEGA[0] + DEFAULT_OMEGA[1] * s2 + DEFAULT_OMEGA[2] * s2 * s2
+            a = math.exp(-age / 10.0)
+            sg = math.sqrt(1.0 + age / 5.0)
+            sh = (rate - 360.0 / CARRINGTON_SYNODIC_DAYS) * age
+            half = 0.5 * math.radians(p.sep)
+            tilt = math.radians(p.tilt)
+            latc = math.radians(p.lat)
+            lonc = math.radians(p.lon + sh)
+            dlat = half * math.sin(tilt) * (-1.0 if p.lat > 0 else 1.0)
+            dlon = half * math.cos(tilt) / max(math.cos(latc), 1e-3)
+            amp = p.peak * a / sg ** 2
+            sig = math.radians(p.sigma) * sg
+            lobes.append((amp, latc + dlat, lonc + dlon, sig))
+            lobes.append((-amp, latc - dlat, lonc - dlon, sig))
+        for c0 in range(0, len(lobes), chunk):
+            L = torch.tensor(lobes[c0:c0 + chunk], dtype=torch.float64, device=device)
+            a, la, lo, sg = (L[:, q][:, None, None] for q in range(4))
+            cosd = sl * torch.sin(la) + cl * torch.cos(la) * torch.cos(ph[None, None, :] - lo)
+            d = torch.arccos(torch.clamp(cosd, -1.0, 1.0))
+            B += (a * torch.exp(-0.5 * (d / sg) ** 2)).sum(0)
+        B[0, :] = B[0, 0].clone()
+        B[-1, :] = B[-1, 0].clone()
+        return B
+
+    def mu_torch(self, t_hours, device="cuda"):
+        """mu(t_hours) evaluated with torch (FP64) on `device`."""
+        import torch
+        phi_e = self.phi_e0 - 2.0 * math.pi * t_hours / (CARRINGTON_SYNODIC_DAYS * 24.0)
+        th = torch.as_tensor(self.theta, dtype=torch.float64, device=device)
+        ph = torch.as_tensor(self.phi, dtype=torch.float64, device=device)
+        m = torch.clamp(torch.sin(th)[:, None] * torch.cos(ph[None, :] - phi_e), min=0.0)
+        m[0, :] = 0.0
+        m[-1, :] = 0.0
+        return m
+
     def mu(self, t_hours):
         phi_e = self.phi_e0 - 2.0 * math.pi * t_hours / (CARRINGTON_SYNODIC_DAYS * 24.0)
         m = np.sin(self.theta)[:, None] * np.cos(self.phi[None, :] - phi_e)
