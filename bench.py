@@ -446,6 +446,7 @@ def run_gpu(args, rank, world, local_rank):
                        * world / (ms * 1e-3),
                        "rkl2_stages_per_step": st["diff_cell_stages"] / max(st["cell_updates"], 1),
                        "graph": True, "rkl2_stages_per_launch": g.get_fusion(),
+                       "band_rows": g.get_band_rows(0), "tile_rows": g.get_tile_rows(0),
                        "flow_attenuation_b0": args.atten_b0, "splitting": args.splitting,
                        "rfe": ({"method": 2, "rate_mx_per_hour": args.rfe_rate, "lifetime_hours": args.rfe_lifetime}
                                if args.rfe_rate > 0.0 else None),
@@ -667,6 +668,69 @@ def run_config(args):
     return 0
 
 
+def run_sharded_c4(args, rank, world, local_rank):
+    """The uneven 256-realization batch sharded over the ranks (one process
+    per GPU): realizations bin-packed by cost (LPT over cells x (stages + 4)
+    x steps), each rank advancing its own shard for args.hours hours with no
+    collective on the data path, then every realization's FP64 diagnostics
+    gathered on rank 0.  value: realization-hours / the slowest rank's time
+    (grid set-up included); scaling strong (the batch is fixed)."""
+    import torch
+    import sft_inputs as I
+    from paper_2501_06377_gb300 import build as B
+    from paper_2501_06377_gb300 import sharding as SH
+    from paper_2501_06377_gb300.sft import FlowParams, Grid
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    shapes = [sh for sh, n in C4_SHAPES for _ in range(n)]
+    params = [FlowParams(*dr) for dr in I.draw_realization_params(len(shapes), seed=3)]
+    # cost of each realization from its own step plan (one small grid per shape)
+    costs = []
+    plan = {}
+    for sh, _ in C4_SHAPES:
+        plan[sh] = Grid([sh], "fp32")
+    for sh, fp in zip(shapes, params):
+        plan[sh].set_flows([fp])
+        dt_cfl, _, s = plan[sh].step_plan(0, 1.0)
+        steps = max(1, math.ceil(1.0 / min(1.0, dt_cfl) - 1e-12))
+        costs.append(SH.shard_costs([sh], [plan[sh].step_plan(0, 1.0 / steps)[2]], steps)[0])
+    for gp in plan.values():
+        gp.close()
+    dip = {}
+
+    def start(sh):
+        if sh not in dip:
+            dip[sh] = I.dipole(*sh).astype(np.float32)
+        return dip[sh]
+    advance = SH.grid_advance(shapes, params, start, float(args.hours))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    shards, recs, sec = SH.run_sharded(costs, advance, world, rank)
+    torch.cuda.synchronize()
+    sec = SH.max_over_ranks(sec, device="cuda") if dist is not None else sec
+    if rank == 0:
+        drift = max(abs(d["flux_signed"]) / d["flux_pos"] for _, d in recs)
+        loads = [sum(costs[i] for i in s) for s in shards]
+        line = {"metric": "sharded uneven batch: realization-hours/s", "value": len(shapes) * args.hours / sec,
+                "unit": "realization-hours/s", "n_gpus": world, "scaling": "strong", "dtype": "f32",
+                "data": "synthetic", "seconds": sec, "hours": args.hours,
+                "records_gathered": len(recs), "max_net_flux_over_unsigned": drift,
+                "shard_sizes": [len(s) for s in shards],
+                "shard_cost_balance": max(loads) / (sum(loads) / len(loads)),
+                "config": {"workload": "C4 uneven batch: 256 realizations (128 x 256x512, 96 x 512x1024, "
+                                       "32 x 1440x2880), FP32, sharded by cost over ranks, no data-path "
+                                       "collective, FP64 diagnostics gathered on rank 0 (grid set-up timed)"}}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_smoother(args):
     """The flux-preserving map smoother (grid-based diffusivity, Eq. diffgrid):
     a batch of 512x1024 FP32 maps, alpha_nu = 0.5, diffusion only, one hour
@@ -747,8 +811,10 @@ def main():
     ap.add_argument("--members", type=int, default=512)
     ap.add_argument("--days", type=int, default=27)
     ap.add_argument("--epochs", type=int, default=16)
-    ap.add_argument("--config", choices=["c2", "c4"], default=None,
-                    help="a long assimilative run instead of the benchmark (c2: 365 days, c4: 90 days)")
+    ap.add_argument("--config", choices=["c2", "c4", "c4s"], default=None,
+                    help="a long assimilative run instead of the benchmark (c2: 365 days, c4: 90 days), or "
+                         "c4s: the uneven batch sharded over the ranks for --hours")
+    ap.add_argument("--hours", type=float, default=6.0, help="simulated hours of --config c4s")
     ap.add_argument("--no-c1", action="store_true", help="skip the single-realization FP64 run")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the (reduced-training) surrogate ensemble of the default run")
@@ -766,6 +832,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.config == "c4s":
+        return run_sharded_c4(args, rank, world, local_rank)
     if args.config:
         return run_config(args)
     if args.surrogate:

@@ -20,6 +20,7 @@
 #include <memory>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "sft.h"
@@ -44,6 +45,7 @@ struct ShapeInfo {
   int geo = 0;        // first row in the geometry tables
   int col = 0;        // first entry in the cos/sin(phi) tables
   int tile_rows = 0;  // 0 = autotune on first step
+  int band_rows = 0;  // rows per band of the fused RKL2 work items; 0 = autotune on first step
   double dth = 0, dph = 0, cap = 0;
   std::vector<double> sin_t, sin_h, cos_t;  // sin th_j, sin th_{f+1/2}, cos th_j
 };
@@ -87,6 +89,7 @@ struct Config {
   std::vector<double> dt;        // per wave member (wave order)
   std::vector<int> s;            // per wave member
   std::vector<int> tr;           // tile rows per shape at build time
+  std::vector<int> band;         // fused band rows per shape at build time
   int smax = 0, n_adv_tiles = 0;  // advection tiles (row groups of kAdvRun rows per thread)
   std::vector<int> stage_tiles;  // [j] = tiles launched at RKL2 stage j (1..smax)
   Tile* d_tiles = nullptr;       // single-stage RKL2 tiles
@@ -554,6 +557,7 @@ std::string check_desc(const sft_grid* h) {
     if (d.woff < 0 || d.woff + cells > h->work_elems) return "work extent" + at;
     if (h->fused_ok && (d.poff < 0 || d.poff + fused::part_elems(d.np) > h->polar_elems))
       return "ring-sum partials extent" + at;
+    if (h->fused_ok && (d.band <= fused::K || d.band > (1 << 16))) return "band rows" + at;
     if (d.geo < 0 || d.geo + d.nt > h->geo_rows) return "geometry rows" + at;
     if (d.flow < 0 || d.flow + d.nt > h->flow_rows) return "flow rows" + at;
     if (d.col < 0 || d.col + d.np > h->col_entries) return "longitude table" + at;
@@ -576,7 +580,7 @@ std::string check_tiles(const sft_grid* h, const std::vector<Tile>& tiles, bool 
     if (kind == 3) return "tile kind" + at;
     if (kind != 0) continue;
     if (fused_tiles) {
-      if (t.j0 < 0 || t.j0 >= fused::n_bands(d.nt) * fused::n_strips(d.np)) return "fused work item" + at;
+      if (t.j0 < 0 || t.j0 >= fused::n_bands(d.nt, d.band) * fused::n_strips(d.np)) return "fused work item" + at;
     } else {
       const int lx = t.kind >> 8;
       if (lx < 0 || (1 << lx) > kThreads) return "tile width" + at;
@@ -610,7 +614,7 @@ void append_fused_poles(int r, std::vector<Tile>& tiles) {
 void append_fused_interior(const sft_grid* h, int r, std::vector<Tile>& tiles) {
   const ShapeInfo& s = h->shapes[h->reals[r].shape];
   // rows 1 .. nt-2: (band, strip) work items, one per warp, WARPS per block
-  const int items = fused::n_bands(s.nt) * fused::n_strips(s.np);
+  const int items = fused::n_bands(s.nt, h->desc[r].band) * fused::n_strips(s.np);
   for (int i0 = 0; i0 < items; i0 += fused::WARPS) tiles.push_back(Tile{r, i0, 0, 0});
 }
 
@@ -629,6 +633,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
   c->dt = dt;
   c->s = s;
   for (auto& sh : h->shapes) c->tr.push_back(sh.tile_rows);
+  for (auto& sh : h->shapes) c->band.push_back(sh.band_rows);
   const int nw = (int)w.reals.size();
   // active members (dt > 0) sorted by stage count, descending
   std::vector<int> order;
@@ -918,16 +923,19 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
     *any = true;
   }
   if (!*any) return SFT_OK;
-  for (int r : w.reals)
-    if (h->shapes[h->reals[r].shape].tile_rows == 0) {
+  for (int r : w.reals) {
+    const ShapeInfo& sh = h->shapes[h->reals[r].shape];
+    if (sh.tile_rows == 0 || (h->fused && sh.band_rows == 0)) {
       sft_status st = autotune<T>(h, w);
       if (st != SFT_OK) return st;
       break;
     }
+  }
   Config* c = nullptr;
   for (auto& cfg : w.configs) {
     bool same = cfg->dt == dt && cfg->s == s && cfg->fused == h->fused;
-    for (size_t i = 0; same && i < h->shapes.size(); ++i) same = cfg->tr[i] == h->shapes[i].tile_rows;
+    for (size_t i = 0; same && i < h->shapes.size(); ++i)
+      same = cfg->tr[i] == h->shapes[i].tile_rows && cfg->band[i] == h->shapes[i].band_rows;
     if (same) {
       c = cfg.get();
       break;
@@ -1049,10 +1057,115 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
 
 // Pick the tile height of the stage kernels per shape by timing RKL2 stage 2
 // (a non-final stage: it writes only work arrays) for each candidate.
+// Band rows of shape si for the fused RKL2 kernel, and the descriptors of
+// its realizations (uploaded when no step is in flight).
+sft_status set_band(sft_handle h, int si, int band) {
+  h->shapes[si].band_rows = band;
+  for (int r = 0; r < h->n_real; ++r)
+    if (h->reals[r].shape == si) h->desc[r].band = band;
+  SFT_CUDA(h, cudaStreamSynchronize(h->stream));
+  SFT_CUDA(h, cudaMemcpy(h->d_desc, h->desc.data(), h->desc.size() * sizeof(RealDesc), cudaMemcpyHostToDevice));
+  return SFT_OK;
+}
+
+// The fused kernel's band rows for shape si: one launch of eight stages
+// (stages 10..17 of a 30-stage super step, so that no launch is final and
+// only work arrays are written) over up to 32 of the wave's realizations of
+// that shape, timed for each candidate (128, 256, 512 rows; those no wider
+// than twice the interior), two rounds keeping each candidate's faster time.
+// Results do not depend on the choice (every band computes the same stages
+// point for point); the work arrays and ring-sum partials it overwrites are
+// rebuilt by every step before they are read.
+sft_status tune_band(sft_handle h, Wave& w, int si) {
+  ShapeInfo& sh = h->shapes[si];
+  std::vector<int> members;
+  for (int r : w.reals)
+    if (h->reals[r].shape == si && members.size() < 32) members.push_back(r);
+  if (members.empty()) return SFT_OK;
+  const int S = 30, J0 = 10;
+  std::vector<StepParam> sp(h->n_real);
+  std::memset(sp.data(), 0, sp.size() * sizeof(StepParam));
+  for (int r : members) {
+    sp[r].dt = 1.0;
+    sp[r].nudt = 1e-6;
+    sp[r].s = S;
+    sp[r].coef = 0;
+    sp[r].cap_nu = 1.0;
+  }
+  std::vector<Coef<float>> coefs;
+  rkl2_coefs<float>(S, coefs);
+  StepParam* d_sp = nullptr;
+  Coef<float>* d_coef = nullptr;
+  Tile* d_tiles = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = fused::default_band_rows(sh.nt);
+  float best_ms = 1e30f;
+  cudaError_t err = dev_malloc(&d_sp, sp.size() * sizeof(StepParam));
+  if (err == cudaSuccess) err = dev_malloc(&d_coef, coefs.size() * sizeof(Coef<float>));
+  if (err == cudaSuccess) err = cudaMemcpy(d_sp, sp.data(), sp.size() * sizeof(StepParam), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(d_coef, coefs.data(), coefs.size() * sizeof(Coef<float>), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  const int cand[3] = {128, 256, 512};
+  float* P[4] = {ptr<float>(h->work[1]), ptr<float>(h->work[2]), ptr<float>(h->work[3]), ptr<float>(h->work[4])};
+  for (int ci = 0; ci < 6 && err == cudaSuccess; ++ci) {
+    const int band = cand[ci % 3];
+    if (band != 128 && band >= 2 * (sh.nt - 2)) continue;
+    sft_status st = set_band(h, si, band);
+    if (st != SFT_OK) {
+      err = cudaErrorUnknown;
+      break;
+    }
+    std::vector<Tile> tiles;
+    for (int r : members) append_fused_interior(h, r, tiles);
+    cudaFree(d_tiles);
+    d_tiles = nullptr;
+    if (!check_tiles(h, tiles, true).empty()) {
+      err = cudaErrorInvalidValue;
+      break;
+    }
+    err = dev_malloc(&d_tiles, tiles.size() * sizeof(Tile));
+    if (err == cudaSuccess) err = cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    const int nt = (int)tiles.size();
+    auto launch = [&]() {
+      return launch_rkl2_fused(nt, h->stream, d_tiles, h->d_desc, d_sp, ptr<const RowGeo<float>>(h->d_geo),
+                               h->d_shc, d_coef, ptr<float>(h->state), ptr<const float>(h->work[0]), P[0], P[1],
+                               P[2], P[3], ptr<double>(h->polar), 0, J0, h->d_status);
+    };
+    if (err == cudaSuccess) err = launch();
+    if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+    for (int it = 0; it < 3 && err == cudaSuccess; ++it) err = launch();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = band;
+    }
+  }
+  cudaFree(d_tiles);
+  cudaFree(d_sp);
+  cudaFree(d_coef);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err != cudaSuccess)
+    return fail(h, err == cudaErrorMemoryAllocation ? SFT_ERR_OOM : SFT_ERR_CUDA,
+                std::string("band autotune: ") + cudaGetErrorString(err));
+  return set_band(h, si, best);
+}
+
 template <typename T>
 sft_status autotune(sft_handle h, Wave& w) {
   for (size_t si = 0; si < h->shapes.size(); ++si) {
     ShapeInfo& sh = h->shapes[si];
+    if constexpr (std::is_same<T, float>::value) {
+      if (h->fused && sh.band_rows == 0) {
+        sft_status st = tune_band(h, w, (int)si);
+        if (st != SFT_OK) return st;
+      }
+    }
     if (sh.tile_rows != 0) continue;
     std::vector<int> members;
     for (int r : w.reals)
@@ -1421,7 +1534,8 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   for (int r = 0; r < n_real; ++r) {
     const RealInfo& ri = h->reals[r];
     const ShapeInfo& s = h->shapes[ri.shape];
-    desc[r] = RealDesc{ri.off, ri.woff, s.nt, s.np, s.pitch, ri.shape, s.geo, ri.flow_row, s.col, poff[r]};
+    desc[r] = RealDesc{ri.off,  ri.woff,       s.nt,  s.np,    s.pitch,
+                       ri.shape, s.geo, ri.flow_row, s.col, poff[r], fused::default_band_rows(s.nt)};
   }
   CREATE_CUDA(dev_malloc(&h->d_desc, desc.size() * sizeof(RealDesc)));
   CREATE_CUDA(cudaMemcpy(h->d_desc, desc.data(), desc.size() * sizeof(RealDesc), cudaMemcpyHostToDevice));
@@ -1908,6 +2022,24 @@ sft_status sft_set_tile_rows(sft_handle h, int32_t shape_id, int32_t rows) {
 int32_t sft_get_tile_rows(sft_handle h, int32_t shape_id) {
   if (!h || shape_id < 0 || shape_id >= (int)h->shapes.size()) return 0;
   return h->shapes[shape_id].tile_rows;
+}
+
+sft_status sft_set_band_rows(sft_handle h, int32_t shape_id, int32_t rows) {
+  if (!h) return fail(nullptr, SFT_ERR_ARG, "NULL handle");
+  if (shape_id < 0 || shape_id >= (int)h->shapes.size()) return fail(h, SFT_ERR_ARG, "bad shape id");
+  if (rows != 0 && (rows <= fused::K || rows > (1 << 16)))
+    return fail(h, SFT_ERR_ARG, "band rows must be 0 or in (" + std::to_string(fused::K) + ", 65536]");
+  if (rows == 0) {  // the next step tunes it; until then the default
+    sft_status st = set_band(h, shape_id, fused::default_band_rows(h->shapes[shape_id].nt));
+    h->shapes[shape_id].band_rows = 0;
+    return st;
+  }
+  return set_band(h, shape_id, rows);
+}
+
+int32_t sft_get_band_rows(sft_handle h, int32_t shape_id) {
+  if (!h || shape_id < 0 || shape_id >= (int)h->shapes.size()) return 0;
+  return h->shapes[shape_id].band_rows;
 }
 
 int32_t sft_wave_size(sft_handle h) { return h ? h->wave_size : 0; }

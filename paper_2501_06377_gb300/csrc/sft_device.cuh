@@ -86,6 +86,7 @@ struct RealDesc {
   int32_t flow;    // first row of this realization's flow table
   int32_t col;     // first entry of the shape's cos/sin(phi_k) tables
   int32_t poff;    // offset of this realization's ring-sum partials (doubles, fused RKL2)
+  int32_t band;    // rows per band of the fused RKL2 work items (the shape's tuned choice)
 };
 
 // Per-row geometry of a shape (uniform grid, Sec. 3.2).
@@ -203,15 +204,15 @@ constexpr int MG = K - 1;        // mirrored slots
 constexpr int GSLOTS = RG + MG;  // slots of the G ring and of the coefficient table
 constexpr int RING_F4 = (2 * D + GSLOTS) * LANES;  // float4 slots of one warp's rings (C, A, G)
 constexpr int TAB_F4 = (GSLOTS + 1) * 2 * K;       // one warp's table: per slot K levels x (ka, kb), + a spare slot
-// Band height of a grid: 256 rows from 512 rows up (fewer band-overlap rows),
-// 128 below (more work items for small grids).
-__host__ __device__ constexpr int band_rows(int nt) { return nt >= 512 ? SFT_FUSED_BAND : 128; }
+// Band height of a grid before the autotuner has chosen one: 256 rows from
+// 512 rows up (fewer band-overlap rows), 128 below (more work items).
+__host__ __device__ constexpr int default_band_rows(int nt) { return nt >= 512 ? SFT_FUSED_BAND : 128; }
 constexpr int POLE_F4 = (2 * K + 3) / 4;           // one warp's pole values (north, south)
 constexpr size_t kSmemBytes = sizeof(float4) * (RING_F4 + TAB_F4 + POLE_F4) * WARPS;
 static_assert((D & (D - 1)) == 0 && RG >= D + K && MG >= K - 1, "ring sizes");
 static_assert(4 * K <= LANES, "at most one coefficient of a row per lane");
-// Bands of a grid: rows 1 .. nt-2 in bands of band_rows(nt).
-__host__ __device__ constexpr int n_bands(int nt) { return (nt - 2 + band_rows(nt) - 1) / band_rows(nt); }
+// Bands of a grid: rows 1 .. nt-2 in bands of `band` rows (>= 2K).
+__host__ __device__ constexpr int n_bands(int nt, int band) { return (nt - 2 + band - 1) / band; }
 __host__ __device__ constexpr int n_strips(int np) { return (np + STRIP - 1) / STRIP; }
 // A grid shape can use the fused path when the K rows next to each pole are
 // disjoint and inside one band, and a strip is at least its halo wide.

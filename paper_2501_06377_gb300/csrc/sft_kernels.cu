@@ -1046,9 +1046,9 @@ rkl2_fused_kernel(const Tile* __restrict__ tiles, const RealDesc* __restrict__ r
   // warp w of the block marches work item (tl.j0 + w) = (band, strip)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = n_strips(np);
-  const int band = band_rows(nt);
+  const int band = d.band;
   const int item = tl.j0 + warp;
-  if (item >= n_bands(nt) * ns) return;  // whole warp
+  if (item >= n_bands(nt, band) * ns) return;  // whole warp
   const int strip = item % ns;
   const int J0 = 1 + (item / ns) * band;
   const int J1 = min(J0 + band, nt - 1);

@@ -101,6 +101,8 @@ _SIGS = {
     "sft_get_fusion": (C.c_int32, [C.c_void_p]),
     "sft_set_tile_rows": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "sft_get_tile_rows": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "sft_set_band_rows": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "sft_get_band_rows": (C.c_int32, [C.c_void_p, C.c_int32]),
     "sft_wave_size": (C.c_int32, [C.c_void_p]),
     "sft_step_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
@@ -393,6 +395,12 @@ class Grid:
 
     def get_tile_rows(self, shape_id):
         return self.lib.sft_get_tile_rows(self.h, shape_id)
+
+    def set_band_rows(self, shape_id, rows):
+        self._check(self.lib.sft_set_band_rows(self.h, shape_id, rows))
+
+    def get_band_rows(self, shape_id):
+        return self.lib.sft_get_band_rows(self.h, shape_id)
 
     def wave_size(self):
         return self.lib.sft_wave_size(self.h)

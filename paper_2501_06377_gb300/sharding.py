@@ -10,7 +10,11 @@ rank advances its own shard.  This module holds the host logic:
 * ``max_over_ranks``: the timing reduction of a benchmark (the only
   collective, outside the timed data path);
 * ``checked_barrier``: a barrier that names the ranks that did not arrive
-  within a timeout (gloo's monitored barrier) instead of hanging.
+  within a timeout (gloo's monitored barrier) instead of hanging;
+* ``run_sharded``: the launcher: plan the shards, advance this rank's own
+  realizations with no collective, then gather every rank's FP64
+  diagnostics records to rank 0 (host objects, after the run);
+* ``grid_advance``: the shard step of ``run_sharded`` on this rank's GPU.
 """
 from __future__ import annotations
 
@@ -71,3 +75,49 @@ def checked_barrier(timeout_s=5.0):
 
     import torch.distributed as dist
     dist.monitored_barrier(timeout=datetime.timedelta(seconds=timeout_s), wait_all_ranks=True)
+
+
+def gather_records(records, world, dst=0):
+    """Every rank's list of (realization index, record) on rank ``dst``, in
+    realization order (None on the other ranks; the local list without a
+    process group)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or world == 1:
+        return sorted(records, key=lambda x: x[0])
+    rank = dist.get_rank()
+    out = [None] * world if rank == dst else None
+    dist.gather_object(records, out, dst=dst)
+    if rank != dst:
+        return None
+    return sorted((x for part in out for x in part), key=lambda x: x[0])
+
+
+def run_sharded(costs, advance, world, rank):
+    """Plan the shards by cost (LPT), advance this rank's realizations with
+    ``advance(indices) -> [(index, record), ...]`` (no collective inside),
+    and gather all records on rank 0.  Returns (shards, records on rank 0 or
+    None, this rank's seconds)."""
+    import time
+    shards = lpt_shards(costs, world)
+    t0 = time.perf_counter()
+    mine = advance(shards[rank]) if shards[rank] else []
+    sec = time.perf_counter() - t0
+    return shards, gather_records(mine, world), sec
+
+
+def grid_advance(shapes, params, start_map, t_target, stream=None):
+    """The shard step on this rank's GPU: one batched Grid over the given
+    realizations (FP32), each started from ``start_map(shape)``, advanced to
+    t_target hours; returns the ``advance`` callable of run_sharded, whose
+    records are the realizations' FP64 diagnostics (sft_flux_diagnostics)."""
+    def advance(idx):
+        from .sft import Grid
+        g = Grid([shapes[i] for i in idx], "fp32", stream=stream)
+        for q, i in enumerate(idx):
+            g.set_state(q, start_map(shapes[i]))
+        g.set_flows([params[i] for i in idx])
+        g.step(t_target)
+        diag = g.diagnostics()
+        g.close()
+        return [(i, d) for i, d in zip(idx, diag)]
+    return advance

@@ -549,3 +549,31 @@ def test_rkg2_soccer_ball_one_step_matches_the_paper():
     g.step(672.0)
     ex = I.soccer_ball(nt, np_, nu * O.KM2_S_TO_RS2_HR, 672.0)
     assert O.hh_metric(g.get_state(0), ex) == pytest.approx(6.3e-5, rel=0.05)
+
+
+def test_band_rows_autotuned_and_bitwise_independent():
+    """The fused kernel's band rows: the autotuner picks one per grid shape
+    on the first step (128, 256 or 512), and every choice gives the same
+    bits (each band computes the same stages point for point, halos
+    included, and the pole values come from the same ring sums)."""
+    shapes = [(1024, 512), (300, 200), (1024, 512)]
+    ref = None
+    for band in (0, 128, 256, 512, 40):
+        g, params, maps = _batch(shapes, "fp32", seed=33)
+        if band:
+            for sid in range(2):
+                g.set_band_rows(sid, band)
+        g.step(6.0)
+        got = [g.get_band_rows(sid) for sid in range(2)]
+        if band == 0:
+            assert all(b in (128, 256, 512) for b in got), got
+        else:
+            assert got == [band, band]
+        out = [g.get_state(r) for r in range(len(shapes))]
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(out, ref):
+                np.testing.assert_array_equal(a, b)
+    with pytest.raises(SFTError):
+        g.set_band_rows(0, 8)

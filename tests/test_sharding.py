@@ -54,6 +54,18 @@ def _worker(rank, world, port, mode, q):
             dist.all_gather_object(got, mine)
             t = SH.max_over_ranks(1.0 + rank)
             q.put((rank, got, t))
+        elif mode == "gather":
+            # the uneven 256-realization batch planned by cost; the shard step
+            # is mocked (records say which rank advanced which realization)
+            shapes = [(256, 512)] * 128 + [(512, 1024)] * 96 + [(1440, 2880)] * 32
+            costs = SH.shard_costs(shapes, [36] * 128 + [145] * 96 + [1191] * 32)
+            calls = []
+
+            def advance(idx):
+                calls.append(list(idx))
+                return [(i, {"rank": rank, "flux_signed": float(i)}) for i in idx]
+            shards, recs, sec = SH.run_sharded(costs, advance, world, rank)
+            q.put((rank, shards, recs, calls))
         elif mode == "dropout":
             if rank == 1:
                 q.put((rank, "left"))
@@ -64,7 +76,7 @@ def _worker(rank, world, port, mode, q):
             except RuntimeError as e:
                 q.put((rank, "detected: " + str(e)[:200]))
     finally:
-        if mode == "shards":
+        if mode in ("shards", "gather"):
             dist.destroy_process_group()
 
 
@@ -96,3 +108,20 @@ def test_missing_rank_is_detected_by_the_checked_barrier():
     assert out[1][1] == "left"
     assert out[0][1].startswith("detected"), out[0][1]
     assert "1" in out[0][1]
+
+
+def test_sharded_run_plans_by_cost_and_gathers_on_rank_zero():
+    """run_sharded over two gloo ranks: each rank advances exactly its LPT
+    shard (one call, no collective inside), and rank 0 alone receives every
+    realization's record, in realization order, from the rank that owns it."""
+    out = _run("gather")
+    (r0, sh0, rec0, calls0), (r1, sh1, rec1, calls1) = out
+    assert sh0 == sh1
+    assert calls0 == [sh0[0]] and calls1 == [sh0[1]]
+    assert rec1 is None
+    assert [i for i, _ in rec0] == list(range(256))
+    owner = {i: r for r in (0, 1) for i in sh0[r]}
+    assert all(d["rank"] == owner[i] and d["flux_signed"] == float(i) for i, d in rec0)
+    # the costly 1440x2880 realizations are split between the ranks
+    big = set(range(224, 256))
+    assert 0 < len(big & set(sh0[0])) < 32
