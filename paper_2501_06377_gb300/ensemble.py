@@ -152,6 +152,24 @@ def _dev_index(a):
     return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().to("cuda", non_blocking=True)
 
 
+def _warm_merge_ops(S, prop):
+    """Run the host-side merge operations of a rollout day once on scratch
+    rows (index upload, gather, scatter, masked select), so that loading or
+    compiling their torch kernels, done once per process (and once per box
+    for a kernel compiled on first use), is not timed as part of the
+    rollout."""
+    import torch
+    n = S.shape[0]
+    k = min(2, n)
+    idx = _dev_index(np.arange(k, dtype=np.int64))
+    rows = S.index_select(0, idx).contiguous()
+    scratch = torch.empty_like(rows)
+    scratch.index_copy_(0, _dev_index(np.arange(k, dtype=np.int64)), rows)
+    keep = _dev_index(np.zeros(k, dtype=bool))
+    torch.where(keep[:, None, None], prop[:k], scratch, out=scratch)
+    torch.cuda.current_stream().synchronize()
+
+
 def _advance_subset(g, gs, S, members, t0, t1):
     """Queue the plain solver's day [t0, t1] for the given members (every
     other member idles at t1) on the grid's stream gs, after the maps of S
@@ -197,6 +215,7 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
     rng = np.random.default_rng(seed)
     stats = {"member_days": 0, "accepted": 0, "rejected_drift": 0, "rejected_spot": 0, "spot_checked": 0}
     ph = {"queue_spot_day": 0.0, "proposals_and_flux": 0.0, "fetch_solver_maps": 0.0, "rest": 0.0}
+    _warm_merge_ops(S, prop)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     phi_old, abs_old = _fluxes(net, S)
