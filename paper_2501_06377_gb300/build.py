@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsft.so")
 LIB_DEBUG = os.path.join(PKG, "libsft_debug.so")
-SOURCES = ["sft_api.cu", "sft_kernels.cu", "sft_noalloc.cu", "sfs.cu", "sfs_fused.cu"]
+SOURCES = ["sft_api.cu", "sft_kernels.cu", "sft_noalloc.cu", "sfs.cu", "sfs_fused.cu", "sfs_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -1,14 +1,16 @@
-// sfs.cu -- the learned one-day surrogate (include/sfs.h): BF16 tensor-core
-// GEMMs with FP32 accumulation, the network's forward and backward passes,
-// AdamW, and the C-ABI.
+// sfs.cu -- the learned one-day surrogate (include/sfs.h): the network's
+// training forward and backward passes, AdamW, and the C-ABI.
 //
-// GEMM: mma.sync m16n8k16 (BF16 x BF16 -> FP32) on 128 x 64 x 32 block
-// tiles, operands converted from FP32 to BF16 as they are staged in shared
-// memory and fed to the tensor cores with ldmatrix; batched (strides, a
-// zero stride shares an operand), transposes by layout flags, split-K for
-// the weight gradients (K = batch x tokens), and a split-BF16 mode (hi*hi +
-// hi*lo + lo*hi) for products that must stay ~FP32-accurate.  The fixed
-// rotation layer is an FFT per map row (rot_fft_kernel), not a GEMM.
+// Every contraction of the training pass is a BF16 x BF16 -> FP32 product on
+// the tcgen05 tensor cores (sfs_gemm.cu): batched by strides (a zero stride
+// shares an operand), either operand K-major or MN-major, split-K for the
+// weight gradients (K = batch x tokens).  Activations that only ever feed a
+// product (the embedding E, the spectral outputs Yh and dHh, the GELU
+// outputs A, the decoder gradient dD and the pre-activation gradient dZ)
+// are stored in BF16, which is the precision the product reads them in, so
+// they cost half the bytes and reach shared memory by TMA; the residual
+// stream and its gradient stay FP32.  The fixed rotation layer is an FFT per
+// map row (rot_fft_kernel), not a GEMM.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -20,6 +22,7 @@
 
 #include "sfs.h"
 #include "sfs_fused.cuh"
+#include "sfs_gemm.cuh"
 #include <nvtx3/nvToolsExt.h>
 
 namespace sft {
@@ -34,222 +37,69 @@ constexpr float SCALE = 100.0f;         // map normalisation (G)
 constexpr int kRedBlocks = 64;          // blocks per map of the per-map reductions
 constexpr double PI = 3.14159265358979323846;
 
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint2 pack4(float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+
 // ---------------------------------------------------------------------------
-// GEMM
+// GEMM (sfs_gemm.cu: tcgen05 tensor cores, TMEM accumulators, TMA for the
+// BF16 operands); the split-K partial products are folded here
 // ---------------------------------------------------------------------------
-struct GemmArgs {
-  int M, N, K;
-  const float* A;
-  long long lda, sA;
-  int tA;  // 0: A[m*lda + k]; 1: A[k*lda + m]
-  const float* B;
-  long long ldb, sB;
-  int tB;  // 0: B[k*ldb + n]; 1: B[n*ldb + k]
-  float* C;
-  long long ldc, sC;
-  float alpha, beta;
-  const float* bias;  // per column, may be null
-  int kchunk;         // > 0: batch b covers k in [b*kchunk, (b+1)*kchunk) (split-K)
-  int vecA, vecB;     // float4 loads allowed along the contiguous dimension
-};
-
-constexpr int BM = 128, BN = 64, BK = 32, PADK = 8;
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Global -> register staging of one k-tile: A is BM x BK, B is BK x BN, 16
-// and 8 values per thread, as float4 along the contiguous dimension when the
-// layout and alignment allow it (vecA / vecB), else element by element.
-struct Stage {
-  float a[16], b[8];
-};
-
-__device__ __forceinline__ void load_tile(const GemmArgs& g, const float* A, const float* Bm, int m0, int n0, int k0,
-                                          int kb1, Stage& st) {
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int v = tid + q * 256;  // float4 index within the tile
-    int m, k;
-    if (!g.tA) { m = v >> 3; k = (v & 7) * 4; } else { k = v >> 5; m = (v & 31) * 4; }
-    const int gm = m0 + m, gk = k0 + k;
-    if (!g.tA) {
-      if (g.vecA && gm < g.M && gk + 3 < kb1) {
-        const float4 t = *reinterpret_cast<const float4*>(A + (long long)gm * g.lda + gk);
-        st.a[4 * q] = t.x; st.a[4 * q + 1] = t.y; st.a[4 * q + 2] = t.z; st.a[4 * q + 3] = t.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          st.a[4 * q + e] = (gm < g.M && gk + e < kb1) ? A[(long long)gm * g.lda + gk + e] : 0.f;
-      }
-    } else {
-      if (g.vecA && gm + 3 < g.M && gk < kb1) {
-        const float4 t = *reinterpret_cast<const float4*>(A + (long long)gk * g.lda + gm);
-        st.a[4 * q] = t.x; st.a[4 * q + 1] = t.y; st.a[4 * q + 2] = t.z; st.a[4 * q + 3] = t.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          st.a[4 * q + e] = (gm + e < g.M && gk < kb1) ? A[(long long)gk * g.lda + gm + e] : 0.f;
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int v = tid + q * 256;
-    int n, k;
-    if (!g.tB) { k = v >> 4; n = (v & 15) * 4; } else { n = v >> 3; k = (v & 7) * 4; }
-    const int gn = n0 + n, gk = k0 + k;
-    if (!g.tB) {
-      if (g.vecB && gn + 3 < g.N && gk < kb1) {
-        const float4 t = *reinterpret_cast<const float4*>(Bm + (long long)gk * g.ldb + gn);
-        st.b[4 * q] = t.x; st.b[4 * q + 1] = t.y; st.b[4 * q + 2] = t.z; st.b[4 * q + 3] = t.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          st.b[4 * q + e] = (gn + e < g.N && gk < kb1) ? Bm[(long long)gk * g.ldb + gn + e] : 0.f;
-      }
-    } else {
-      if (g.vecB && gn < g.N && gk + 3 < kb1) {
-        const float4 t = *reinterpret_cast<const float4*>(Bm + (long long)gn * g.ldb + gk);
-        st.b[4 * q] = t.x; st.b[4 * q + 1] = t.y; st.b[4 * q + 2] = t.z; st.b[4 * q + 3] = t.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          st.b[4 * q + e] = (gn < g.N && gk + e < kb1) ? Bm[(long long)gn * g.ldb + gk + e] : 0.f;
-      }
-    }
-  }
-}
-
-template <bool SPLIT>
-__device__ __forceinline__ void store_tile(const GemmArgs& g, const Stage& st,
-                                           __nv_bfloat16 (*sA)[BM][BK + PADK], __nv_bfloat16 (*sB)[BN][BK + PADK]) {
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int v = tid + q * 256;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      int m, k;
-      if (!g.tA) { m = v >> 3; k = (v & 7) * 4 + e; } else { k = v >> 5; m = (v & 31) * 4 + e; }
-      const float x = st.a[4 * q + e];
-      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-      sA[0][m][k] = hi;
-      if (SPLIT) sA[1][m][k] = __float2bfloat16_rn(x - __bfloat162float(hi));
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int v = tid + q * 256;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      int n, k;
-      if (!g.tB) { k = v >> 4; n = (v & 15) * 4 + e; } else { n = v >> 3; k = (v & 7) * 4 + e; }
-      const float x = st.b[4 * q + e];
-      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-      sB[0][n][k] = hi;
-      if (SPLIT) sB[1][n][k] = __float2bfloat16_rn(x - __bfloat162float(hi));
-    }
-  }
-}
-
-template <bool SPLIT>
-__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
-  constexpr int NS = SPLIT ? 2 : 1;
-  __shared__ __align__(16) __nv_bfloat16 sA[NS][BM][BK + PADK];
-  __shared__ __align__(16) __nv_bfloat16 sB[NS][BN][BK + PADK];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;  // 4 x 2 warps, 32 x 32 each
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, b = blockIdx.z;
-  const float* A = g.A + (g.kchunk ? 0 : b * g.sA);
-  const float* Bm = g.B + (g.kchunk ? 0 : b * g.sB);
-  float* C = g.C + b * g.sC;
-  const int kb0 = g.kchunk ? b * g.kchunk : 0;
-  const int kb1 = g.kchunk ? min(g.K, kb0 + g.kchunk) : g.K;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  (void)tid;
-  Stage st;
-  if (kb0 < kb1) load_tile(g, A, Bm, m0, n0, kb0, kb1, st);
-  for (int k0 = kb0; k0 < kb1; k0 += BK) {
-    store_tile<SPLIT>(g, st, sA, sB);
-    __syncthreads();
-    // the next tile's global loads are in flight while the tensor cores work
-    if (k0 + BK < kb1) load_tile(g, A, Bm, m0, n0, k0 + BK, kb1, st);
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      uint32_t af[NS][2][4], bf[NS][4][2];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-          ldsm_x4(af[s][mt], &sA[s][wm * 32 + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-#pragma unroll
-        for (int np2 = 0; np2 < 2; ++np2) {
-          uint32_t r[4];
-          ldsm_x4(r, &sB[s][wn * 32 + np2 * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
-          bf[s][np2 * 2][0] = r[0];
-          bf[s][np2 * 2][1] = r[1];
-          bf[s][np2 * 2 + 1][0] = r[2];
-          bf[s][np2 * 2 + 1][1] = r[3];
-        }
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          mma16816(acc[mt][nt], af[0][mt], bf[0][nt][0], bf[0][nt][1]);
-          if (SPLIT) {
-            mma16816(acc[mt][nt], af[0][mt], bf[NS - 1][nt][0], bf[NS - 1][nt][1]);
-            mma16816(acc[mt][nt], af[NS - 1][mt], bf[0][nt][0], bf[0][nt][1]);
-          }
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int row = m0 + wm * 32 + mt * 16 + (lane >> 2) + (q >= 2 ? 8 : 0);
-        const int col = n0 + wn * 32 + nt * 8 + (lane & 3) * 2 + (q & 1);
-        if (row < g.M && col < g.N) {
-          float* cp = C + (long long)row * g.ldc + col;
-          float v = g.alpha * acc[mt][nt][q];
-          if (g.beta != 0.f) v += g.beta * *cp;
-          if (g.bias) v += g.bias[col];
-          *cp = v;
-        }
-      }
-}
-
-// out[i] = beta * out[i] + sum_s part[s * n + i]
-__global__ void splitk_reduce(const float* __restrict__ part, int ns, long long n, float beta,
-                              float* __restrict__ out) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+// out[i] = beta * out[i] + sum_q part[q * n + i], q < ns: one warp per
+// output, lane l adding q = l, l + 32, ... in order and a fixed shuffle tree
+// combining the lanes (deterministic, independent of the launch shape).
+__global__ void fold_parts_kernel(const float* __restrict__ part, int ns, long long n, float beta,
+                                  float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
     float s = 0.f;
-    for (int q = 0; q < ns; ++q) s += part[q * n + i];
-    out[i] = (beta != 0.f ? beta * out[i] : 0.f) + s;
+    for (int q = lane; q < ns; q += 32) s += part[(long long)q * n + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = (beta != 0.f ? beta * out[i] : 0.f) + s;
+  }
+}
+
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&v)[4]) {
+  const uint2 t = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&t.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&t.y);
+  v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
+}
+
+// Column sums of X[rows][ncols] (the bias gradients): block b adds its
+// contiguous row range into part[b][ncols] in a fixed order (four columns
+// per thread, ncols / 4 threads per row, the row offsets folded in order
+// through shared memory).  ncols divides 1024 and is a multiple of 4.
+template <typename T>
+__global__ void __launch_bounds__(256) colsum_part_kernel(const T* __restrict__ X, long long rows, int ncols,
+                                                         float* __restrict__ part) {
+  __shared__ float sh[1024];
+  const int tpr = ncols / 4, c4 = (threadIdx.x % tpr) * 4, rl = threadIdx.x / tpr, rstep = blockDim.x / tpr;
+  const long long per = (rows + gridDim.x - 1) / gridDim.x;
+  const long long r0 = (long long)blockIdx.x * per, r1 = min(rows, r0 + per);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (long long r = r0 + rl; r < r1; r += rstep) {
+    float v[4];
+    load4(X + r * ncols + c4, v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] += v[e];
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) sh[rl * ncols + c4 + e] = acc[e];
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    float s = 0.f;
+    for (int q = 0; q < rstep; ++q) s += sh[q * ncols + c];
+    part[(long long)blockIdx.x * ncols + c] = s;
   }
 }
 
@@ -331,7 +181,7 @@ __global__ void __launch_bounds__(256) rot_fft_kernel(const float* __restrict__ 
 // E[token][48]: 4x4 patches of x/s and r/s, normalised parameters, cos/sin of
 // the patch-row colatitude, zeros.  One thread per token.
 __global__ void embed_kernel(const float* __restrict__ x, const float* __restrict__ r,
-                             const float* __restrict__ p, int nb, float* __restrict__ E) {
+                             const float* __restrict__ p, int nb, bf16* __restrict__ E) {
   const long long n = (long long)nb * NTOK;
   const float ref[5] = {13.38f, -2.30f, -1.62f, 15.0f, 500.0f};
   const float spr[5] = {1.338f, 0.230f, 0.162f, 5.0f, 250.0f};
@@ -339,7 +189,7 @@ __global__ void embed_kernel(const float* __restrict__ x, const float* __restric
        tok += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(tok / NTOK), t = (int)(tok % NTOK);
     const int i = t / WT, l = t % WT;
-    float4* out = reinterpret_cast<float4*>(E + tok * KE);
+    uint2* out = reinterpret_cast<uint2*>(E + tok * KE);
     const float inv = 1.0f / SCALE;
 #pragma unroll
     for (int pr = 0; pr < PATCH; ++pr) {
@@ -348,23 +198,23 @@ __global__ void embed_kernel(const float* __restrict__ x, const float* __restric
       float4 vr = *reinterpret_cast<const float4*>(r + off);
       vx.x *= inv; vx.y *= inv; vx.z *= inv; vx.w *= inv;
       vr.x *= inv; vr.y *= inv; vr.z *= inv; vr.w *= inv;
-      out[pr] = vx;
-      out[4 + pr] = vr;
+      out[pr] = pack4(vx.x, vx.y, vx.z, vx.w);
+      out[4 + pr] = pack4(vr.x, vr.y, vr.z, vr.w);
     }
     const float q0 = (p[5 * b + 0] - ref[0]) / spr[0], q1 = (p[5 * b + 1] - ref[1]) / spr[1];
     const float q2 = (p[5 * b + 2] - ref[2]) / spr[2], q3 = (p[5 * b + 3] - ref[3]) / spr[3];
     const float q4 = (p[5 * b + 4] - ref[4]) / spr[4];
     const double th = (i + 0.5) * PATCH * (PI / (H - 1));
-    out[8] = make_float4(q0, q1, q2, q3);
-    out[9] = make_float4(q4, (float)cos(th), (float)sin(th), 0.f);
-    out[10] = make_float4(0.f, 0.f, 0.f, 0.f);
-    out[11] = make_float4(0.f, 0.f, 0.f, 0.f);
+    out[8] = pack4(q0, q1, q2, q3);
+    out[9] = pack4(q4, (float)cos(th), (float)sin(th), 0.f);
+    out[10] = make_uint2(0u, 0u);
+    out[11] = make_uint2(0u, 0u);
   }
 }
 
 // Yh = w (.) Hh per (latent row i, mode k, channel c); layout [(b*HT+i)][2M][C].
 __global__ void spectral_fwd_kernel(const float* __restrict__ Hh, const float* __restrict__ w, int nb, int M,
-                                    int C, float* __restrict__ Yh) {
+                                    int C, bf16* __restrict__ Yh) {
   const long long n = (long long)nb * HT * M * C;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(e % C);
@@ -372,17 +222,17 @@ __global__ void spectral_fwd_kernel(const float* __restrict__ Hh, const float* _
     const long long bi = e / ((long long)C * M);
     const int i = (int)(bi % HT);
     const float* hp = Hh + bi * 2 * M * C;
-    float* yp = Yh + bi * 2 * M * C;
+    bf16* yp = Yh + bi * 2 * M * C;
     const float hr = hp[(long long)k * C + c], hi = hp[(long long)(M + k) * C + c];
     const float wr = w[(((long long)i * M + k) * C + c) * 2], wi = w[(((long long)i * M + k) * C + c) * 2 + 1];
-    yp[(long long)k * C + c] = wr * hr - wi * hi;
-    yp[(long long)(M + k) * C + c] = wr * hi + wi * hr;
+    yp[(long long)k * C + c] = __float2bfloat16_rn(wr * hr - wi * hi);
+    yp[(long long)(M + k) * C + c] = __float2bfloat16_rn(wr * hi + wi * hr);
   }
 }
 
 // dHh = conj-transpose action of w on dYh.
 __global__ void spectral_bwd_x_kernel(const float* __restrict__ dYh, const float* __restrict__ w, int nb, int M,
-                                      int C, float* __restrict__ dHh) {
+                                      int C, bf16* __restrict__ dHh) {
   const long long n = (long long)nb * HT * M * C;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(e % C);
@@ -390,11 +240,11 @@ __global__ void spectral_bwd_x_kernel(const float* __restrict__ dYh, const float
     const long long bi = e / ((long long)C * M);
     const int i = (int)(bi % HT);
     const float* dp = dYh + bi * 2 * M * C;
-    float* op = dHh + bi * 2 * M * C;
+    bf16* op = dHh + bi * 2 * M * C;
     const float dr = dp[(long long)k * C + c], di = dp[(long long)(M + k) * C + c];
     const float wr = w[(((long long)i * M + k) * C + c) * 2], wi = w[(((long long)i * M + k) * C + c) * 2 + 1];
-    op[(long long)k * C + c] = wr * dr + wi * di;
-    op[(long long)(M + k) * C + c] = -wi * dr + wr * di;
+    op[(long long)k * C + c] = __float2bfloat16_rn(wr * dr + wi * di);
+    op[(long long)(M + k) * C + c] = __float2bfloat16_rn(-wi * dr + wr * di);
   }
 }
 
@@ -430,15 +280,15 @@ __device__ __forceinline__ float gelu_g(float z) {
   return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * c * (1.f + 3.f * 0.044715f * z * z);
 }
 
-__global__ void gelu_fwd_kernel(const float* __restrict__ z, long long n, float* __restrict__ a) {
+__global__ void gelu_fwd_kernel(const float* __restrict__ z, long long n, bf16* __restrict__ a) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    a[e] = gelu_f(z[e]);
+    a[e] = __float2bfloat16_rn(gelu_f(z[e]));
 }
 
 __global__ void gelu_bwd_kernel(const float* __restrict__ da, const float* __restrict__ z, long long n,
-                                float* __restrict__ dz) {
+                                bf16* __restrict__ dz) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    dz[e] = da[e] * gelu_g(z[e]);
+    dz[e] = __float2bfloat16_rn(da[e] * gelu_g(z[e]));
 }
 
 // delta map from the decoder's patches: out[b][row][col] = d[token][4 pr + pc]
@@ -455,12 +305,13 @@ __global__ void unpatch_kernel(const float* __restrict__ d, int nb, float* __res
 // x_next = r + s (delta - <delta>_A) in place over delta; msum[2b] = sum A delta.
 __global__ void center_kernel(float* __restrict__ xn, const float* __restrict__ r,
                               const double* __restrict__ msum, double area_total, int nb) {
-  const long long n = (long long)nb * H * W;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e / (H * W));
-    const float mean = (float)(msum[2 * b] / area_total);
-    xn[e] = r[e] + SCALE * (xn[e] - mean);
-  }
+  // block row blockIdx.y is map b: its mean (an FP64 division) is formed once per thread
+  const int b = blockIdx.y;
+  const float mean = (float)(msum[2 * b] / area_total);
+  float* xm = xn + (long long)b * H * W;
+  const float* rm = r + (long long)b * H * W;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < H * W; e += gridDim.x * blockDim.x)
+    xm[e] = rm[e] + SCALE * (xm[e] - mean);
 }
 
 // Per map m, block partials of sum (x - y)^2, sum y^2, sum (x - y) (three per block).
@@ -529,19 +380,21 @@ __global__ void sumsq_kernel(const float* __restrict__ a, const float* __restric
 }
 
 // dd[token][16]: the loss gradient g = 2 (x_next - y) / (||y||^2 n) through
-// the centring: s (g - A_row sum(g) / sum(A)).
+// the centring: s (g - A_row sum(g) / sum(A)).  Block row blockIdx.y is map
+// b, whose two FP64 constants each thread forms once.
 __global__ void loss_grad_kernel(const float* __restrict__ xn, const float* __restrict__ y,
                                  const double* __restrict__ sums, const double* __restrict__ area,
-                                 double area_total, int nb, float* __restrict__ dd) {
-  const long long n = (long long)nb * H * W;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e / (H * W)), rem = (int)(e % (H * W));
-    const int row = rem / W, col = rem % W;
+                                 double area_total, int nb, bf16* __restrict__ dd) {
+  const int b = blockIdx.y;
+  const double k = 2.0 / (sums[3 * b + 1] * nb);
+  const double gs = k * sums[3 * b + 2] / area_total;
+  const float* xm = xn + (long long)b * H * W;
+  const float* ym = y + (long long)b * H * W;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < H * W; e += gridDim.x * blockDim.x) {
+    const int row = e / W, col = e % W;
     const long long tok = (long long)b * NTOK + (row / PATCH) * WT + col / PATCH;
-    const double k = 2.0 / (sums[3 * b + 1] * nb);
-    const double g = k * (double(xn[e]) - double(y[e]));
-    const double gsum = k * sums[3 * b + 2];
-    dd[tok * 16 + (row % PATCH) * PATCH + col % PATCH] = (float)(SCALE * (g - area[row] * gsum / area_total));
+    const double g = k * (double(xm[e]) - double(ym[e]));
+    dd[tok * 16 + (row % PATCH) * PATCH + col % PATCH] = __float2bfloat16_rn((float)(SCALE * (g - area[row] * gs)));
   }
 }
 
@@ -600,10 +453,6 @@ __global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ g,
   }
 }
 
-__global__ void fill_kernel(float* __restrict__ a, long long n, float v) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    a[e] = v;
-}
 
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
 
@@ -620,14 +469,20 @@ struct sfs_net {
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
   int t = 0;
   // fixed matrices
-  float *Fm = nullptr, *Gm = nullptr, *ones = nullptr;
+  float *Fm = nullptr, *Gm = nullptr;
   float2* tw = nullptr;  // FFT twiddles exp(-2 pi i j / W), j < W/2
   // activations
-  float *R = nullptr, *E = nullptr, *D = nullptr, *XN = nullptr;
-  std::vector<float*> Hs, Hh, U, Z, A;
-  float *Yh = nullptr;
+  // (BF16: the activations that only feed products)
+  float *R = nullptr, *D = nullptr, *XN = nullptr;
+  bf16* E = nullptr;
+  std::vector<float*> Hs, Hh, U, Z;
+  std::vector<bf16*> A;
+  bf16* Yh = nullptr;
   // gradients of activations
-  float *dD = nullptr, *dH = nullptr, *dU = nullptr, *dA = nullptr, *dZ = nullptr, *dYh = nullptr, *dHh = nullptr;
+  float *dH = nullptr, *dU = nullptr, *dA = nullptr, *dYh = nullptr;
+  bf16 *dD = nullptr, *dZ = nullptr, *dHh = nullptr;
+  int* gerr = nullptr;   // device: nonzero once a GEMM wait ran out of time
+  int* hgerr = nullptr;  // pinned host copy
   float* part = nullptr;
   long long part_elems = 0;
   double *sums = nullptr, *hsums = nullptr;
@@ -672,45 +527,60 @@ sft_status dalloc(sfs_handle h, T** p, long long n) {
   return SFT_OK;
 }
 
-// float4 loads need 16-byte aligned rows: base, leading dimension and batch
-// stride all multiples of four floats.
-int vec_ok(const float* p, long long ld, long long stride) {
-  return ((reinterpret_cast<uintptr_t>(p) & 15) == 0 && ld % 4 == 0 && stride % 4 == 0) ? 1 : 0;
+// Operands of a product: element (mn, k) at p[mn*ld + k] (KMAJ) or at
+// p[k*ld + mn] (MNMAJ), batch stride s (0: shared by every batch).
+constexpr int KMAJ = 0, MNMAJ = 1;
+sfs_gemm::Operand opnd(const float* p, long long ld, long long s, int major) {
+  return sfs_gemm::Operand{p, sfs_gemm::F32, major, ld, s};
+}
+sfs_gemm::Operand opnd(const bf16* p, long long ld, long long s, int major) {
+  return sfs_gemm::Operand{p, sfs_gemm::BF16, major, ld, s};
 }
 
-// C = alpha op(A) op(B) + beta C + bias, batched (strides) or split-K.
-sft_status gemm(sfs_handle h, int M, int N, int K, const float* A, long long lda, long long sA, int tA,
-                const float* B, long long ldb, long long sB, int tB, float* C, long long ldc, long long sC,
-                float alpha, float beta, const float* bias, int batch, bool split = false) {
-  GemmArgs g{M, N, K, A, lda, sA, tA, B, ldb, sB, tB, C, ldc, sC, alpha, beta, bias, 0,
-             vec_ok(A, lda, sA), vec_ok(B, ldb, sB)};
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-  if (split) gemm_kernel<true><<<grid, 256, 0, h->stream>>>(g);
-  else gemm_kernel<false><<<grid, 256, 0, h->stream>>>(g);
-  SFS_CUDA(cudaGetLastError());
+// C = alpha A B + beta C + bias (A: M x K, B: K x N), batched by strides.
+sft_status gemm(sfs_handle h, int M, int N, int K, const sfs_gemm::Operand& a, const sfs_gemm::Operand& b, float* C,
+                long long ldc, long long sC, float alpha, float beta, const float* bias, int batch) {
+  sfs_gemm::Problem pr{M, N, K, a, b, C, ldc, sC, alpha, beta, bias, 0, batch};
+  SFS_CUDA(sfs_gemm::launch(pr, h->gerr, h->stream));
   h->gemms += 1;
   h->kernels += 1;
-  h->flops += 2.0 * M * N * (double)K * batch * (split ? 3 : 1);
+  h->flops += 2.0 * M * N * (double)K * batch;
   return SFT_OK;
 }
 
-// Weight gradient C[M][N] (ldc = N) = op(A) op(B) with a long K: split-K into
+// Weight gradient C[M][N] (ldc = N) = A B with a long K: split-K into
 // partial products, then a fixed-order reduction.
-sft_status gemm_wgrad(sfs_handle h, int M, int N, int K, const float* A, long long lda, int tA, const float* B,
-                      long long ldb, int tB, float* C) {
+sft_status gemm_wgrad(sfs_handle h, int M, int N, int K, const sfs_gemm::Operand& a, const sfs_gemm::Operand& b,
+                      float* C) {
   const int kchunk = 1024;
   const int ns = (K + kchunk - 1) / kchunk;
   if ((long long)ns * M * N > h->part_elems) return fail("split-K scratch too small", SFT_ERR_ARG);
-  GemmArgs g{M, N, K, A, lda, 0, tA, B, ldb, 0, tB, h->part, N, (long long)M * N, 1.f, 0.f, nullptr, kchunk,
-             vec_ok(A, lda, 0), vec_ok(B, ldb, 0)};
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, ns);
-  gemm_kernel<false><<<grid, 256, 0, h->stream>>>(g);
-  SFS_CUDA(cudaGetLastError());
-  splitk_reduce<<<grid_for((long long)M * N), 256, 0, h->stream>>>(h->part, ns, (long long)M * N, 0.f, C);
+  sfs_gemm::Problem pr{M, N, K, a, b, h->part, N, (long long)M * N, 1.f, 0.f, nullptr, kchunk, ns};
+  SFS_CUDA(sfs_gemm::launch(pr, h->gerr, h->stream));
+  fold_parts_kernel<<<grid_for((long long)M * N * 32), 256, 0, h->stream>>>(h->part, ns, (long long)M * N, 0.f, C);
   SFS_CUDA(cudaGetLastError());
   h->gemms += 1;
   h->kernels += 2;
   h->flops += 2.0 * M * N * (double)K;
+  return SFT_OK;
+}
+
+// Bias gradient out[c] = sum over the ntok rows of X[row][c] (fixed order).
+template <typename T>
+sft_status bias_grad(sfs_handle h, const T* X, long long rows, int ncols, float* out) {
+  const int nblk = 256;
+  if ((long long)nblk * ncols > h->part_elems) return fail("column-sum scratch too small", SFT_ERR_ARG);
+  colsum_part_kernel<T><<<nblk, 256, 0, h->stream>>>(X, rows, ncols, h->part);
+  fold_parts_kernel<<<grid_for((long long)ncols * 32), 256, 0, h->stream>>>(h->part, nblk, ncols, 0.f, out);
+  SFS_CUDA(cudaGetLastError());
+  h->kernels += 2;
+  return SFT_OK;
+}
+
+// A GEMM wait that ran out of time leaves a code in h->gerr; read it with the
+// step's other results (after a stream synchronisation).
+sft_status check_gemm_error(sfs_handle h) {
+  if (*h->hgerr != 0) return fail("tensor-core GEMM: a wait inside the kernel ran out of time", SFT_ERR_CUDA);
   return SFT_OK;
 }
 
@@ -752,39 +622,40 @@ sft_status forward(sfs_handle h, const float* x, const float* p, int nb) {
   rot_fft_kernel<<<nb * H, 256, 0, h->stream>>>(x, h->alpha, h->tw, h->R);
   embed_kernel<<<grid_for(ntok), 256, 0, h->stream>>>(x, h->R, p, nb, h->E);
   h->kernels += 3;
-  sft_status st = gemm(h, (int)ntok, C, KE, h->E, KE, 0, 0, h->P + h->oWe, C, 0, 0, h->Hs[0], C, 0, 1.f, 0.f, h->P + h->obe, 1);
+  sft_status st = gemm(h, (int)ntok, C, KE, opnd(h->E, KE, 0, KMAJ), opnd(h->P + h->oWe, C, 0, MNMAJ), h->Hs[0], C, 0,
+                       1.f, 0.f, h->P + h->obe, 1);
   if (st != SFT_OK) return st;
   for (int l = 0; l < h->L; ++l) {
     float* hcur = h->Hs[l];
     // Hh_bi = Fm h_bi (batched over b*HT + i)
-    st = gemm(h, 2 * M, C, WT, h->Fm, WT, 0, 0, hcur, C, (long long)WT * C, 0, h->Hh[l], C,
+    st = gemm(h, 2 * M, C, WT, opnd(h->Fm, WT, 0, KMAJ), opnd(hcur, C, (long long)WT * C, MNMAJ), h->Hh[l], C,
               (long long)2 * M * C, 1.f, 0.f, nullptr, nb * HT);
     if (st != SFT_OK) return st;
     spectral_fwd_kernel<<<grid_for((long long)nb * HT * M * C), 256, 0, h->stream>>>(h->Hh[l], h->P + h->ow[l], nb,
                                                                                       M, C, h->Yh);
     h->kernels += 1;
     SFS_CUDA(cudaMemcpyAsync(h->U[l], hcur, ntok * C * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    st = gemm(h, WT, C, 2 * M, h->Gm, 2 * M, 0, 0, h->Yh, C, (long long)2 * M * C, 0, h->U[l], C, (long long)WT * C,
-              1.f, 1.f, nullptr, nb * HT);
+    st = gemm(h, WT, C, 2 * M, opnd(h->Gm, 2 * M, 0, KMAJ), opnd(h->Yh, C, (long long)2 * M * C, MNMAJ), h->U[l], C,
+              (long long)WT * C, 1.f, 1.f, nullptr, nb * HT);
     if (st != SFT_OK) return st;
-    st = gemm(h, (int)ntok, 2 * C, C, h->U[l], C, 0, 0, h->P + h->oW1[l], 2 * C, 0, 0, h->Z[l], 2 * C, 0, 1.f, 0.f,
-              h->P + h->ob1[l], 1);
+    st = gemm(h, (int)ntok, 2 * C, C, opnd(h->U[l], C, 0, KMAJ), opnd(h->P + h->oW1[l], 2 * C, 0, MNMAJ), h->Z[l],
+              2 * C, 0, 1.f, 0.f, h->P + h->ob1[l], 1);
     if (st != SFT_OK) return st;
     gelu_fwd_kernel<<<grid_for(ntok * 2 * C), 256, 0, h->stream>>>(h->Z[l], ntok * 2 * C, h->A[l]);
     h->kernels += 1;
     SFS_CUDA(cudaMemcpyAsync(h->Hs[l + 1], h->U[l], ntok * C * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    st = gemm(h, (int)ntok, C, 2 * C, h->A[l], 2 * C, 0, 0, h->P + h->oW2[l], C, 0, 0, h->Hs[l + 1], C, 0, 1.f, 1.f,
-              h->P + h->ob2[l], 1);
+    st = gemm(h, (int)ntok, C, 2 * C, opnd(h->A[l], 2 * C, 0, KMAJ), opnd(h->P + h->oW2[l], C, 0, MNMAJ),
+              h->Hs[l + 1], C, 0, 1.f, 1.f, h->P + h->ob2[l], 1);
     if (st != SFT_OK) return st;
   }
-  st = gemm(h, (int)ntok, 16, C, h->Hs[h->L], C, 0, 0, h->P + h->oWd, 16, 0, 0, h->D, 16, 0, 1.f, 0.f,
-            h->P + h->obd, 1);
+  st = gemm(h, (int)ntok, 16, C, opnd(h->Hs[h->L], C, 0, KMAJ), opnd(h->P + h->oWd, 16, 0, MNMAJ), h->D, 16, 0, 1.f,
+            0.f, h->P + h->obd, 1);
   if (st != SFT_OK) return st;
   // x_next = r + s (delta - <delta>_A): the correction carries no net flux
   unpatch_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->D, nb, h->XN);
   flux_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, h->area, h->mpart);
   fold_map_sums<<<nb, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->msum);
-  center_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
+  center_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
   h->kernels += 4;
   SFS_CUDA(cudaGetLastError());
   return SFT_OK;
@@ -808,7 +679,7 @@ sft_status forward_fused(sfs_handle h, const float* x, const float* p, int nb) {
               ((double)KE * h->C + h->L * (2.0 * 2 * h->M * h->C + 2.0 * 2 * h->C * h->C) + 16.0 * h->C);
   flux_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, h->area, h->mpart);
   fold_map_sums<<<nb, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->msum);
-  center_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
+  center_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, h->R, h->msum, h->area_total, nb);
   h->kernels += 3;
   SFS_CUDA(cudaGetLastError());
   return SFT_OK;
@@ -820,38 +691,42 @@ sft_status backward(sfs_handle h, const float* y, int nb) {
   const long long ntok = (long long)nb * NTOK;
   loss_sums_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, y, h->mpart);
   fold_map_sums<<<nb, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 3, h->lsum);
-  loss_grad_kernel<<<grid_for((long long)nb * H * W), 256, 0, h->stream>>>(h->XN, y, h->lsum, h->area,
+  loss_grad_kernel<<<dim3(kRedBlocks, nb), 256, 0, h->stream>>>(h->XN, y, h->lsum, h->area,
                                                                           h->area_total, nb, h->dD);
   h->kernels += 3;
   SFS_CUDA(cudaGetLastError());
   // decoder
-  sft_status st = gemm_wgrad(h, C, 16, (int)ntok, h->Hs[h->L], C, 1, h->dD, 16, 0, h->G + h->oWd);
+  sft_status st = gemm_wgrad(h, C, 16, (int)ntok, opnd(h->Hs[h->L], C, 0, MNMAJ), opnd(h->dD, 16, 0, MNMAJ),
+                             h->G + h->oWd);
   if (st != SFT_OK) return st;
-  st = gemm_wgrad(h, 1, 16, (int)ntok, h->ones, 1, 1, h->dD, 16, 0, h->G + h->obd);
+  st = bias_grad(h, h->dD, ntok, 16, h->G + h->obd);
   if (st != SFT_OK) return st;
-  st = gemm(h, (int)ntok, C, 16, h->dD, 16, 0, 0, h->P + h->oWd, 16, 0, 1, h->dH, C, 0, 1.f, 0.f, nullptr, 1);
+  st = gemm(h, (int)ntok, C, 16, opnd(h->dD, 16, 0, KMAJ), opnd(h->P + h->oWd, 16, 0, KMAJ), h->dH, C, 0, 1.f, 0.f,
+            nullptr, 1);
   if (st != SFT_OK) return st;
   for (int l = h->L - 1; l >= 0; --l) {
     // h_{l+1} = u + a W2 + b2
     SFS_CUDA(cudaMemcpyAsync(h->dU, h->dH, ntok * C * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    st = gemm_wgrad(h, 2 * C, C, (int)ntok, h->A[l], 2 * C, 1, h->dH, C, 0, h->G + h->oW2[l]);
+    st = gemm_wgrad(h, 2 * C, C, (int)ntok, opnd(h->A[l], 2 * C, 0, MNMAJ), opnd(h->dH, C, 0, MNMAJ), h->G + h->oW2[l]);
     if (st != SFT_OK) return st;
-    st = gemm_wgrad(h, 1, C, (int)ntok, h->ones, 1, 1, h->dH, C, 0, h->G + h->ob2[l]);
+    st = bias_grad(h, h->dH, ntok, C, h->G + h->ob2[l]);
     if (st != SFT_OK) return st;
-    st = gemm(h, (int)ntok, 2 * C, C, h->dH, C, 0, 0, h->P + h->oW2[l], C, 0, 1, h->dA, 2 * C, 0, 1.f, 0.f, nullptr, 1);
+    st = gemm(h, (int)ntok, 2 * C, C, opnd(h->dH, C, 0, KMAJ), opnd(h->P + h->oW2[l], C, 0, KMAJ), h->dA, 2 * C, 0,
+              1.f, 0.f, nullptr, 1);
     if (st != SFT_OK) return st;
     gelu_bwd_kernel<<<grid_for(ntok * 2 * C), 256, 0, h->stream>>>(h->dA, h->Z[l], ntok * 2 * C, h->dZ);
     h->kernels += 1;
-    st = gemm_wgrad(h, C, 2 * C, (int)ntok, h->U[l], C, 1, h->dZ, 2 * C, 0, h->G + h->oW1[l]);
+    st = gemm_wgrad(h, C, 2 * C, (int)ntok, opnd(h->U[l], C, 0, MNMAJ), opnd(h->dZ, 2 * C, 0, MNMAJ),
+                    h->G + h->oW1[l]);
     if (st != SFT_OK) return st;
-    st = gemm_wgrad(h, 1, 2 * C, (int)ntok, h->ones, 1, 1, h->dZ, 2 * C, 0, h->G + h->ob1[l]);
+    st = bias_grad(h, h->dZ, ntok, 2 * C, h->G + h->ob1[l]);
     if (st != SFT_OK) return st;
-    st = gemm(h, (int)ntok, C, 2 * C, h->dZ, 2 * C, 0, 0, h->P + h->oW1[l], 2 * C, 0, 1, h->dU, C, 0, 1.f, 1.f,
-              nullptr, 1);
+    st = gemm(h, (int)ntok, C, 2 * C, opnd(h->dZ, 2 * C, 0, KMAJ), opnd(h->P + h->oW1[l], 2 * C, 0, KMAJ), h->dU, C,
+              0, 1.f, 1.f, nullptr, 1);
     if (st != SFT_OK) return st;
     // u = h + Gm (w (.) Fm h)
-    st = gemm(h, 2 * M, C, WT, h->Gm, 2 * M, 0, 1, h->dU, C, (long long)WT * C, 0, h->dYh, C, (long long)2 * M * C,
-              1.f, 0.f, nullptr, nb * HT);
+    st = gemm(h, 2 * M, C, WT, opnd(h->Gm, 2 * M, 0, MNMAJ), opnd(h->dU, C, (long long)WT * C, MNMAJ), h->dYh, C,
+              (long long)2 * M * C, 1.f, 0.f, nullptr, nb * HT);
     if (st != SFT_OK) return st;
     spectral_bwd_w_kernel<<<grid_for((long long)HT * M * C), 256, 0, h->stream>>>(h->dYh, h->Hh[l], nb, M, C,
                                                                                   h->G + h->ow[l]);
@@ -859,13 +734,13 @@ sft_status backward(sfs_handle h, const float* y, int nb) {
                                                                                         M, C, h->dHh);
     h->kernels += 2;
     SFS_CUDA(cudaMemcpyAsync(h->dH, h->dU, ntok * C * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    st = gemm(h, WT, C, 2 * M, h->Fm, WT, 0, 1, h->dHh, C, (long long)2 * M * C, 0, h->dH, C, (long long)WT * C, 1.f,
-              1.f, nullptr, nb * HT);
+    st = gemm(h, WT, C, 2 * M, opnd(h->Fm, WT, 0, MNMAJ), opnd(h->dHh, C, (long long)2 * M * C, MNMAJ), h->dH, C,
+              (long long)WT * C, 1.f, 1.f, nullptr, nb * HT);
     if (st != SFT_OK) return st;
   }
-  st = gemm_wgrad(h, KE, C, (int)ntok, h->E, KE, 1, h->dH, C, 0, h->G + h->oWe);
+  st = gemm_wgrad(h, KE, C, (int)ntok, opnd(h->E, KE, 0, MNMAJ), opnd(h->dH, C, 0, MNMAJ), h->G + h->oWe);
   if (st != SFT_OK) return st;
-  st = gemm_wgrad(h, 1, C, (int)ntok, h->ones, 1, 1, h->dH, C, 0, h->G + h->obe);
+  st = bias_grad(h, h->dH, ntok, C, h->G + h->obe);
   if (st != SFT_OK) return st;
   SFS_CUDA(cudaGetLastError());
   return SFT_OK;
@@ -978,8 +853,6 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
       return bail(fail("dft upload failed"));
   }
   const long long nb = h->maxb, ntok = nb * NTOK;
-  CR(dalloc(h, &h->ones, ntok));
-  fill_kernel<<<grid_for(ntok), 256, 0, h->stream>>>(h->ones, ntok, 1.f);
   CR(dalloc(h, &h->R, nb * H * W));
   CR(dalloc(h, &h->XN, nb * H * W));
   CR(dalloc(h, &h->E, ntok * KE));
@@ -1006,6 +879,9 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
   CR(dalloc(h, &h->dHh, nb * HT * 2 * M * C));
   h->part_elems = ((ntok + 1023) / 1024) * (long long)std::max(2 * C * C, KE * C);
   CR(dalloc(h, &h->part, h->part_elems));
+  CR(dalloc(h, &h->gerr, 1));
+  if (cudaMemsetAsync(h->gerr, 0, sizeof(int), h->stream) != cudaSuccess) return bail(fail("memset failed"));
+  if (sfs_gemm::prepare() != cudaSuccess) return bail(fail("tensor-core GEMM: shared-memory limit not granted"));
   CR(dalloc(h, &h->sums, 2 * nb));
   CR(dalloc(h, &h->alpha, nb * H));
   CR(dalloc(h, &h->msum, 2 * nb));
@@ -1023,6 +899,8 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
   }
   if (cudaMallocHost(&h->hsums, 2 * nb * sizeof(double)) != cudaSuccess) return bail(fail("pinned alloc failed"));
   if (cudaMallocHost(&h->hlsum, 3 * nb * sizeof(double)) != cudaSuccess) return bail(fail("pinned alloc failed"));
+  if (cudaMallocHost(&h->hgerr, sizeof(int)) != cudaSuccess) return bail(fail("pinned alloc failed"));
+  *h->hgerr = 0;
   h->fused = C == sfs_fused::kChannels && M == sfs_fused::kModes && L <= sfs_fused::kMaxBlocks;
   if (h->fused) {
     int dev = 0;
@@ -1055,6 +933,7 @@ sft_status sfs_destroy(sfs_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->hsums) cudaFreeHost(h->hsums);
   if (h->hlsum) cudaFreeHost(h->hlsum);
+  if (h->hgerr) cudaFreeHost(h->hgerr);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return SFT_OK;
@@ -1105,7 +984,10 @@ sft_status sfs_loss_grad(sfs_handle h, const float* x, const float* p, const flo
   if (st != SFT_OK) return st;
   SFS_CUDA(cudaMemcpyAsync(h->hlsum, h->lsum, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   SFS_CUDA(cudaMemcpyAsync(host_grad, h->G, h->np * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  SFS_CUDA(cudaMemcpyAsync(h->hgerr, h->gerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   SFS_CUDA(cudaStreamSynchronize(h->stream));
+  st = check_gemm_error(h);
+  if (st != SFT_OK) return st;
   *loss = host_loss(h, n);
   return SFT_OK;
 }
@@ -1132,7 +1014,10 @@ sft_status sfs_train_step(sfs_handle h, const float* x, const float* p, const fl
   SFS_CUDA(cudaGetLastError());
   if (loss) {
     SFS_CUDA(cudaMemcpyAsync(h->hlsum, h->lsum, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SFS_CUDA(cudaMemcpyAsync(h->hgerr, h->gerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     SFS_CUDA(cudaStreamSynchronize(h->stream));
+    st = check_gemm_error(h);
+    if (st != SFT_OK) return st;
     *loss = host_loss(h, n);
   }
   return SFT_OK;
