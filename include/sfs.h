@@ -81,15 +81,23 @@ sft_status sfs_train_step(sfs_handle h, const float* x, const float* p, const fl
                           double lr, double wd, float* loss);
 
 /* Relative L2 error ||a_b - b_b|| / ||b_b|| of n maps (device) into host out[n] (FP64
- * accumulation).  Synchronises. */
+ * accumulation).  Any n >= 1 (reduced max_batch maps at a time); synchronises
+ * once. */
 sft_status sfs_rel_l2(sfs_handle h, const float* a, const float* b, int32_t n, double* out);
 
 /* Total flux sum A B and unsigned flux sum A |B| (code units, FP64) of n
  * maps (device [n][256][512]) into host out[2n], with the grid convention of
  * sft.h (poles included, caps of area 2 pi (1 - cos(dtheta/2))); the judge
- * of the surrogate ensemble uses them for the flux-drift test.  n <= max_batch.
- * Synchronises. */
+ * of the surrogate ensemble uses them for the flux-drift test.  Any n >= 1
+ * (reduced max_batch maps at a time); synchronises once. */
 sft_status sfs_flux(sfs_handle h, const float* maps, int32_t n, double* out);
+
+/* SMs the fused inference forward may occupy (its persistent blocks hold
+ * most of an SM's shared memory each); 0 (the default) means all.  A caller
+ * that runs solver work on another stream beside the forward passes leaves
+ * the remaining SMs to it.  No counterpart in the paper (a scheduling
+ * control of this implementation). */
+sft_status sfs_set_sm_budget(sfs_handle h, int32_t n_sm);
 
 /* Counters: GEMM launches and floating-point operations issued so far. */
 sft_status sfs_counters(sfs_handle h, int64_t* gemm_launches, double* gemm_flops, int64_t* kernel_launches);

@@ -485,7 +485,9 @@ struct sfs_net {
   int* hgerr = nullptr;  // pinned host copy
   float* part = nullptr;
   long long part_elems = 0;
-  double *sums = nullptr, *hsums = nullptr;
+  double* sums = nullptr;
+  double* hbig = nullptr;  // pinned staging of the chunked reductions
+  long long hbig_n = 0;
   double* area = nullptr;   // per-row area weight of one entry
   double* alpha = nullptr;  // per (map, row) rotation angle
   double area_total = 0.0;  // sum of the weights over the whole map
@@ -502,6 +504,7 @@ struct sfs_net {
   unsigned char* img = nullptr;
   long long pver = 0, img_pver = -1;
   int n_sm = 0;
+  int sm_budget = 0;  // > 0: the fused forward's persistent blocks (SMs) are capped at this
   sfs_fused::ParamOffsets po{};
 };
 
@@ -673,7 +676,8 @@ sft_status forward_fused(sfs_handle h, const float* x, const float* p, int nb) {
     h->img_pver = h->pver;
     h->kernels += 1;
   }
-  SFS_CUDA(sfs_fused::forward(h->img, h->L, h->P, h->po, x, h->R, p, nb, h->XN, h->n_sm, h->stream));
+  const int sms = (h->sm_budget > 0 && h->sm_budget < h->n_sm) ? h->sm_budget : h->n_sm;
+  SFS_CUDA(sfs_fused::forward(h->img, h->L, h->P, h->po, x, h->R, p, nb, h->XN, sms, h->stream));
   h->kernels += 1;
   h->flops += 2.0 * nb * NTOK *
               ((double)KE * h->C + h->L * (2.0 * 2 * h->M * h->C + 2.0 * 2 * h->C * h->C) + 16.0 * h->C);
@@ -751,6 +755,28 @@ sft_status check_batch(sfs_handle h, const void* a, const void* b, int n) {
   if (!a || !b) return fail("NULL argument", SFT_ERR_ARG);
   if ((reinterpret_cast<uintptr_t>(a) & 15) != 0) return fail("maps must be 16-byte aligned", SFT_ERR_ARG);
   if (n <= 0 || n > h->maxb) return fail("batch size out of range", SFT_ERR_ARG);
+  return SFT_OK;
+}
+
+// maps of the reductions: any count, in chunks of max_batch
+sft_status check_maps(sfs_handle h, const void* a, const void* b, int n) {
+  if (!h) return fail("NULL handle", SFT_ERR_ARG);
+  if (!a || !b) return fail("NULL argument", SFT_ERR_ARG);
+  if ((reinterpret_cast<uintptr_t>(a) & 15) != 0 || (reinterpret_cast<uintptr_t>(b) & 15) != 0)
+    return fail("maps must be 16-byte aligned", SFT_ERR_ARG);
+  if (n <= 0) return fail("map count out of range", SFT_ERR_ARG);
+  return SFT_OK;
+}
+
+// pinned host staging of at least n doubles (grown between calls: every call
+// that uses it ends with a stream synchronisation)
+sft_status stage_host(sfs_handle h, long long n) {
+  if (n <= h->hbig_n) return SFT_OK;
+  if (h->hbig) cudaFreeHost(h->hbig);
+  h->hbig = nullptr;
+  h->hbig_n = 0;
+  if (cudaMallocHost(&h->hbig, n * sizeof(double)) != cudaSuccess) return fail("pinned alloc failed", SFT_ERR_OOM);
+  h->hbig_n = n;
   return SFT_OK;
 }
 
@@ -897,7 +923,6 @@ sft_status sfs_create(const sfs_config* cfg, void* cuda_stream, sfs_handle* out)
     if (cudaMemcpy(h->area, ar.data(), H * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail("area upload failed"));
   }
-  if (cudaMallocHost(&h->hsums, 2 * nb * sizeof(double)) != cudaSuccess) return bail(fail("pinned alloc failed"));
   if (cudaMallocHost(&h->hlsum, 3 * nb * sizeof(double)) != cudaSuccess) return bail(fail("pinned alloc failed"));
   if (cudaMallocHost(&h->hgerr, sizeof(int)) != cudaSuccess) return bail(fail("pinned alloc failed"));
   *h->hgerr = 0;
@@ -931,15 +956,22 @@ sft_status sfs_destroy(sfs_handle h) {
   if (!h) return SFT_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : h->allocs) cudaFree(p);
-  if (h->hsums) cudaFreeHost(h->hsums);
   if (h->hlsum) cudaFreeHost(h->hlsum);
   if (h->hgerr) cudaFreeHost(h->hgerr);
+  if (h->hbig) cudaFreeHost(h->hbig);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return SFT_OK;
 }
 
 int64_t sfs_num_params(sfs_handle h) { return h ? h->np : 0; }
+
+sft_status sfs_set_sm_budget(sfs_handle h, int32_t n_sm) {
+  if (!h) return fail("NULL handle", SFT_ERR_ARG);
+  if (n_sm < 0) return fail("SM budget must be >= 0", SFT_ERR_ARG);
+  h->sm_budget = n_sm;
+  return SFT_OK;
+}
 
 sft_status sfs_set_params(sfs_handle h, const float* host_params) {
   if (!h || !host_params) return fail("NULL argument", SFT_ERR_ARG);
@@ -1024,29 +1056,41 @@ sft_status sfs_train_step(sfs_handle h, const float* x, const float* p, const fl
 }
 
 sft_status sfs_rel_l2(sfs_handle h, const float* a, const float* b, int32_t n, double* out) {
-  sft_status st = check_batch(h, a, b, n);
+  sft_status st = check_maps(h, a, b, n);
   if (st != SFT_OK) return st;
   if (!out) return fail("NULL output", SFT_ERR_ARG);
-  sumsq_kernel<<<dim3(kRedBlocks, n), 256, 0, h->stream>>>(a, b, n, h->mpart);
-  fold_map_sums<<<n, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->sums);
-  h->kernels += 2;
-  SFS_CUDA(cudaGetLastError());
-  SFS_CUDA(cudaMemcpyAsync(h->hsums, h->sums, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  st = stage_host(h, 2 * (long long)n);
+  if (st != SFT_OK) return st;
+  for (int c0 = 0; c0 < n; c0 += h->maxb) {  // chunks of max_batch maps, one synchronisation
+    const int m = std::min(h->maxb, n - c0);
+    const long long off = (long long)c0 * H * W;
+    sumsq_kernel<<<dim3(kRedBlocks, m), 256, 0, h->stream>>>(a + off, b + off, m, h->mpart);
+    fold_map_sums<<<m, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->sums);
+    h->kernels += 2;
+    SFS_CUDA(cudaGetLastError());
+    SFS_CUDA(cudaMemcpyAsync(h->hbig + 2 * c0, h->sums, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
   SFS_CUDA(cudaStreamSynchronize(h->stream));
-  for (int i = 0; i < n; ++i) out[i] = std::sqrt(h->hsums[2 * i] / h->hsums[2 * i + 1]);
+  for (int i = 0; i < n; ++i) out[i] = std::sqrt(h->hbig[2 * i] / h->hbig[2 * i + 1]);
   return SFT_OK;
 }
 
 sft_status sfs_flux(sfs_handle h, const float* maps, int32_t n, double* out) {
-  sft_status st = check_batch(h, maps, maps, n);
+  sft_status st = check_maps(h, maps, maps, n);
   if (st != SFT_OK) return st;
   if (!out) return fail("NULL output", SFT_ERR_ARG);
-  flux_kernel<<<dim3(kRedBlocks, n), 256, 0, h->stream>>>(maps, h->area, h->mpart);
-  fold_map_sums<<<n, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->sums);
-  h->kernels += 2;
-  SFS_CUDA(cudaGetLastError());
-  SFS_CUDA(cudaMemcpyAsync(out, h->sums, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  st = stage_host(h, 2 * (long long)n);
+  if (st != SFT_OK) return st;
+  for (int c0 = 0; c0 < n; c0 += h->maxb) {
+    const int m = std::min(h->maxb, n - c0);
+    flux_kernel<<<dim3(kRedBlocks, m), 256, 0, h->stream>>>(maps + (long long)c0 * H * W, h->area, h->mpart);
+    fold_map_sums<<<m, 32, 0, h->stream>>>(h->mpart, kRedBlocks, 2, h->sums);
+    h->kernels += 2;
+    SFS_CUDA(cudaGetLastError());
+    SFS_CUDA(cudaMemcpyAsync(h->hbig + 2 * c0, h->sums, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
   SFS_CUDA(cudaStreamSynchronize(h->stream));
+  std::memcpy(out, h->hbig, 2 * (size_t)n * sizeof(double));
   return SFT_OK;
 }
 

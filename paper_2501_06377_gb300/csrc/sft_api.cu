@@ -69,6 +69,7 @@ struct RealInfo {
 };
 
 constexpr int kMaxChains = 2;   // concurrent launch chains of the fused RKL2 passes
+constexpr int kStageRing = 8;   // pinned staging buffers of the configuration tables
 constexpr int kMaxConfigs = 24; // cached step configurations (tile tables, graphs) per wave
 
 struct Config {
@@ -96,6 +97,7 @@ struct Config {
   Tile* d_atiles = nullptr;      // advection tiles
   StepParam* d_sp = nullptr;
   void* d_coef = nullptr;
+  void* d_blob = nullptr;        // the one allocation holding the tables above
   cudaGraphExec_t exec = nullptr;
   uint64_t last_use = 0;
   int uses = 0;  // steps run with this configuration (graphs are captured from the second)
@@ -175,6 +177,13 @@ struct sft_grid {
   int n_sm = 152;                               // streaming multiprocessors of the device
   cudaEvent_t fork = nullptr;                   // ordering events (no timing)
   cudaEvent_t join[kMaxChains] = {};
+  // pinned staging of the step-configuration tables: a ring of buffers, each
+  // reused once the upload that last read it has completed (its event)
+  char* cfg_stage[kStageRing] = {};
+  size_t cfg_stage_bytes[kStageRing] = {};
+  cudaEvent_t cfg_stage_ev[kStageRing] = {};
+  bool cfg_stage_pending[kStageRing] = {};
+  int cfg_stage_next = 0;
   sft_stats stats{};
 };
 
@@ -467,15 +476,12 @@ template <typename T> T* ptr(void* p) { return static_cast<T*>(p); }
 // still in flight is released by the runtime when it completes).
 void free_config(Config& c, cudaStream_t st) {
   if (c.exec) cudaGraphExecDestroy(c.exec);
-  if (c.d_ftiles) cudaFreeAsync(c.d_ftiles, st);
-  c.d_ftiles = nullptr;
-  if (c.d_tiles) cudaFreeAsync(c.d_tiles, st);
-  if (c.d_atiles) cudaFreeAsync(c.d_atiles, st);
-  c.d_atiles = nullptr;
-  if (c.d_sp) cudaFreeAsync(c.d_sp, st);
-  if (c.d_coef) cudaFreeAsync(c.d_coef, st);
+  if (c.d_blob) cudaFreeAsync(c.d_blob, st);
   c.exec = nullptr;
+  c.d_blob = nullptr;
+  c.d_ftiles = nullptr;
   c.d_tiles = nullptr;
+  c.d_atiles = nullptr;
   c.d_sp = nullptr;
   c.d_coef = nullptr;
 }
@@ -513,6 +519,13 @@ void free_handle(sft_handle h) {
   if (h->fork) cudaEventDestroy(h->fork);
   for (auto& e : h->join)
     if (e) cudaEventDestroy(e);
+  for (int i = 0; i < kStageRing; ++i) {
+    if (h->cfg_stage_ev[i]) {
+      if (h->cfg_stage_pending[i]) cudaEventSynchronize(h->cfg_stage_ev[i]);
+      cudaEventDestroy(h->cfg_stage_ev[i]);
+    }
+    if (h->cfg_stage[i]) cudaFreeHost(h->cfg_stage[i]);
+  }
   for (auto& q : h->side)
     if (q) cudaStreamDestroy(q);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -550,18 +563,18 @@ std::string check_desc(const sft_grid* h) {
   std::vector<std::pair<int64_t, int64_t>> ext;
   for (int r = 0; r < h->n_real; ++r) {
     const RealDesc& d = h->desc[r];
-    const std::string at = " (realization " + std::to_string(r) + ")";
-    if (d.nt < 5 || d.np < 8 || d.pitch < (int)round_up(d.np, 4) || d.pitch % 4 != 0) return "shape" + at;
+    const auto at_ = [r]() { return " (realization " + std::to_string(r) + ")"; };  // formatted on failure only
+    if (d.nt < 5 || d.np < 8 || d.pitch < (int)round_up(d.np, 4) || d.pitch % 4 != 0) return "shape" + at_();
     const int64_t cells = (int64_t)d.nt * d.pitch;
-    if (d.off < 0 || d.off + cells > h->state_elems) return "state extent" + at;
-    if (d.woff < 0 || d.woff + cells > h->work_elems) return "work extent" + at;
+    if (d.off < 0 || d.off + cells > h->state_elems) return "state extent" + at_();
+    if (d.woff < 0 || d.woff + cells > h->work_elems) return "work extent" + at_();
     if (h->fused_ok && (d.poff < 0 || d.poff + fused::part_elems(d.np) > h->polar_elems))
-      return "ring-sum partials extent" + at;
-    if (h->fused_ok && (d.band <= fused::K || d.band > (1 << 16))) return "band rows" + at;
-    if (d.geo < 0 || d.geo + d.nt > h->geo_rows) return "geometry rows" + at;
-    if (d.flow < 0 || d.flow + d.nt > h->flow_rows) return "flow rows" + at;
-    if (d.col < 0 || d.col + d.np > h->col_entries) return "longitude table" + at;
-    if (d.shape < 0 || d.shape >= (int)h->shapes.size()) return "shape id" + at;
+      return "ring-sum partials extent" + at_();
+    if (h->fused_ok && (d.band <= fused::K || d.band > (1 << 16))) return "band rows" + at_();
+    if (d.geo < 0 || d.geo + d.nt > h->geo_rows) return "geometry rows" + at_();
+    if (d.flow < 0 || d.flow + d.nt > h->flow_rows) return "flow rows" + at_();
+    if (d.col < 0 || d.col + d.np > h->col_entries) return "longitude table" + at_();
+    if (d.shape < 0 || d.shape >= (int)h->shapes.size()) return "shape id" + at_();
     ext.emplace_back(d.off, d.off + cells);
   }
   std::sort(ext.begin(), ext.end());
@@ -571,20 +584,22 @@ std::string check_desc(const sft_grid* h) {
 }
 
 std::string check_tiles(const sft_grid* h, const std::vector<Tile>& tiles, bool fused_tiles) {
+  // (the message is formatted only for a failing tile: this runs over every
+  // tile of every new step configuration)
+  auto at = [](size_t i) { return " (tile " + std::to_string(i) + ")"; };
   for (size_t i = 0; i < tiles.size(); ++i) {
     const Tile& t = tiles[i];
-    const std::string at = " (tile " + std::to_string(i) + ")";
-    if (t.r < 0 || t.r >= h->n_real) return "realization index" + at;
+    if (t.r < 0 || t.r >= h->n_real) return "realization index" + at(i);
     const RealDesc& d = h->desc[t.r];
     const int kind = t.kind & 3;
-    if (kind == 3) return "tile kind" + at;
+    if (kind == 3) return "tile kind" + at(i);
     if (kind != 0) continue;
     if (fused_tiles) {
-      if (t.j0 < 0 || t.j0 >= fused::n_bands(d.nt, d.band) * fused::n_strips(d.np)) return "fused work item" + at;
+      if (t.j0 < 0 || t.j0 >= fused::n_bands(d.nt, d.band) * fused::n_strips(d.np)) return "fused work item" + at(i);
     } else {
       const int lx = t.kind >> 8;
-      if (lx < 0 || (1 << lx) > kThreads) return "tile width" + at;
-      if (t.j0 < 1 || t.j0 > d.nt - 2 || t.k0 < 0 || t.k0 >= d.np) return "tile origin" + at;
+      if (lx < 0 || (1 << lx) > kThreads) return "tile width" + at(i);
+      if (t.j0 < 1 || t.j0 > d.nt - 2 || t.k0 < 0 || t.k0 >= d.np) return "tile origin" + at(i);
     }
   }
   return "";
@@ -677,6 +692,7 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
   }
   c->realization_steps = (int)order.size();
   c->fused = h->fused;
+  std::vector<Tile> ft;  // fused-pass tiles
   if (c->fused) {
     // fused passes start at stages 2, 2+K, 2+2K, ...; stage 1 uses the
     // single-stage kernel (it forms G = dt L(Y_0)).
@@ -689,7 +705,6 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
       pass_tiles = tmp.size();
     }
     c->n_chains = pass_tiles >= (size_t)4 * h->n_sm ? std::min<int>(kMaxChains, (int)order.size()) : 1;
-    std::vector<Tile> ft;
     for (int ch = 0; ch < c->n_chains; ++ch) {
       c->fbase[ch] = (int)ft.size();
       std::vector<int> mem, fend;  // chain members (descending s) and their interior tile ends
@@ -717,11 +732,6 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     }
     const std::string bad = check_tiles(h, ft, true);
     if (!bad.empty()) return fail(h, SFT_ERR_STATE, "internal table check: " + bad);
-    if (!ft.empty()) {
-      SFT_CUDA(h, dev_malloc_async(&c->d_ftiles, ft.size() * sizeof(Tile), h->stream));
-      SFT_CUDA(h, cudaMemcpyAsync(c->d_ftiles, ft.data(), ft.size() * sizeof(Tile),
-                                  cudaMemcpyHostToDevice, h->stream));
-    }
   }
   c->n_adv_tiles = (int)atiles.size();
   c->stage_tiles.assign(c->smax + 1, 0);
@@ -735,25 +745,51 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     if (bad.empty()) bad = check_tiles(h, atiles, false);
     if (!bad.empty()) return fail(h, SFT_ERR_STATE, "internal table check: " + bad);
   }
-  if (!atiles.empty()) {
-    SFT_CUDA(h, dev_malloc_async(&c->d_atiles, atiles.size() * sizeof(Tile), h->stream));
-    SFT_CUDA(h, cudaMemcpyAsync(c->d_atiles, atiles.data(), atiles.size() * sizeof(Tile),
-                                cudaMemcpyHostToDevice, h->stream));
-  }
-  if (!tiles.empty()) {
-    SFT_CUDA(h, dev_malloc_async(&c->d_tiles, tiles.size() * sizeof(Tile), h->stream));
-    SFT_CUDA(h, cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(Tile),
-                                cudaMemcpyHostToDevice, h->stream));
-  }
-  SFT_CUDA(h, dev_malloc_async(&c->d_sp, sp.size() * sizeof(StepParam), h->stream));
-  SFT_CUDA(h, cudaMemcpyAsync(c->d_sp, sp.data(), sp.size() * sizeof(StepParam),
-                              cudaMemcpyHostToDevice, h->stream));
   if (coefs.empty()) coefs.push_back(Coef<T>{});
-  SFT_CUDA(h, dev_malloc_async(&c->d_coef, coefs.size() * sizeof(Coef<T>), h->stream));
-  SFT_CUDA(h, cudaMemcpyAsync(c->d_coef, coefs.data(), coefs.size() * sizeof(Coef<T>),
-                              cudaMemcpyHostToDevice, h->stream));
-  // (pageable-source async copies are staged before they return: the host
-  // vectors may die at return without a synchronisation)
+  {
+    // all tables in one device allocation, uploaded by one copy from a pinned
+    // staging buffer (a handful of allocations and pageable copies per new
+    // configuration cost more host time than the step's launches)
+    size_t total = 0;
+    auto place = [&total](size_t bytes) {
+      const size_t o = total;
+      total += (bytes + 255) & ~(size_t)255;
+      return o;
+    };
+    const size_t o_ft = place(ft.size() * sizeof(Tile)), o_at = place(atiles.size() * sizeof(Tile));
+    const size_t o_ti = place(tiles.size() * sizeof(Tile)), o_sp = place(sp.size() * sizeof(StepParam));
+    const size_t o_cf = place(coefs.size() * sizeof(Coef<T>));
+    const int slot = h->cfg_stage_next;
+    h->cfg_stage_next = (slot + 1) % kStageRing;
+    if (h->cfg_stage_pending[slot]) {  // the upload that last read this buffer
+      SFT_CUDA(h, cudaEventSynchronize(h->cfg_stage_ev[slot]));
+      h->cfg_stage_pending[slot] = false;
+    }
+    if (h->cfg_stage_bytes[slot] < total) {
+      const size_t want = std::max<size_t>(total, 2 * h->cfg_stage_bytes[slot]);
+      if (h->cfg_stage[slot]) cudaFreeHost(h->cfg_stage[slot]);
+      h->cfg_stage[slot] = nullptr;
+      h->cfg_stage_bytes[slot] = 0;
+      SFT_CUDA(h, host_malloc(&h->cfg_stage[slot], want));
+      h->cfg_stage_bytes[slot] = want;
+    }
+    char* st = h->cfg_stage[slot];
+    if (!ft.empty()) std::memcpy(st + o_ft, ft.data(), ft.size() * sizeof(Tile));
+    if (!atiles.empty()) std::memcpy(st + o_at, atiles.data(), atiles.size() * sizeof(Tile));
+    if (!tiles.empty()) std::memcpy(st + o_ti, tiles.data(), tiles.size() * sizeof(Tile));
+    std::memcpy(st + o_sp, sp.data(), sp.size() * sizeof(StepParam));
+    std::memcpy(st + o_cf, coefs.data(), coefs.size() * sizeof(Coef<T>));
+    SFT_CUDA(h, dev_malloc_async(&c->d_blob, total, h->stream));
+    char* b = static_cast<char*>(c->d_blob);
+    SFT_CUDA(h, cudaMemcpyAsync(b, st, total, cudaMemcpyHostToDevice, h->stream));
+    SFT_CUDA(h, cudaEventRecord(h->cfg_stage_ev[slot], h->stream));
+    h->cfg_stage_pending[slot] = true;
+    c->d_ftiles = ft.empty() ? nullptr : reinterpret_cast<Tile*>(b + o_ft);
+    c->d_atiles = atiles.empty() ? nullptr : reinterpret_cast<Tile*>(b + o_at);
+    c->d_tiles = tiles.empty() ? nullptr : reinterpret_cast<Tile*>(b + o_ti);
+    c->d_sp = reinterpret_cast<StepParam*>(b + o_sp);
+    c->d_coef = b + o_cf;
+  }
   // keep at most kMaxConfigs configurations per wave
   if ((int)w.configs.size() >= kMaxConfigs) {
     auto it = std::min_element(w.configs.begin(), w.configs.end(),
@@ -1572,6 +1608,7 @@ sft_status sft_create_grid(const sft_shape* shapes, int32_t n_real, sft_prec pre
   for (auto& e : h->ev) CREATE_CUDA(cudaEventCreate(&e));
   CREATE_CUDA(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device));
   CREATE_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+  for (auto& e : h->cfg_stage_ev) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (int ch = 1; ch < kMaxChains; ++ch) {
     CREATE_CUDA(cudaStreamCreateWithFlags(&h->side[ch], cudaStreamNonBlocking));
     CREATE_CUDA(cudaEventCreateWithFlags(&h->join[ch], cudaEventDisableTiming));

@@ -170,15 +170,22 @@ def _warm_merge_ops(S, prop):
     torch.cuda.current_stream().synchronize()
 
 
-def _advance_subset(g, gs, S, members, t0, t1):
+def _advance_subset(g, gs, S, members, t0, t1, sel=None, ready=None):
     """Queue the plain solver's day [t0, t1] for the given members (every
     other member idles at t1) on the grid's stream gs, after the maps of S
-    written so far on the current stream."""
+    written so far on the current stream.  With ``sel`` (the members' rows of
+    S, gathered on the current stream) and ``ready`` (an event recorded after
+    that gather), gs waits for the event only, not for later work of the
+    current stream."""
     import torch
     g.set_time(t1)
     if len(members):
-        sel = S.index_select(0, _dev_index(np.asarray(members, dtype=np.int64))).contiguous()
-        gs.wait_stream(torch.cuda.current_stream())
+        if sel is None:
+            sel = S.index_select(0, _dev_index(np.asarray(members, dtype=np.int64))).contiguous()
+            gs.wait_stream(torch.cuda.current_stream())
+        else:
+            gs.wait_event(ready)
+        sel.record_stream(gs)  # gs reads it: its memory is not reused before that
         g.set_states(members, sel)
         g.set_times(members, t0)
     g.step(t1)
@@ -195,20 +202,26 @@ def _fetch(g, gs, members):
     return out
 
 
-def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, seed=7, max_fail=0.25):
+def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, seed=7, max_fail=0.25,
+            solver_sms=48, solver_priority=-1):
     """Surrogate + judge + plain-solver fallback.  Returns (final maps, stats).
 
     A day on which more than ``max_fail`` of the spot checks fail rejects
     every proposal of that day (the unchecked members cannot be trusted
     either); otherwise only the failing members fall back.  stats["phase_s"]
-    splits the host time of the days: queueing the spot checks' solver day,
-    the proposals and their flux sums (running while the solver day does),
-    waiting for and fetching the solver's maps, and the rest (spot-check
-    L2, updates, flux sums of the accepted maps)."""
+    splits the host time of the days: queueing the spot checks' solver day
+    (while the GPU runs the proposals, which are enqueued first), the
+    proposals and their flux sums, waiting for and fetching the solver's
+    maps, and the rest (spot-check L2, updates, flux sums of the accepted
+    maps).  ``solver_sms`` > 0 keeps that many SMs free of the surrogate's
+    persistent forward blocks, for the solver's kernels on the grid stream
+    (created with ``solver_priority``) to run beside the proposals."""
     import torch
     n = S0.shape[0]
     params = P.cpu().numpy().astype(np.float64)
-    gs = torch.cuda.Stream()
+    gs = torch.cuda.Stream(priority=solver_priority)
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    net.set_sm_budget(max(1, n_sm - solver_sms) if solver_sms > 0 else 0)
     g = _grid(n, params, stream=gs)
     S = S0.clone()
     prop = torch.empty_like(S)
@@ -225,12 +238,18 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
         chk = np.sort(rng.choice(n, size=min(spot, n), replace=False))
         run = np.zeros(n, dtype=bool)
         run[chk] = True
-        # the plain solver's day for the spot-checked members is queued first
-        # (sft_step returns without waiting) so that it runs on the grid's
-        # stream while the surrogate proposes on its own
-        _advance_subset(g, gs, S, chk, t_day0, t_day1)
-        tb = time.perf_counter()
+        # the spot-checked members' rows are gathered, then the proposals are
+        # enqueued (cheap on the host) and the plain solver's day for those
+        # members is queued on the grid's stream (sft_step returns without
+        # waiting; its host work overlaps the proposals on the GPU, and its
+        # kernels run beside them)
+        sel = S.index_select(0, _dev_index(chk.astype(np.int64))).contiguous()
+        ready = torch.cuda.Event()
+        ready.record()
         propose(net, S, P, prop)
+        tb = time.perf_counter()
+        _advance_subset(g, gs, S, chk, t_day0, t_day1, sel=sel, ready=ready)
+        tb2 = time.perf_counter()
         phi_new, abs_new = _fluxes(net, prop)
         tc = time.perf_counter()
         drift = np.abs(phi_new - phi_old) / np.maximum(abs_old, 1e-300)
@@ -270,8 +289,8 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
         stats.setdefault("spot_l2_median", []).append(float(np.median(err)))
         phi_old, abs_old = _fluxes(net, S)
         te = time.perf_counter()
-        ph["queue_spot_day"] += tb - ta
-        ph["proposals_and_flux"] += tc - tb
+        ph["queue_spot_day"] += tb2 - tb
+        ph["proposals_and_flux"] += (tb - ta) + (tc - tb2)
         ph["fetch_solver_maps"] += td - tc
         ph["rest"] += te - td
     torch.cuda.synchronize()
@@ -279,6 +298,8 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
     stats["member_days_per_s"] = stats["member_days"] / stats["seconds"]
     stats["phase_s"] = ph
     stats["tile_rows"] = g.get_tile_rows(0)  # the autotuner's choice for this grid shape
+    stats["solver_sms"] = solver_sms
+    net.set_sm_budget(0)
     g.close()
     return S, stats
 

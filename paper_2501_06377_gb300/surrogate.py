@@ -34,6 +34,7 @@ _SIGS = {
                                  C.c_double, C.c_double, C.POINTER(C.c_float)]),
     "sfs_rel_l2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sfs_flux": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sfs_set_sm_budget": (C.c_int, [C.c_void_p, C.c_int32]),
     "sfs_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                C.POINTER(C.c_int64)]),
 }
@@ -120,27 +121,23 @@ class Surrogate:
         return float(loss.value) if want_loss else None
 
     def rel_l2(self, a, b):
-        """||a - b|| / ||b|| per map, in chunks of max_batch."""
+        """||a - b|| / ||b|| per map (one call, one synchronisation)."""
         n = a.shape[0]
         out = np.empty(n, dtype=np.float64)
-        for c0 in range(0, n, self.max_batch):
-            c1 = min(n, c0 + self.max_batch)
-            o = np.empty(c1 - c0, dtype=np.float64)
-            self._check(self.lib.sfs_rel_l2(self.h, _dev(a[c0:c1]), _dev(b[c0:c1]), c1 - c0,
-                                            C.c_void_p(o.ctypes.data)))
-            out[c0:c1] = o
+        self._check(self.lib.sfs_rel_l2(self.h, _dev(a), _dev(b), n, C.c_void_p(out.ctypes.data)))
         return out
 
     def flux(self, maps):
-        """(signed, unsigned) FP64 flux of each map, in chunks of max_batch."""
+        """(signed, unsigned) FP64 flux of each map (one call, one synchronisation)."""
         n = maps.shape[0]
-        out = np.empty((n, 2), dtype=np.float64)
-        for c0 in range(0, n, self.max_batch):
-            c1 = min(n, c0 + self.max_batch)
-            o = np.empty(2 * (c1 - c0), dtype=np.float64)
-            self._check(self.lib.sfs_flux(self.h, _dev(maps[c0:c1]), c1 - c0, C.c_void_p(o.ctypes.data)))
-            out[c0:c1] = o.reshape(-1, 2)
-        return out[:, 0], out[:, 1]
+        o = np.empty(2 * n, dtype=np.float64)
+        self._check(self.lib.sfs_flux(self.h, _dev(maps), n, C.c_void_p(o.ctypes.data)))
+        o = o.reshape(-1, 2)
+        return o[:, 0].copy(), o[:, 1].copy()
+
+    def set_sm_budget(self, n_sm):
+        """SMs the fused forward may occupy (0: all)."""
+        self._check(self.lib.sfs_set_sm_budget(self.h, int(n_sm)))
 
     def counters(self):
         g, f, k = C.c_int64(), C.c_double(), C.c_int64()
