@@ -118,64 +118,134 @@ __global__ void rot_angle_kernel(const float* __restrict__ p, int rows, double* 
   }
 }
 
-// Layer R by FFT, one block of 256 threads per map row: the 512-point DFT of
-// the real row (radix-2 in shared memory: decimation in time from a
-// bit-reversed load), Y_k = X_k exp(-i k alpha_row) on modes 0..256, the
-// Hermitian extension Z_{512-k} = conj(Y_k) (the Nyquist mode keeps its real
-// part only, as the truncated synthesis G does), and the inverse transform
-// (decimation in frequency, conjugate twiddles) scaled by 1/512.  The same map
-// as r = phase(x F^T) G^T, in FP32 with O(log n) rounding.
-// tw[j] = exp(-2 pi i j / 512), j < 256.
+// Layer R by FFT: the 512-point DFT X of the real row, Y_k = X_k
+// exp(-i k alpha_row) on modes 0..256, the Hermitian extension Y_{512-k} =
+// conj(Y_k) (the Nyquist mode keeps its real part only, as the truncated
+// synthesis G does), and the inverse transform scaled by 1/512, taken as
+// Re(DFT(conj Y)) / 512.  The same map as r = phase(x F^T) G^T, in FP32 with
+// O(log n) rounding.
+//
+// Each DFT is three radix-8 passes of the Stockham autosort formulation
+// (Govindaraju et al., SC 2008): with Ns = 1, 8, 64, butterfly j (0..63)
+// reads v_q = a[j + 64 q], multiplies v_q by exp(-2 pi i q (j mod Ns) /
+// (8 Ns)), takes the 8-point DFT and writes it to b[(j / Ns) 8 Ns + (j mod Ns)
+// + q Ns]; after the third pass butterfly j holds X_{j + 64 q} in order.  A
+// block of 256 threads transforms 4 rows (64 threads each); the passes
+// exchange through shared memory.  tw[j] = exp(-2 pi i j / 512), j < 256.
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__global__ void __launch_bounds__(256) rot_fft_kernel(const float* __restrict__ x, const double* __restrict__ alpha,
-                                                      const float2* __restrict__ tw, float* __restrict__ r) {
-  static_assert(W == 512, "rot_fft_kernel is written for 512-point rows");
-  __shared__ float2 s[W];
-  const int row = blockIdx.x, t = threadIdx.x;
-  const float* xr = x + (long long)row * W;
-  s[__brev(t) >> 23] = make_float2(xr[t], 0.f);
-  s[__brev(t + 256) >> 23] = make_float2(xr[t + 256], 0.f);
-  __syncthreads();
-  for (int half = 1; half < W; half <<= 1) {  // DIT stages
-    const int pos = t & (half - 1), i0 = ((t - pos) << 1) + pos, i1 = i0 + half;
-    const float2 u = s[i0], v = cmul(s[i1], tw[pos * (256 / half)]);
-    s[i0] = make_float2(u.x + v.x, u.y + v.y);
-    s[i1] = make_float2(u.x - v.x, u.y - v.y);
-    __syncthreads();
+// in-place 8-point DFT (exponent sign -1): two radix-2 layers and radix-4
+// DFTs of the even and odd outputs
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  constexpr float c = 0.70710678118654752f;
+  float2 a[4], b[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = make_float2(v[k].x + v[k + 4].x, v[k].y + v[k + 4].y);
+    b[k] = make_float2(v[k].x - v[k + 4].x, v[k].y - v[k + 4].y);
   }
-  // phase on k = t (and k = 256 by thread 0); Z_{512-k} = conj(Y_k) lands in
-  // slots 257..511, which no thread reads
-  const double a = alpha[row];
-  for (int k = t; k <= W / 2; k += 256) {
+  // b_k *= exp(-2 pi i k / 8)
+  b[1] = make_float2(c * (b[1].x + b[1].y), c * (b[1].y - b[1].x));
+  b[2] = make_float2(b[2].y, -b[2].x);
+  b[3] = make_float2(c * (b[3].y - b[3].x), -c * (b[3].x + b[3].y));
+  float2* io[2] = {a, b};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // 4-point DFTs: outputs 2m + h
+    const float2* x = io[h];
+    const float2 s02 = make_float2(x[0].x + x[2].x, x[0].y + x[2].y), d02 = make_float2(x[0].x - x[2].x, x[0].y - x[2].y);
+    const float2 s13 = make_float2(x[1].x + x[3].x, x[1].y + x[3].y), d13 = make_float2(x[1].x - x[3].x, x[1].y - x[3].y);
+    v[h] = make_float2(s02.x + s13.x, s02.y + s13.y);
+    v[4 + h] = make_float2(s02.x - s13.x, s02.y - s13.y);
+    v[2 + h] = make_float2(d02.x + d13.y, d02.y - d13.x);  // d02 - i d13
+    v[6 + h] = make_float2(d02.x - d13.y, d02.y + d13.x);  // d02 + i d13
+  }
+}
+
+// One Stockham radix-8 pass of butterfly j on shared rows: a -> v -> b.
+template <int NS>
+__device__ __forceinline__ void stockham_pass(const float2* a, float2* b, const float2* tws, int j, float2 (&v)[8],
+                                              bool write) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = a[j + 64 * q];
+  if (NS > 1) {
+    const int e0 = (j % NS) * (512 / (8 * NS));  // exponent step (units of 2 pi / 512)
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      const int e = q * e0;  // < 512
+      const float2 w = e < 256 ? tws[e] : make_float2(-tws[e - 256].x, -tws[e - 256].y);
+      v[q] = cmul(v[q], w);
+    }
+  }
+  dft8(v);
+  if (write) {
+    const int base = (j / NS) * 8 * NS + (j % NS);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) b[base + NS * q] = v[q];
+  }
+}
+
+__global__ void __launch_bounds__(256) rot_fft_kernel(const float* __restrict__ x, const double* __restrict__ alpha,
+                                                      const float2* __restrict__ tw, int rows, float* __restrict__ r) {
+  static_assert(W == 512, "rot_fft_kernel is written for 512-point rows");
+  __shared__ float2 tws[256];
+  __shared__ float2 s0[4][W], s1[4][W];
+  const int t = threadIdx.x, q4 = t >> 6, j = t & 63;
+  const int row = blockIdx.x * 4 + q4;
+  const bool live = row < rows;
+  tws[t] = tw[t];
+  float2 v[8];
+  // pass 1 (Ns = 1) straight from the real row in global memory
+  const float* xr = x + (long long)(live ? row : 0) * W;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = make_float2(live ? xr[j + 64 * q] : 0.f, 0.f);
+  dft8(v);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s0[q4][8 * j + q] = v[q];
+  __syncthreads();
+  stockham_pass<8>(s0[q4], s1[q4], tws, j, v, true);
+  __syncthreads();
+  stockham_pass<64>(s1[q4], nullptr, tws, j, v, false);  // v[q] = X_{j + 64 q}
+  // phase on modes k = j + 64 q <= 256, Hermitian extension into s0
+  const double a = live ? alpha[row] : 0.0;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int k = j + 64 * q;
+    if (k > W / 2) break;
     const double ang = k * a;
     const double red = ang - (2.0 * PI) * rint(ang * (1.0 / (2.0 * PI)));  // in [-pi, pi]
     float sn, cs;
     sincosf((float)red, &sn, &cs);
-    const float2 X = s[k];
+    const float2 X = v[q];
     const float2 Y = make_float2(X.x * cs + X.y * sn, X.y * cs - X.x * sn);
     if (k == W / 2) {
-      s[k] = make_float2(Y.x, 0.f);
+      s0[q4][k] = make_float2(Y.x, 0.f);
     } else {
-      s[k] = Y;
-      if (k > 0) s[W - k] = make_float2(Y.x, -Y.y);
+      s0[q4][k] = Y;
+      if (k > 0) s0[q4][W - k] = make_float2(Y.x, -Y.y);
     }
   }
   __syncthreads();
-  for (int half = W / 2; half >= 1; half >>= 1) {  // DIF stages, conjugate twiddles
-    const int pos = t & (half - 1), i0 = ((t - pos) << 1) + pos, i1 = i0 + half;
-    const float2 u = s[i0], v = s[i1];
-    const float2 w = tw[pos * (256 / half)];
-    s[i0] = make_float2(u.x + v.x, u.y + v.y);
-    s[i1] = cmul(make_float2(u.x - v.x, u.y - v.y), make_float2(w.x, -w.y));
-    __syncthreads();
+  // inverse: the forward DFT of conj(Y), real part / 512
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float2 y = s0[q4][j + 64 * q];
+    v[q] = make_float2(y.x, -y.y);
   }
-  float* rr = r + (long long)row * W;
-  constexpr float inv = 1.0f / W;
-  rr[t] = s[__brev(t) >> 23].x * inv;
-  rr[t + 256] = s[__brev(t + 256) >> 23].x * inv;
+  dft8(v);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s1[q4][8 * j + q] = v[q];
+  __syncthreads();
+  stockham_pass<8>(s1[q4], s0[q4], tws, j, v, true);
+  __syncthreads();
+  stockham_pass<64>(s0[q4], nullptr, tws, j, v, false);  // v[q] = Z_{j + 64 q}
+  if (live) {
+    float* rr = r + (long long)row * W;
+    constexpr float inv = 1.0f / W;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) rr[j + 64 * q] = v[q].x * inv;
+  }
 }
 
 // E[token][48]: 4x4 patches of x/s and r/s, normalised parameters, cos/sin of
@@ -622,7 +692,7 @@ sft_status forward(sfs_handle h, const float* x, const float* p, int nb) {
   const long long ntok = (long long)nb * NTOK;
   // rotation layer r = phase(x F^T) G^T, by FFT per map row (FP32)
   rot_angle_kernel<<<grid_for((long long)nb * H), 256, 0, h->stream>>>(p, nb * H, h->alpha);
-  rot_fft_kernel<<<nb * H, 256, 0, h->stream>>>(x, h->alpha, h->tw, h->R);
+  rot_fft_kernel<<<(nb * H + 3) / 4, 256, 0, h->stream>>>(x, h->alpha, h->tw, nb * H, h->R);
   embed_kernel<<<grid_for(ntok), 256, 0, h->stream>>>(x, h->R, p, nb, h->E);
   h->kernels += 3;
   sft_status st = gemm(h, (int)ntok, C, KE, opnd(h->E, KE, 0, KMAJ), opnd(h->P + h->oWe, C, 0, MNMAJ), h->Hs[0], C, 0,
@@ -669,7 +739,7 @@ sft_status forward(sfs_handle h, const float* x, const float* p, int nb) {
 // flux-free centring.
 sft_status forward_fused(sfs_handle h, const float* x, const float* p, int nb) {
   rot_angle_kernel<<<grid_for((long long)nb * H), 256, 0, h->stream>>>(p, nb * H, h->alpha);
-  rot_fft_kernel<<<nb * H, 256, 0, h->stream>>>(x, h->alpha, h->tw, h->R);
+  rot_fft_kernel<<<(nb * H + 3) / 4, 256, 0, h->stream>>>(x, h->alpha, h->tw, nb * H, h->R);
   h->kernels += 2;
   if (h->img_pver != h->pver) {
     SFS_CUDA(sfs_fused::build_image(h->P, h->po, h->L, h->Fm, h->Gm, h->img, h->stream));
