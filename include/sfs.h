@@ -99,6 +99,21 @@ sft_status sfs_flux(sfs_handle h, const float* maps, int32_t n, double* out);
  * control of this implementation). */
 sft_status sfs_set_sm_budget(sfs_handle h, int32_t n_sm);
 
+/* One training-pass product on the handle's stream, for tests of the tensor-
+ * core GEMM: C[z] = alpha A[z] B[z] + beta C[z] + bias (A: M x K, B: K x N,
+ * device pointers).  Operand element (mn, k) is at p[mn*ld + k] (mn_major 0)
+ * or p[k*ld + mn] (mn_major 1), batch z at p + z*stride (stride 0: shared);
+ * *_bf16 = 1 for BF16 operands (16-byte aligned, ld and stride multiples of
+ * 8), 0 for FP32 (rounded to BF16, nearest even, as staged).  C is FP32,
+ * C[z][m*ldc + n] with C + z*sC; bias (may be NULL) is per column.  kchunk > 0
+ * splits K into batch chunks of kchunk (partial products into C[z], the
+ * operands unbatched).  Synchronises; SFT_ERR_CUDA if a wait inside the
+ * kernel ran out of time.  No counterpart in the paper (a test entry point). */
+sft_status sfs_debug_gemm(sfs_handle h, int32_t M, int32_t N, int32_t K, const void* A, int32_t a_bf16,
+                          int32_t a_mn_major, int64_t lda, int64_t sA, const void* B, int32_t b_bf16,
+                          int32_t b_mn_major, int64_t ldb, int64_t sB, float* C, int64_t ldc, int64_t sC,
+                          float alpha, float beta, const float* bias, int32_t kchunk, int32_t batch);
+
 /* Counters: GEMM launches and floating-point operations issued so far. */
 sft_status sfs_counters(sfs_handle h, int64_t* gemm_launches, double* gemm_flops, int64_t* kernel_launches);
 

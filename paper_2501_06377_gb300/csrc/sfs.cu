@@ -1043,6 +1043,24 @@ sft_status sfs_set_sm_budget(sfs_handle h, int32_t n_sm) {
   return SFT_OK;
 }
 
+sft_status sfs_debug_gemm(sfs_handle h, int32_t M, int32_t N, int32_t K, const void* A, int32_t a_bf16,
+                          int32_t a_mn_major, int64_t lda, int64_t sA, const void* B, int32_t b_bf16,
+                          int32_t b_mn_major, int64_t ldb, int64_t sB, float* C, int64_t ldc, int64_t sC,
+                          float alpha, float beta, const float* bias, int32_t kchunk, int32_t batch) {
+  if (!h) return fail("NULL handle", SFT_ERR_ARG);
+  if (!A || !B || !C) return fail("NULL argument", SFT_ERR_ARG);
+  if (M <= 0 || N <= 0 || K < 0 || batch <= 0 || kchunk < 0) return fail("GEMM shape out of range", SFT_ERR_ARG);
+  const sfs_gemm::Operand a{A, a_bf16 ? sfs_gemm::BF16 : sfs_gemm::F32, a_mn_major ? 1 : 0, lda, sA};
+  const sfs_gemm::Operand b{B, b_bf16 ? sfs_gemm::BF16 : sfs_gemm::F32, b_mn_major ? 1 : 0, ldb, sB};
+  const sfs_gemm::Problem pr{M, N, K, a, b, C, ldc, sC, alpha, beta, bias, kchunk, batch};
+  const cudaError_t e = sfs_gemm::launch(pr, h->gerr, h->stream);
+  if (e == cudaErrorInvalidValue) return fail("GEMM operands the kernel cannot take", SFT_ERR_ARG);
+  SFS_CUDA(e);
+  SFS_CUDA(cudaMemcpyAsync(h->hgerr, h->gerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  SFS_CUDA(cudaStreamSynchronize(h->stream));
+  return check_gemm_error(h);
+}
+
 sft_status sfs_set_params(sfs_handle h, const float* host_params) {
   if (!h || !host_params) return fail("NULL argument", SFT_ERR_ARG);
   SFS_CUDA(cudaMemcpyAsync(h->P, host_params, h->np * sizeof(float), cudaMemcpyHostToDevice, h->stream));

@@ -35,6 +35,10 @@ _SIGS = {
     "sfs_rel_l2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sfs_flux": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sfs_set_sm_budget": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sfs_debug_gemm": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                 C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
+                                 C.c_void_p, C.c_int64, C.c_int64, C.c_float, C.c_float, C.c_void_p, C.c_int32,
+                                 C.c_int32]),
     "sfs_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                C.POINTER(C.c_int64)]),
 }
@@ -138,6 +142,23 @@ class Surrogate:
     def set_sm_budget(self, n_sm):
         """SMs the fused forward may occupy (0: all)."""
         self._check(self.lib.sfs_set_sm_budget(self.h, int(n_sm)))
+
+    def debug_gemm(self, M, N, K, A, a_mn, lda, sA, B, b_mn, ldb, sB, Cm, ldc, sC, alpha=1.0, beta=0.0,
+                   bias=None, kchunk=0, batch=1):
+        """One tensor-core product C = alpha A B + beta C + bias (test entry
+        point; A, B float32 or bfloat16 CUDA tensors, Cm float32)."""
+        import torch
+
+        def ptr(t):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype in (torch.float32, torch.bfloat16)):
+                raise TypeError("expected a float32 or bfloat16 CUDA tensor")
+            return C.c_void_p(t.data_ptr()), 1 if t.dtype == torch.bfloat16 else 0
+
+        pa, abf = ptr(A)
+        pb, bbf = ptr(B)
+        self._check(self.lib.sfs_debug_gemm(self.h, M, N, K, pa, abf, a_mn, lda, sA, pb, bbf, b_mn, ldb, sB,
+                                            _dev(Cm), ldc, sC, float(alpha), float(beta),
+                                            _dev(bias) if bias is not None else None, kchunk, batch))
 
     def counters(self):
         g, f, k = C.c_int64(), C.c_double(), C.c_int64()
