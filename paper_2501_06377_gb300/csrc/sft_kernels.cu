@@ -175,15 +175,22 @@ __device__ __forceinline__ T weno_half(T p0, T p1, T b0, T b1, T eps) {
   return weno_div(a0 * p0 + a1 * p1, a0 + a1);
 }
 
+// The two halves of the split face flux: LM (from LM_{i-2}, LM_{i-1}, LM_i)
+// and LP (from LP_{i-1}, LP_i, LP_{i+1}).
+template <typename T>
+__device__ __forceinline__ T weno_lm(T lmm2, T lmm1, T lm0, T eps) {
+  const T dm0 = lmm1 - lmm2, dm1 = lm0 - lmm1;
+  return weno_half(T(1.5) * lmm1 - T(0.5) * lmm2, T(0.5) * (lmm1 + lm0), dm0 * dm0, dm1 * dm1, eps);
+}
+template <typename T>
+__device__ __forceinline__ T weno_lp(T lpm1, T lp0, T lpp1, T eps) {
+  const T dp0 = lpp1 - lp0, dp1 = lp0 - lpm1;
+  return weno_half(T(1.5) * lp0 - T(0.5) * lpp1, T(0.5) * (lp0 + lpm1), dp0 * dp0, dp1 * dp1, eps);
+}
+
 template <typename T>
 __device__ __forceinline__ T weno_flux(T lmm2, T lmm1, T lm0, T lpm1, T lp0, T lpp1, T eps) {
-  const T dm0 = lmm1 - lmm2, dm1 = lm0 - lmm1;
-  const T um = weno_half(T(1.5) * lmm1 - T(0.5) * lmm2, T(0.5) * (lmm1 + lm0), dm0 * dm0,
-                         dm1 * dm1, eps);
-  const T dp0 = lpp1 - lp0, dp1 = lp0 - lpm1;
-  const T up = weno_half(T(1.5) * lp0 - T(0.5) * lpp1, T(0.5) * (lp0 + lpm1), dp0 * dp0,
-                         dp1 * dp1, eps);
-  return um + up;
+  return weno_lm(lmm2, lmm1, lm0, eps) + weno_lp(lpm1, lp0, lpp1, eps);
 }
 
 }  // namespace
@@ -363,11 +370,17 @@ __device__ __forceinline__ void phi_faces(const AdvConst<T>& q, T v, const T (&e
       }
 #pragma unroll
       for (int i = 0; i <= N; ++i) F[i] = weno_flux(lm[i], lm[i + 1], lm[i + 2], lp[i + 1], lp[i + 2], lp[i + 3], eps);
-    } else {
-      const T hp = T(0.5) * (v + av), hm = T(0.5) * (v - av);
+    } else if (v >= T(0)) {
+      // v_phi is one value per row, so one half of the LLF split vanishes:
+      // hm = (v - |v|)/2 = 0 and the LP half-fluxes are zeros (the face flux
+      // is the LM half alone, up to the sign of a zero)
+      const T hp = T(0.5) * (v + av);
 #pragma unroll
-      for (int i = 0; i <= N; ++i)
-        F[i] = weno_flux(hp * e[i], hp * e[i + 1], hp * e[i + 2], hm * e[i + 1], hm * e[i + 2], hm * e[i + 3], eps);
+      for (int i = 0; i <= N; ++i) F[i] = weno_lm(hp * e[i], hp * e[i + 1], hp * e[i + 2], eps);
+    } else {
+      const T hm = T(0.5) * (v - av);  // hp = 0: the LP half alone
+#pragma unroll
+      for (int i = 0; i <= N; ++i) F[i] = weno_lp(hm * e[i + 1], hm * e[i + 2], hm * e[i + 3], eps);
     }
   } else {
 #pragma unroll

@@ -1,5 +1,6 @@
 """The no-allocation diagnostics entry point (sft_flux_diagnostics_noalloc)
-against the handle-based sft_flux_diagnostics, through the C-ABI.
+against the handle-based sft_flux_diagnostics, through the C-ABI, and on
+the smaller map against the FP64 oracle's Sec. 2.6 quantities directly.
 
 This entry point is for callers that cannot allocate device memory while
 they run (a solver inside a model whose memory pool already owns the
@@ -13,6 +14,7 @@ in its own file, collected last, and works alone in a fresh process.
 import numpy as np
 import pytest
 
+import oracle.sft_oracle as O
 import sft_inputs as I
 from paper_2501_06377_gb300 import build as B
 from paper_2501_06377_gb300.sft import Grid, flux_diagnostics_noalloc
@@ -54,6 +56,15 @@ def test_noalloc_diagnostics_match_handle_twice(prec):
            flux_diagnostics_noalloc(maps[1], lat_cut_deg=60.0)]
     for a, b in zip(got, refs):
         _compare(a, b)
+    # the 91 x 180 map against the oracle's definition (the map as the GPU holds it)
+    ref = O.diagnostics(O.Grid(91, 180), maps[1].double().cpu().numpy(), 60.0)
+    for k in SUM_FIELDS:
+        scale = max(abs(ref.flux_pos), 1.0) if k.startswith("flux") else max(abs(ref.brmax), 1.0)
+        if k.startswith("area"):
+            scale = max(abs(getattr(ref, k)), 1.0)
+        assert abs(got[1][k] - getattr(ref, k)) <= 1e-12 * scale, (k, got[1][k], getattr(ref, k))
+    for k in ("brmin", "brmax", "absmin"):
+        assert got[1][k] == getattr(ref, k), k
     # once the library's device code is loaded (first call in the context),
     # further calls take no device memory: the free figure does not move
     torch.cuda.synchronize()
