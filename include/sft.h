@@ -308,7 +308,7 @@ int32_t sft_get_tile_rows(sft_handle h, int32_t shape_id);
 
 /* Rows per band of the fused RKL2 work items for shape_id (a warp marches
  * one band of one strip): 0 = chosen by the built-in autotuner on the first
- * step (one timed launch per candidate 128, 256, 512), else rows > 8.
+ * step (one timed launch per candidate 64, 128, 256, 512), else rows > 8.
  * Results do not depend on it. */
 sft_status sft_set_band_rows(sft_handle h, int32_t shape_id, int32_t rows);
 

@@ -937,7 +937,7 @@ int adv_stage_count(sft_handle h) {
 }
 
 template <typename T>
-sft_status autotune(sft_handle h, Wave& w);
+sft_status autotune(sft_handle h, Wave& w, const std::vector<int>& active);
 
 template <typename T>
 sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
@@ -962,7 +962,10 @@ sft_status run_step(sft_handle h, Wave& w, double t_target, bool* any) {
   for (int r : w.reals) {
     const ShapeInfo& sh = h->shapes[h->reals[r].shape];
     if (sh.tile_rows == 0 || (h->fused && sh.band_rows == 0)) {
-      sft_status st = autotune<T>(h, w);
+      std::vector<int> active;  // realizations this step advances: the batch the choice serves
+      for (int i = 0; i < nw; ++i)
+        if (dt[i] > 0.0) active.push_back(w.reals[i]);
+      sft_status st = autotune<T>(h, w, active);
       if (st != SFT_OK) return st;
       break;
     }
@@ -1106,17 +1109,20 @@ sft_status set_band(sft_handle h, int si, int band) {
 
 // The fused kernel's band rows for shape si: one launch of eight stages
 // (stages 10..17 of a 30-stage super step, so that no launch is final and
-// only work arrays are written) over up to 32 of the wave's realizations of
-// that shape, timed for each candidate (128, 256, 512 rows; those no wider
-// than twice the interior), two rounds keeping each candidate's faster time.
+// only work arrays are written) over the realizations of that shape that the
+// step being planned advances (up to 1024: the batch the choice serves),
+// timed for each candidate (64, 128, 256, 512 rows; those above 128 no
+// wider than twice the interior), two rounds keeping each candidate's
+// faster time.  Short bands pay more halo rows but give a small batch more,
+// shorter work items (the march of one band is serial).
 // Results do not depend on the choice (every band computes the same stages
 // point for point); the work arrays and ring-sum partials it overwrites are
 // rebuilt by every step before they are read.
-sft_status tune_band(sft_handle h, Wave& w, int si) {
+sft_status tune_band(sft_handle h, const std::vector<int>& active, int si) {
   ShapeInfo& sh = h->shapes[si];
-  std::vector<int> members;
-  for (int r : w.reals)
-    if (h->reals[r].shape == si && members.size() < 32) members.push_back(r);
+  std::vector<int> members;  // the shape's realizations in the step being planned (at most 1024)
+  for (int r : active)
+    if (h->reals[r].shape == si && members.size() < 1024) members.push_back(r);
   if (members.empty()) return SFT_OK;
   const int S = 30, J0 = 10;
   std::vector<StepParam> sp(h->n_real);
@@ -1143,11 +1149,12 @@ sft_status tune_band(sft_handle h, Wave& w, int si) {
     err = cudaMemcpy(d_coef, coefs.data(), coefs.size() * sizeof(Coef<float>), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
-  const int cand[3] = {128, 256, 512};
+  constexpr int kCand = 4;
+  const int cand[kCand] = {64, 128, 256, 512};
   float* P[4] = {ptr<float>(h->work[1]), ptr<float>(h->work[2]), ptr<float>(h->work[3]), ptr<float>(h->work[4])};
-  for (int ci = 0; ci < 6 && err == cudaSuccess; ++ci) {
-    const int band = cand[ci % 3];
-    if (band != 128 && band >= 2 * (sh.nt - 2)) continue;
+  for (int ci = 0; ci < 2 * kCand && err == cudaSuccess; ++ci) {
+    const int band = cand[ci % kCand];
+    if (band > 128 && band >= 2 * (sh.nt - 2)) continue;
     sft_status st = set_band(h, si, band);
     if (st != SFT_OK) {
       err = cudaErrorUnknown;
@@ -1193,12 +1200,12 @@ sft_status tune_band(sft_handle h, Wave& w, int si) {
 }
 
 template <typename T>
-sft_status autotune(sft_handle h, Wave& w) {
+sft_status autotune(sft_handle h, Wave& w, const std::vector<int>& active) {
   for (size_t si = 0; si < h->shapes.size(); ++si) {
     ShapeInfo& sh = h->shapes[si];
     if constexpr (std::is_same<T, float>::value) {
       if (h->fused && sh.band_rows == 0) {
-        sft_status st = tune_band(h, w, (int)si);
+        sft_status st = tune_band(h, active, (int)si);
         if (st != SFT_OK) return st;
       }
     }
