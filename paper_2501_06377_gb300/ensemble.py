@@ -203,7 +203,7 @@ def _fetch(g, gs, members):
 
 
 def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, seed=7, max_fail=0.25,
-            solver_sms=48, solver_priority=-1):
+            solver_sms=24, solver_priority=-1):
     """Surrogate + judge + plain-solver fallback.  Returns (final maps, stats).
 
     A day on which more than ``max_fail`` of the spot checks fail rejects
@@ -269,7 +269,8 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
         err = net.rel_l2(chk_prop, chk_plain)
         spot_bad = np.zeros(n, dtype=bool)
         spot_bad[chk[err > l2_tol]] = True
-        if np.mean(err > l2_tol) > max_fail:
+        day_rejected = np.mean(err > l2_tol) > max_fail
+        if day_rejected:
             # untrustworthy day: every member advances with the plain solver
             rest = np.flatnonzero(~run)
             if len(rest):
@@ -287,7 +288,17 @@ def rollout(net: Surrogate, S0, P, days, drift_tol=1e-4, l2_tol=0.02, spot=32, s
         stats["rejected_spot"] += int((spot_bad & ~bad).sum())
         stats["spot_checked"] += len(chk)
         stats.setdefault("spot_l2_median", []).append(float(np.median(err)))
-        phi_old, abs_old = _fluxes(net, S)
+        if day_rejected:
+            phi_old, abs_old = _fluxes(net, S)
+        else:
+            # the new states' fluxes: an accepted member's is its proposal's
+            # (computed above), every other member took the solver's map,
+            # so only those maps are summed (the same kernel on the same
+            # values: the same numbers as summing all of S)
+            phi_old, abs_old = phi_new.copy(), abs_new.copy()
+            if len(idx):
+                fp, fa = _fluxes(net, plain)
+                phi_old[idx], abs_old[idx] = fp, fa
         te = time.perf_counter()
         ph["queue_spot_day"] += tb2 - tb
         ph["proposals_and_flux"] += (tb - ta) + (tc - tb2)
