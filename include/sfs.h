@@ -15,10 +15,12 @@
  *            weights per row/mode/channel) + residual;
  *            channel MLP C -> 2C -> C with GELU + residual }
  *   x_next = r + 100 G * unpatchify(h Wd + bd)
- * Every learned contraction is a BF16 tensor-core GEMM with FP32
- * accumulation (operands rounded to BF16 as they are staged); the fixed
- * rotation is an FP32 FFT per map row (the 512-point DFT, the phase, the
- * inverse transform).  Master weights, gradients and AdamW moments are FP32.
+ * Every learned contraction is a BF16 tensor-core product with FP32
+ * accumulation: in training a tcgen05 GEMM (accumulator in tensor memory;
+ * BF16 activations by TMA, FP32 ones rounded to BF16 as they are staged), in
+ * inference one fused mma.sync kernel; the fixed rotation is an FP32 FFT per
+ * map row (the 512-point DFT, the phase, the inverse transform).  Master
+ * weights, gradients and AdamW moments are FP32.
  *
  * Parameter vector order (FP32, flat): We[48][C], be[C], Wd[C][16], bd[16],
  * then per block l: w_l[64][M][C][2], W1_l[C][2C], b1_l[2C], W2_l[2C][C],
