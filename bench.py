@@ -388,7 +388,7 @@ def run_gpu(args, rank, world, local_rank):
     updates = st["cell_updates"] * world
     value = updates / (ms * 1e-3)
     peak, peak_kind = _peaks()
-    # per RKL2 pass (a fused pass = 8 stages; its launches on the two chains overlap)
+    # per RKL2 pass (a fused pass = 8 stages; the launches of the chains overlap)
     diff_pass_ms = st["diff_ms"] / max(st["diff_launches"], 1)
     diff_pass_bytes = st["diff_bytes"] / max(st["diff_launches"], 1)
     achieved = diff_pass_bytes / (diff_pass_ms * 1e-3) / 1e9
@@ -455,7 +455,7 @@ def run_gpu(args, rank, world, local_rank):
                                              "advection": st["adv_ms"] / args.steps,
                                              "rest": (ms - st["diff_ms"] - st["adv_ms"]) / args.steps}},
             "roofline": {"bound": "hbm",
-                         "kernel": ("rkl2_fused_kernel (8 RKL2 stages per launch, two launch chains)"
+                         "kernel": ("rkl2_fused_kernel (8 RKL2 stages per launch, up to six launch chains)"
                                     if g.get_fusion() > 1 else "rkl2_stage_kernel<float>"),
                          "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,

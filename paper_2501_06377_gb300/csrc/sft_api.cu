@@ -68,7 +68,7 @@ struct RealInfo {
   int64_t rfe_m0 = -1;    // map window whose balance factors are on the device (-1: none)
 };
 
-constexpr int kMaxChains = 2;   // concurrent launch chains of the fused RKL2 passes
+constexpr int kMaxChains = 6;   // concurrent launch chains of the fused RKL2 passes (2, 3, 4, 6, 8 measured)
 constexpr int kStageRing = 8;   // pinned staging buffers of the configuration tables
 constexpr int kMaxConfigs = 24; // cached step configurations (tile tables, graphs) per wave
 
@@ -696,8 +696,9 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
   if (c->fused) {
     // fused passes start at stages 2, 2+K, 2+2K, ...; stage 1 uses the
     // single-stage kernel (it forms G = dt L(Y_0)).
-    // a second chain pays off only when a pass fills the GPU several times
-    // over; small batches keep one chain (half the launches)
+    // more chains pay off only when a pass fills the GPU several times over
+    // (their launches overlap the other chains' shrinking tails as the
+    // members with fewer stages finish); small batches keep one chain
     size_t pass_tiles = 0;
     {
       std::vector<Tile> tmp;
