@@ -68,7 +68,7 @@ struct RealInfo {
   int64_t rfe_m0 = -1;    // map window whose balance factors are on the device (-1: none)
 };
 
-constexpr int kMaxChains = 6;   // concurrent launch chains of the fused RKL2 passes (2, 3, 4, 6, 8 measured)
+constexpr int kMaxChains = 6;   // concurrent launch chains of the fused RKL2 passes (at most)
 constexpr int kStageRing = 8;   // pinned staging buffers of the configuration tables
 constexpr int kMaxConfigs = 24; // cached step configurations (tile tables, graphs) per wave
 
@@ -698,14 +698,24 @@ sft_status build_config(sft_handle h, Wave& w, const std::vector<double>& dt,
     // single-stage kernel (it forms G = dt L(Y_0)).
     // more chains pay off only when a pass fills the GPU several times over
     // (their launches overlap the other chains' shrinking tails as the
-    // members with fewer stages finish); small batches keep one chain
+    // members with fewer stages finish); small batches keep one chain.  Six
+    // chains for large grids, two for small ones: measured on GB300, 64 x
+    // 1024x2048 (2 M cells a realization) runs 57.9 / 56.3 / 56.2 ms per
+    // step with 2 / 4 / 6 chains, 512 x 256x512 (131 K) 9250 / 9020 / 8880
+    // member-days/s.
     size_t pass_tiles = 0;
+    double pass_cells = 0.0;
     {
       std::vector<Tile> tmp;
-      for (int i : order) append_fused_interior(h, w.reals[i], tmp);
+      for (int i : order) {
+        append_fused_interior(h, w.reals[i], tmp);
+        const ShapeInfo& sh = h->shapes[h->reals[w.reals[i]].shape];
+        pass_cells += (double)sh.nt * sh.np;
+      }
       pass_tiles = tmp.size();
     }
-    c->n_chains = pass_tiles >= (size_t)4 * h->n_sm ? std::min<int>(kMaxChains, (int)order.size()) : 1;
+    const int want = pass_cells >= (double)(1 << 20) * (double)order.size() ? kMaxChains : 2;
+    c->n_chains = pass_tiles >= (size_t)4 * h->n_sm ? std::min<int>(want, (int)order.size()) : 1;
     for (int ch = 0; ch < c->n_chains; ++ch) {
       c->fbase[ch] = (int)ft.size();
       std::vector<int> mem, fend;  // chain members (descending s) and their interior tile ends
