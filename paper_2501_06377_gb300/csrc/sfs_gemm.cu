@@ -16,7 +16,12 @@
 //    mbarrier, which frees the stage for the next load;
 //  * the accumulator is BN columns of tensor memory; the epilogue reads it
 //    with tcgen05.ld (warp w: lanes 32 (w mod 4) .. +31, half w / 4 of the
-//    columns) and applies alpha, beta, bias.
+//    columns), transposes each warp's 32 x 32 block through padded shared
+//    memory and writes rows of 128 contiguous bytes, with alpha, beta and
+//    bias applied;
+//  * a CTA takes output tiles in turn (two CTAs per SM); the next tile's
+//    first operands are loaded and copied while the current accumulator is
+//    read out.
 // Every mbarrier wait gives up after about two seconds of global time: the
 // kernel then records a code in *err, waits (again bounded) for the copies
 // and products it issued, frees its tensor memory and returns.
