@@ -1280,14 +1280,7 @@ reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __res
   const double* w = aa.wpar ? aa.wpar + 4 * tl.r : nullptr;
   const int64_t obase = aa.obs_off ? aa.obs_off[tl.r] : 0;
   T tmn = T(INFINITY), tmx = T(-INFINITY), tamn = T(INFINITY);
-  // FP32 diagnostics: each row to one group of 64 threads (kThreads / 64
-  // rows at a time), so that a thread's FP64 row work (four conversions and
-  // the row-weighted sums) serves 4x more cells; every other mode: the whole
-  // block on each row
-  const bool grouped = mode == RED_DIAG && sizeof(T) == 4;
-  const int rgrp = grouped ? (int)(threadIdx.x >> 6) : 0, rstep = grouped ? kThreads / 64 : 1;
-  const int k0 = grouped ? (int)(threadIdx.x & 63) : (int)threadIdx.x, kstep = grouped ? 64 : (int)blockDim.x;
-  for (int j = j0 + rgrp; j < j1; j += rstep) {
+  for (int j = j0; j < j1; ++j) {
     const RowGeoD gd = geod[d.geo + j];
     const bool pole = (j == 0) || (j == d.nt - 1);
     const T* row = b + (int64_t)j * d.pitch;
@@ -1301,7 +1294,7 @@ reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __res
         // FP64 pipe is narrow), cos / sin phi as hi + lo float pairs; FP64
         // from the row sums on
         CSum ss, sp, sc, sn;
-        for (int k = k0; k < d.np; k += kstep) {
+        for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
           const float bv = float(row[k]);
           if (!isfinite(bv)) {
             acc[10] += 1.0;
@@ -1344,11 +1337,11 @@ reduce_kernel(int mode, const RedTile* __restrict__ tiles, const RealDesc* __res
       acc[2] += gd.area * (rs - rp);
       if (gd.lat >= lat_cut - 1e-12) {
         acc[3] += gd.area * rs;
-        if (k0 == 0) acc[5] += gd.area * d.np;  // once per row
+        if (threadIdx.x == 0) acc[5] += gd.area * d.np;
       }
       if (gd.lat <= -lat_cut + 1e-12) {
         acc[4] += gd.area * rs;
-        if (k0 == 0) acc[6] += gd.area * d.np;
+        if (threadIdx.x == 0) acc[6] += gd.area * d.np;
       }
       acc[7] += gd.area * gd.cos_t * rs;
       acc[8] += gd.area * gd.sin_t * rc;
